@@ -1,0 +1,124 @@
+"""Seeded synthetic workloads: the flow configurations and random test inputs.
+
+This module holds parameter sets and random-number draws only; none of the
+method's arithmetic lives here.  Both the CUDA path's tests and the oracle's
+tests take their inputs from it.
+
+Configurations (non-dimensional, chord = U_inf = 1):
+  plunge_192x128   uniform 192x128 on [-4,8]x[-4,4], ellipse t/c 0.12, Re 300,
+                   h 0.25, k 2, dt 2e-3, 100 steps, Poisson residual 1e-10.
+  plunge_2048x1024 stretched 2048x1024 on the paper's domain [-7.5,24]x[-12.5,12.5]
+                   (Sec. 2.3), min spacing 0.005, Re 1000, h 0.25, k 2, dt 1e-3,
+                   divergence 1e-8 (Poisson residual 1e-8/dt).
+  plunge_4096x2048 stretched 4096x2048, min spacing 0.0025, Re 1000, h 0.4, k 3,
+                   dt 5e-4, divergence 1e-8.
+  batch64          64 cases, numpy default_rng(17337): h~U[0.1,0.5], k~U[1,4],
+                   Re~U[100,1000], nx uniform on {512,576,...,1536}, ny = nx/2;
+                   min spacing 10/nx (uniform block ~30 % of nx), dt = 0.25 hmin/(1+k h).
+  unet_1024x512    1024x512, min spacing 0.01, dt 2e-3.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+PAPER_DOMAIN = (-7.5, 24.0, -12.5, 12.5)
+UBOX = (-1.0, 2.0, -0.75, 0.75)
+
+
+@dataclasses.dataclass
+class FlowConfig:
+    name: str
+    x0: float
+    x1: float
+    y0: float
+    y1: float
+    nx: int
+    ny: int
+    hmin: float            # <= 0: uniform grid
+    Re: float
+    dt: float
+    steps: int
+    h: float = 0.25        # plunge amplitude (chords)
+    k: float = 2.0         # reduced frequency
+    chord: float = 1.0
+    tc: float = 0.12       # thickness / chord
+    xc: float = 0.0
+    yc: float = 0.0
+    bc: int = 0
+    u_in: float = 1.0
+    ubox: tuple = UBOX
+    ptol: float = 1e-10    # Poisson residual infinity-norm tolerance
+    htol: float = 1e-12    # velocity-system residual tolerance
+    div_tol: float = 1e-8
+    check_p: int = 8
+    check_h: int = 2
+    omega_p: float | None = None
+    omega_h: float = 1.0
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny
+
+    def omega(self) -> float:
+        if self.omega_p is not None:
+            return self.omega_p
+        return 2.0 / (1.0 + math.sin(math.pi / max(self.nx, self.ny)))
+
+
+def plunge_192x128() -> FlowConfig:
+    return FlowConfig("plunge_192x128", -4.0, 8.0, -4.0, 4.0, 192, 128, 0.0, Re=300.0, dt=2e-3,
+                      steps=100, h=0.25, k=2.0, ptol=1e-10)
+
+
+def plunge_2048x1024() -> FlowConfig:
+    dt = 1e-3
+    return FlowConfig("plunge_2048x1024", *PAPER_DOMAIN, 2048, 1024, 0.005, Re=1000.0, dt=dt,
+                      steps=2000, h=0.25, k=2.0, ptol=1e-8 / dt)
+
+
+def plunge_4096x2048() -> FlowConfig:
+    dt = 5e-4
+    return FlowConfig("plunge_4096x2048", *PAPER_DOMAIN, 4096, 2048, 0.0025, Re=1000.0, dt=dt,
+                      steps=500, h=0.4, k=3.0, ptol=1e-8 / dt)
+
+
+def batch64(n: int = 64, seed: int = 17337) -> list[FlowConfig]:
+    rng = np.random.default_rng(seed)
+    out = []
+    sizes = np.arange(512, 1536 + 1, 64)
+    for c in range(n):
+        h = float(rng.uniform(0.1, 0.5))
+        k = float(rng.uniform(1.0, 4.0))
+        Re = float(rng.uniform(100.0, 1000.0))
+        nx = int(rng.choice(sizes))
+        ny = nx // 2
+        hmin = 10.0 / nx
+        dt = 0.25 * hmin / (1.0 + k * h)
+        out.append(FlowConfig(f"batch64[{c}]", *PAPER_DOMAIN, nx, ny, hmin, Re=Re, dt=dt, steps=1000,
+                              h=h, k=k, ptol=1e-8 / dt))
+    return out
+
+
+def unet_1024x512() -> FlowConfig:
+    dt = 2e-3
+    return FlowConfig("unet_1024x512", *PAPER_DOMAIN, 1024, 512, 0.01, Re=300.0, dt=dt, steps=1000,
+                      ptol=1e-10)
+
+
+def small_cases() -> list[FlowConfig]:
+    """Small grids for element-wise parity: several tiles and ragged edges."""
+    return [
+        FlowConfig("plunge_70x45_uniform", -2.0, 5.0, -2.25, 2.25, 70, 45, 0.0, Re=200.0, dt=4e-3,
+                   steps=6, h=0.3, k=2.5, ptol=1e-10, check_p=4),
+        FlowConfig("plunge_97x61_stretched", -7.5, 24.0, -12.5, 12.5, 97, 61, 0.08, Re=500.0,
+                   dt=5e-3, steps=5, h=0.25, k=2.0, ubox=(-1.0, 2.0, -0.8, 0.8), ptol=1e-10,
+                   check_p=6),
+    ]
+
+
+def random_field(shape, seed: int, scale: float = 1.0) -> np.ndarray:
+    """Seeded standard-normal field (float64)."""
+    return np.random.default_rng(seed).standard_normal(shape) * scale
