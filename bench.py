@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Throughput of the immersed-boundary fractional step on GB300.
+
+Metric: cell-steps/s (nx*ny*steps / device time), counted over steps whose
+divergence in fluid cells stays below the workload's tolerance.  A bench
+step is one full fractional step of the plunging-ellipse workload
+(classification, predictor, velocity solves, mass source, pressure solve,
+projection, forces) on the 2048x1024 stretched grid (Re 1000, h 0.25, k 2,
+dt 1e-3, divergence 1e-8).  Synthetic: the flow starts from rest.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the slow, plain restatement of
+the method) on the host cores with the same metric; under torchrun only rank
+0 runs it.  N > 1 runs independent replicas, one per GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP64_FLOPS_PER_CLK_SM = 4.0   # 2 FP64 FMA per clock per SM on GB300 (sm_103)
+SOR_FLOPS_PER_UPDATE = 12     # 4 products + 3 adds, minus b, times 1/d, relaxation (2)
+SOR_BYTES_PER_CELL_HALF = 16  # read phi (8, all cells), read b (4), write phi (4) per half-sweep
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax = max(smax, float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def solver_kwargs(cfg, precision):
+    return dict(x0=cfg.x0, x1=cfg.x1, y0=cfg.y0, y1=cfg.y1, nx=cfg.nx, ny=cfg.ny, hmin=cfg.hmin,
+                ubox=cfg.ubox, bc=cfg.bc, u_in=cfg.u_in, Re=cfg.Re, dt=cfg.dt, ptol=cfg.ptol,
+                htol=cfg.htol, check_p=cfg.check_p, check_h=cfg.check_h, omega_p=cfg.omega(),
+                omega_h=cfg.omega_h, precision=precision)
+
+
+def cpu_oracle_sample(cfg, state=None, max_seconds=60.0):
+    """Times the FP64 oracle on one full step of the workload (all host
+    cores), optionally started from a given (u, v, p, phi) state."""
+    import oracle
+    threads = os.cpu_count() or 1
+    kw = solver_kwargs(cfg, 0)
+    kw.pop("precision")
+    o = oracle.Sim(**kw, threads=threads)
+    o.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
+    if state is not None:
+        for name, arr in state.items():
+            o.set(name, arr)
+    t0 = time.perf_counter()
+    rc, st = o.step(1)
+    t = time.perf_counter() - t0
+    return {"seconds": t, "rc": rc, "sweeps_p": st["sweeps_p"], "threads": threads,
+            "div_max": st["div_max"]}
+
+
+def run_reference(args, cfg):
+    """--impl reference: the oracle on the host cores, same metric."""
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    kw = solver_kwargs(cfg, 0)
+    kw.pop("precision")
+    o = oracle.Sim(**kw, threads=threads)
+    o.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
+    for _ in range(args.warmup):
+        rc, _ = o.step(1)
+        if rc:
+            raise SystemExit(f"oracle failed during warm-up ({rc})")
+    times, ok, sweeps = [], 0, []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        rc, st = o.step(1)
+        times.append(time.perf_counter() - t0)
+        if rc:
+            raise SystemExit(f"oracle failed ({rc})")
+        ok += st["div_max"] < cfg.div_tol
+        sweeps.append(st["sweeps_p"])
+    T = sum(times)
+    value = cfg.cells * ok / T
+    line = {
+        "impl": "reference", "metric": "cell-steps/s", "value": value, "unit": "cell-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg.name, "nx": cfg.nx, "ny": cfg.ny, "global_batch": 1, "path": "cpu-oracle",
+                   "poisson_sweeps_per_step": statistics.mean(sweeps)},
+        "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{args.warmup} untimed + {args.steps} timed full steps of {cfg.name} "
+                                   f"from rest, FP64 oracle, {threads} OpenMP threads in the pressure solve"},
+        "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64"], default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+
+    from paper_2402_17337_gb300 import workloads as W
+    cfg = W.plunge_2048x1024()
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+
+    import numpy as np
+    import torch
+
+    import paper_2402_17337_gb300 as ibm
+    from paper_2402_17337_gb300 import build as B
+
+    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    B.build()
+
+    stream = torch.cuda.Stream()
+    precision = 0
+    s = ibm.Solver(**solver_kwargs(cfg, precision), stream=stream.cuda_stream)
+    s.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
+    for _ in range(args.warmup):
+        s.step(1)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # --------------------------------------------------- device-timed window
+    start_state = {n: s.get(n) for n in ("u", "v", "p", "phi")} if rank == 0 else None
+    s.set_profiling(True)
+    prof0 = s.profile()
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(s.step(1))
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile()
+    ok_steps = sum(1 for st in stats if st["div_max"] < cfg.div_tol)
+    t_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        okt = torch.tensor([ok_steps], device="cuda")
+        dist.all_reduce(okt)
+        total_ok = int(okt.item())
+    else:
+        total_ok = ok_steps
+    value = cfg.cells * total_ok / (t_max / 1e3)
+    launches = prof["launches"] - prof0["launches"]
+
+    # roofline of the dominant kernel (FP64 red-black SOR half-sweep)
+    peaks, peak_src = load_peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp64_peak = n_sm * FP64_FLOPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    roof = None
+    if prof["sweep_launches"] > 0:
+        t_launch = prof["sweep_ms"] / prof["sweep_launches"] / 1e3
+        flops = SOR_FLOPS_PER_UPDATE * cfg.cells / 2
+        achieved = flops / t_launch / 1e12
+        roof = {"bound": "alu", "kernel": "k_poisson_half (FP64 red-black SOR half-sweep)",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "traffic": None, "launch_us": t_launch * 1e6,
+                "hbm_gbs": SOR_BYTES_PER_CELL_HALF * cfg.cells / t_launch / 1e9,
+                "peak_note": f"FP64: {n_sm} SMs x 4 flop/clk x {sm_mhz:.0f} MHz; HBM peak "
+                             f"{peaks.get('hbm_gbs')} GB/s ({peak_src})"}
+
+    # ------------------------------------------------------------- end to end
+    e2e = None
+    if not args.no_e2e:
+        names = ("u", "v", "p", "phi")
+        pinned = {n: torch.empty(s.shape(n), dtype=torch.float64, pin_memory=True).numpy() for n in names}
+        for n in names:
+            pinned[n][...] = s.get(n)
+        h2d = sum(a.nbytes for a in pinned.values())
+        barrier()
+        t0 = time.perf_counter()
+        ok_e2e = 0
+        for _ in range(args.steps):
+            for n in names:
+                s.set(n, pinned[n])
+            st = s.step(1)
+            for n in names:
+                pinned[n][...] = s.get(n)
+            ok_e2e += st["div_max"] < cfg.div_tol
+        barrier()
+        te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": cfg.cells * ok_e2e * world / te, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": h2d,
+               "note": "per step: u, v, p, phi copied in from pinned host memory, step, copied back"}
+
+    # ------------------------------------------------------------ CPU oracle
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        r = cpu_oracle_sample(cfg, start_state)
+        cpu = {"value": cfg.cells / r["seconds"] if r["rc"] == 0 else None, "unit": "cell-steps/s",
+               "cores": r["threads"], "kind": "oracle",
+               "sample": f"one full step of {cfg.name} started from the GPU run's state at the start of the "
+                         f"timed window (AB2 history restarted), {r['sweeps_p']} pressure sweeps, "
+                         f"{r['seconds']:.1f} s, FP64 oracle, {r['threads']} OpenMP threads in the pressure solve"}
+
+    if rank == 0:
+        sweeps = [st["sweeps_p"] for st in stats]
+        line = {
+            "metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": cfg.name, "nx": cfg.nx, "ny": cfg.ny, "global_batch": world,
+                       "parallelism": f"replicas x{world}", "path": "fp64",
+                       "steps_counted": total_ok, "poisson_sweeps_per_step": statistics.mean(sweeps),
+                       "helm_sweeps_per_step": statistics.mean(st["sweeps_u"] + st["sweeps_v"] for st in stats),
+                       "l2": "state 14 FP64 fields x 17 MB > L2; no flush",
+                       "div_max": max(st["div_max"] for st in stats)},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * libibm: GB300 (sm_103a) implementation of one fractional time step of the
+ * discrete-forcing immersed-boundary solver of Sundar, Majumdar, Shah &
+ * Sarkar, "Massive parallelization and performance enhancement of an
+ * immersed boundary method based unsteady flow solver", arXiv 2402.17337.
+ *
+ * The paper's problem (Sec. 2.1-2.3): 2-D incompressible laminar flow past
+ * a rigid elliptic foil of thickness/chord t/c that plunges sinusoidally,
+ * y = h sin(k t), ydot = k h cos(k t) (Eqs. 1-2), governed by the
+ * non-dimensional Navier-Stokes equations with momentum forcing f and mass
+ * source q (Eqs. 3-4), on a Cartesian staggered grid that is uniform where
+ * the body moves and stretched geometrically outward (Sec. 2.3), advanced
+ * by a semi-implicit fractional step (Adams-Bashforth convection,
+ * Crank-Nicolson diffusion) whose velocity and pressure-correction systems
+ * are solved by red-black Gauss-Seidel SOR (Sec. 2.2, Sec. 3.1).
+ *
+ * Units are non-dimensional: chord, free-stream speed and density are 1.
+ *
+ * Conventions of every entry point:
+ *   - return IBM_OK (0) on success, a negative IBM_E_* code otherwise; the
+ *     message of the last failure on the calling thread is returned by
+ *     ibm_last_error();
+ *   - the context owns all of its device memory; host buffers passed in are
+ *     owned by the caller and are only read or written during the call;
+ *   - fields cross the boundary in a compact row-major layout, x fastest:
+ *       u  (nx+1) x ny   u[j*(nx+1)+i] at (x_f[i], y_c[j])
+ *       v  nx x (ny+1)   v[j*nx+i]     at (x_c[i], y_f[j])
+ *       p  nx x ny       p[j*nx+i]     at cell centres
+ *   - all GPU work of a context runs on the stream given at creation (or on
+ *     a stream the context creates); calls that return host data wait for it.
+ */
+#ifndef IBM_H_
+#define IBM_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IBM_OK 0
+#define IBM_E_INVAL (-1)    /* bad argument or state */
+#define IBM_E_CUDA (-2)     /* a CUDA call failed */
+#define IBM_E_NOCONV (-3)   /* an SOR solve hit max_sweeps before its tolerance */
+#define IBM_E_DIVERGED (-4) /* a residual norm became NaN or Inf */
+#define IBM_E_TIMEOUT (-5)  /* a bounded device-side wait gave up */
+
+typedef struct ibm_ctx ibm_ctx;
+
+/* Grid, flow and solver parameters (Sec. 2.1-2.3).
+ *   x0,x1,y0,y1  rectangular domain; the paper uses [-7.5,24] x [-12.5,12.5]
+ *   nx,ny        number of cells (>= 4 each)
+ *   hmin         <= 0: uniform grid; otherwise the spacing of the uniform block
+ *                ubox = [bx0,bx1] x [by0,by1]; outside it the spacing grows
+ *                geometrically to the domain edge (Sec. 2.3)
+ *   bc           0: inflow u = u_in, v = 0 at x0, convective outflow at x1,
+ *                   free-slip walls at y0,y1;  1: free-slip walls all round
+ *   Re, dt       Reynolds number and time step
+ *   precision    0: FP64 throughout;  1: FP32 SOR sweeps inside FP64 defect
+ *                correction (residuals, updates, norms and forces in FP64)
+ *   poisson_tol  the pressure solve stops when
+ *   poisson_rtol ||b - L_p phi||_inf <= max(poisson_tol, poisson_rtol*||b||_inf);
+ *                the divergence left in fluid cells is dt times that residual
+ *   helm_tol     velocity solves stop when their residual <= helm_tol
+ *   check_every_p, check_every_h  residual checked every m full sweeps (<=0: 8, 2)
+ *   max_sweeps   cap per solve (<= 0: 1000000)
+ *   omega_p      SOR factor of the pressure solve (<= 0: 2/(1+sin(pi/max(nx,ny))))
+ *   omega_h      SOR factor of the velocity solves (<= 0: 1)
+ *   cuda_stream  cudaStream_t to run on, or NULL for a stream owned by the context */
+typedef struct {
+  double x0, x1, y0, y1;
+  int nx, ny;
+  double hmin;
+  double ubox[4];
+  int bc;
+  double u_in;
+  double Re, dt;
+  int precision;
+  double poisson_tol, poisson_rtol, helm_tol;
+  int check_every_p, check_every_h;
+  int max_sweeps;
+  double omega_p, omega_h;
+  void* cuda_stream;
+} ibm_grid_params;
+
+/* Statistics of one step. */
+typedef struct {
+  int n;                 /* steps completed */
+  double t;              /* time after the step */
+  int sweeps_u, sweeps_v, sweeps_p;
+  double res_u, res_v, res_p;
+  double div_max;        /* max |div u| over cells whose centre is in the fluid */
+  double cl, cd;         /* lift and drag coefficients of the step */
+} ibm_step_stats;
+
+/* Builds the grid (Sec. 2.3), allocates the fields on the device, zero
+ * interior flow with u = u_in on the inflow face.  *out receives the context.
+ * Errors: IBM_E_INVAL for inconsistent parameters, IBM_E_CUDA. */
+int ibm_create_grid(const ibm_grid_params* params, ibm_ctx** out);
+
+/* Places an elliptic body (Sec. 2.1): chord along x, semi-axes chord/2 and
+ * thickness_ratio*chord/2 (1 = circle), centre (xc, yc + h sin(k t)),
+ * plunge velocity k h cos(k t) (Eqs. 1-2).  h = 0 gives a fixed body.
+ * Must come before the first step; fails with IBM_E_INVAL otherwise or when
+ * the body's swept region does not fit inside the grid. */
+int ibm_set_body(ibm_ctx* ctx, double chord, double thickness_ratio, double h, double k, double xc,
+                 double yc);
+
+/* Advances nsteps fractional steps (Sec. 2.2): classification of the nodes
+ * at t^{n+1}, explicit predictor, implicit velocity solves with the forcing
+ * rows, right-hand side with the mass source, pressure solve, projection,
+ * forces.  *last (may be NULL) receives the statistics of the last step.
+ * On IBM_E_NOCONV / IBM_E_DIVERGED the failing step is not counted. */
+int ibm_step(ibm_ctx* ctx, int nsteps, ibm_step_stats* last);
+
+/* Copies the lift and drag histories (one entry per completed step) into
+ * cl and cd (either may be NULL), at most cap entries; *n_out = steps done. */
+int ibm_forces(const ibm_ctx* ctx, double* cl, double* cd, int cap, int* n_out);
+
+/* Field ids for ibm_get_field / ibm_set_field. */
+#define IBM_U 0
+#define IBM_V 1
+#define IBM_P 2
+#define IBM_PHI 3   /* last pressure increment (gauge cell zero) */
+#define IBM_B 4     /* last Poisson right-hand side */
+#define IBM_UHAT 5  /* last intermediate velocity */
+#define IBM_VHAT 6
+#define IBM_RU 7    /* last explicit right-hand side of the u system */
+#define IBM_RV 8
+#define IBM_HU 9    /* last convective term div(u u) */
+#define IBM_HV 10
+#define IBM_Q 11    /* last mass source */
+
+/* Copies field `which` into host (n must equal the field's size). */
+int ibm_get_field(const ibm_ctx* ctx, int which, double* host, size_t n);
+
+/* Overwrites u, v, p or phi from host (n must equal the field's size). */
+int ibm_set_field(ibm_ctx* ctx, int which, const double* host, size_t n);
+
+/* Classification of the last step: grid 0 = u nodes, 1 = v nodes (kind
+ * 0 fluid, 1 solid, 2 forcing; dir = side of the wall 0 -x, 1 +x, 2 -y, 3 +y;
+ * alpha = interpolation weight), grid 2 = cells (1 = centre inside the body;
+ * dir and alpha unused).  Full field size n, any of the pointers may be NULL. */
+int ibm_get_flags(const ibm_ctx* ctx, int grid, unsigned char* kind, unsigned char* dir, double* alpha,
+                  size_t n);
+
+/* Face coordinates x_f (nx+1) and y_f (ny+1). */
+int ibm_get_grid(const ibm_ctx* ctx, double* xf, double* yf);
+
+/* Solves L_p phi = b (homogeneous Neumann) by red-black SOR on the
+ * context's grid, as inside a step (Sec. 2.2), to
+ * ||b - L_p phi||_inf <= tol checked every check_every sweeps, then shifts
+ * phi so that the cell (nx-1, 0) is zero.  b_dev, phi_dev: device pointers
+ * to nx*ny doubles in the compact layout; phi_dev holds the initial guess
+ * and receives the result.  Uses the context's work arrays, so it must not
+ * overlap a step of the same context.  *sweeps and *res (may be NULL)
+ * receive the sweep count and the final residual norm. */
+int ibm_poisson_solve(ibm_ctx* ctx, const double* b_dev, double* phi_dev, double tol, int check_every,
+                      int max_sweeps, int* sweeps, double* res);
+
+/* Counters of a context.  With profiling on, each run of pressure SOR
+ * launches between two residual checks is bracketed by CUDA events on the
+ * context's stream; sweep_ms is the summed device time of those runs and
+ * sweep_launches the number of launches they contain. */
+typedef struct {
+  long long launches;        /* kernels launched by this context */
+  long long sweep_launches;  /* pressure SOR sweep launches inside timed runs */
+  double sweep_ms;           /* device time of those runs */
+  long long steps;           /* steps completed */
+  long long poisson_sweeps;  /* pressure sweeps over all steps */
+  long long helm_sweeps;     /* velocity sweeps over all steps (u and v) */
+} ibm_profile;
+
+/* Turns the event timing of pressure sweeps on (1) or off (0); counters are
+ * reset.  Timing adds one event pair per run of sweeps. */
+int ibm_set_profiling(ibm_ctx* ctx, int on);
+
+/* Copies the counters. */
+int ibm_get_profile(const ibm_ctx* ctx, ibm_profile* out);
+
+/* Frees the context and its device memory. */
+void ibm_destroy(ibm_ctx* ctx);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* ibm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IBM_H_ */

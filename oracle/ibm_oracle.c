@@ -28,6 +28,14 @@
  *   v   nx x (ny+1)   v[j*nx+i],     centre x_c[i], face y_f[j]
  *   p   nx x ny       p[j*nx+i]
  * Build with -ffp-contract=off so every product and sum is rounded alone.
+ *
+ * Arithmetic recipe.  Where floating point decides an integer (the SOR
+ * iteration count, a node's kind) the GPU path must take the same decision,
+ * so both follow one recipe: divisions by grid spacings are multiplications
+ * by reciprocals computed once, the 5-point operators are fused
+ * multiply-add chains in the order E, W, N, S (fma() below), and the two
+ * sums that feed back into the flow (outflow flux, body-cell source) are
+ * accumulated in index order.  Everything else is a plain expression.
  */
 #include <math.h>
 #include <stdint.h>
@@ -79,6 +87,10 @@ typedef struct {
   double *xf, *yf, *dx, *dy, *xc, *yc;
   double *dxc, *dyc; /* dxc[i] = xc[i]-xc[i-1], i=1..nx-1 (index 0, nx unused) */
   double *wx, *wy;   /* face interpolation weights, i=1..nx-1 */
+  double *idx, *idy, *idxc, *idyc;      /* reciprocals of dx, dy, dxc, dyc */
+  /* 5-point coefficients a_nb of sum_nb a_nb (x_nb - x_P); zero through walls */
+  double *pE, *pW, *pN, *pS, *uE, *uW, *uN, *uS, *vE, *vW, *vN, *vS;
+  double *ipd, *iud, *ivd;              /* reciprocal SOR diagonals per node */
   /* fields */
   double *u, *v, *p, *phi;
   double *uh, *vh, *Ru, *Rv, *Hu, *Hv, *Huo, *Hvo;
@@ -206,6 +218,60 @@ or_sim* or_create(const or_params* P) {
     S->dyc[j] = S->yc[j] - S->yc[j - 1];
     S->wy[j] = (S->yf[j] - S->yc[j - 1]) / S->dyc[j];
   }
+  S->idx = xcalloc(nx, 8); S->idy = xcalloc(ny, 8);
+  S->idxc = xcalloc(nx + 1, 8); S->idyc = xcalloc(ny + 1, 8);
+  for (int i = 0; i < nx; ++i) S->idx[i] = 1.0 / S->dx[i];
+  for (int j = 0; j < ny; ++j) S->idy[j] = 1.0 / S->dy[j];
+  for (int i = 1; i < nx; ++i) S->idxc[i] = 1.0 / S->dxc[i];
+  for (int j = 1; j < ny; ++j) S->idyc[j] = 1.0 / S->dyc[j];
+  /* pressure grid: homogeneous Neumann (no flux through the boundary) */
+  S->pE = xcalloc(nx, 8); S->pW = xcalloc(nx, 8); S->pN = xcalloc(ny, 8); S->pS = xcalloc(ny, 8);
+  for (int i = 0; i < nx; ++i) {
+    S->pE[i] = i < nx - 1 ? 1.0 / (S->dx[i] * S->dxc[i + 1]) : 0.0;
+    S->pW[i] = i > 0 ? 1.0 / (S->dx[i] * S->dxc[i]) : 0.0;
+  }
+  for (int j = 0; j < ny; ++j) {
+    S->pN[j] = j < ny - 1 ? 1.0 / (S->dy[j] * S->dyc[j + 1]) : 0.0;
+    S->pS[j] = j > 0 ? 1.0 / (S->dy[j] * S->dyc[j]) : 0.0;
+  }
+  /* u grid (CV [xc_{i-1},xc_i] x [yf_j,yf_{j+1}]): faces i=0, nx carry
+   * Dirichlet values; free-slip walls y0, y1 pass no flux */
+  S->uE = xcalloc(nx + 1, 8); S->uW = xcalloc(nx + 1, 8); S->uN = xcalloc(ny, 8); S->uS = xcalloc(ny, 8);
+  for (int i = 1; i < nx; ++i) {
+    S->uE[i] = 1.0 / (S->dx[i] * S->dxc[i]);
+    S->uW[i] = 1.0 / (S->dx[i - 1] * S->dxc[i]);
+  }
+  for (int j = 0; j < ny; ++j) {
+    S->uN[j] = j < ny - 1 ? 1.0 / (S->dyc[j + 1] * S->dy[j]) : 0.0;
+    S->uS[j] = j > 0 ? 1.0 / (S->dyc[j] * S->dy[j]) : 0.0;
+  }
+  /* v grid (CV [xf_i,xf_{i+1}] x [yc_{j-1},yc_j]): rows j=0, ny carry v = 0.
+   * At x0 the inflow (bc 0) holds v = 0 on the boundary, half a cell from
+   * the node: flux 2 (0 - v)/dx, i.e. twice the coefficient with a zero
+   * neighbour; free slip (bc 1) passes no flux.  At x1 zero flux. */
+  S->vE = xcalloc(nx, 8); S->vW = xcalloc(nx, 8); S->vN = xcalloc(ny + 1, 8); S->vS = xcalloc(ny + 1, 8);
+  for (int i = 0; i < nx; ++i) {
+    S->vE[i] = i < nx - 1 ? 1.0 / (S->dxc[i + 1] * S->dx[i]) : 0.0;
+    S->vW[i] = i > 0 ? 1.0 / (S->dxc[i] * S->dx[i]) : (P->bc == 0 ? 2.0 / (S->dx[0] * S->dx[0]) : 0.0);
+  }
+  for (int j = 1; j < ny; ++j) {
+    S->vN[j] = 1.0 / (S->dy[j] * S->dyc[j]);
+    S->vS[j] = 1.0 / (S->dy[j - 1] * S->dyc[j]);
+  }
+  {
+    double beta = P->dt / (2.0 * P->Re);
+    S->ipd = xcalloc((size_t)nx * ny, 8);
+    S->iud = xcalloc((size_t)(nx + 1) * ny, 8);
+    S->ivd = xcalloc((size_t)nx * (ny + 1), 8);
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) S->ipd[(size_t)j * nx + i] = 1.0 / (S->pE[i] + S->pW[i] + S->pN[j] + S->pS[j]);
+    for (int j = 0; j < ny; ++j)
+      for (int i = 1; i < nx; ++i)
+        S->iud[(size_t)j * (nx + 1) + i] = 1.0 / (1.0 + beta * (S->uE[i] + S->uW[i] + S->uN[j] + S->uS[j]));
+    for (int j = 1; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        S->ivd[(size_t)j * nx + i] = 1.0 / (1.0 + beta * (S->vE[i] + S->vW[i] + S->vN[j] + S->vS[j]));
+  }
   size_t nu = (size_t)(nx + 1) * ny, nv = (size_t)nx * (ny + 1), np = (size_t)nx * ny;
   S->u = xcalloc(nu, 8); S->uh = xcalloc(nu, 8); S->Ru = xcalloc(nu, 8);
   S->Hu = xcalloc(nu, 8); S->Huo = xcalloc(nu, 8);
@@ -229,7 +295,8 @@ void or_destroy(or_sim* S) {
   void* ptrs[] = {S->xf, S->yf, S->dx, S->dy, S->xc, S->yc, S->dxc, S->dyc, S->wx, S->wy,
                   S->u, S->uh, S->Ru, S->Hu, S->Huo, S->v, S->vh, S->Rv, S->Hv, S->Hvo,
                   S->p, S->phi, S->D, S->q, S->b, S->fu, S->fv, S->du, S->dv, S->au, S->av,
-                  S->cut, S->cl, S->cd};
+                  S->cut, S->cl, S->cd, S->idx, S->idy, S->idxc, S->idyc, S->pE, S->pW, S->pN, S->pS,
+                  S->uE, S->uW, S->uN, S->uS, S->vE, S->vW, S->vN, S->vS, S->ipd, S->iud, S->ivd};
   for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
   free(S);
 }
@@ -248,46 +315,45 @@ int or_get_grid(const or_sim* S, double* xf, double* yf) {
 
 /* ------------------------------------------------- discrete operators (Sec. 2.2) */
 
-/* Laplacian on the u grid (CV [xc[i-1],xc[i]] x [yf[j],yf[j+1]]):
- * free-slip walls give zero flux through y=y0,y1; the faces i=0 and i=nx hold
- * Dirichlet values.  Defined at unknown nodes i=1..nx-1. */
+/* 5-point finite-volume Laplacian sum_nb a_nb (x_nb - x_P) as an fma chain
+ * in the order E, W, N, S; a missing neighbour (outside the node range)
+ * enters with value 0 and, except at an inflow face, a zero coefficient. */
+static double lap5(double aE, double aW, double aN, double aS, double xE, double xW, double xN, double xS,
+                   double c) {
+  double L = aE * (xE - c);
+  L = fma(aW, xW - c, L);
+  L = fma(aN, xN - c, L);
+  L = fma(aS, xS - c, L);
+  return L;
+}
+
+/* Laplacian on the u grid at unknown nodes i = 1..nx-1, j = 0..ny-1 */
 static double lap_u_at(const or_sim* S, const double* u, int i, int j) {
   int nx = S->nx, ny = S->ny;
   double c = u[UI(i, j)];
-  double fe = (u[UI(i + 1, j)] - c) / S->dx[i];
-  double fw = (c - u[UI(i - 1, j)]) / S->dx[i - 1];
-  double fn = (j < ny - 1) ? (u[UI(i, j + 1)] - c) / S->dyc[j + 1] : 0.0;
-  double fs = (j > 0) ? (c - u[UI(i, j - 1)]) / S->dyc[j] : 0.0;
-  return (fe - fw) / S->dxc[i] + (fn - fs) / S->dy[j];
+  double xN = j < ny - 1 ? u[UI(i, j + 1)] : 0.0;
+  double xS = j > 0 ? u[UI(i, j - 1)] : 0.0;
+  return lap5(S->uE[i], S->uW[i], S->uN[j], S->uS[j], u[UI(i + 1, j)], u[UI(i - 1, j)], xN, xS, c);
 }
 
-/* Laplacian on the v grid (CV [xf[i],xf[i+1]] x [yc[j-1],yc[j]]).  Walls y0,y1
- * carry v=0 (Dirichlet face values).  At x0: inflow (bc 0) v=0 on the boundary,
- * half a cell away from the node; free-slip box (bc 1) zero flux.  At x1: zero
- * normal gradient (outflow) or free slip, both zero flux. */
+/* Laplacian on the v grid at unknown nodes i = 0..nx-1, j = 1..ny-1 */
 static double lap_v_at(const or_sim* S, const double* v, int i, int j) {
   int nx = S->nx;
   double c = v[VI(i, j)];
-  double fe = (i < nx - 1) ? (v[VI(i + 1, j)] - c) / S->dxc[i + 1] : 0.0;
-  double fw;
-  if (i > 0)
-    fw = (c - v[VI(i - 1, j)]) / S->dxc[i];
-  else
-    fw = (S->P.bc == 0) ? (c - 0.0) / (0.5 * S->dx[0]) : 0.0;
-  double fn = (v[VI(i, j + 1)] - c) / S->dy[j];
-  double fs = (c - v[VI(i, j - 1)]) / S->dy[j - 1];
-  return (fe - fw) / S->dx[i] + (fn - fs) / S->dyc[j];
+  double xE = i < nx - 1 ? v[VI(i + 1, j)] : 0.0;
+  double xW = i > 0 ? v[VI(i - 1, j)] : 0.0;
+  return lap5(S->vE[i], S->vW[i], S->vN[j], S->vS[j], xE, xW, v[VI(i, j + 1)], v[VI(i, j - 1)], c);
 }
 
 /* Pressure Laplacian L_p = D G with homogeneous Neumann boundaries. */
 static double lap_p_at(const or_sim* S, const double* f, int i, int j) {
   int nx = S->nx, ny = S->ny;
   double c = f[PI_(i, j)];
-  double fe = (i < nx - 1) ? (f[PI_(i + 1, j)] - c) / S->dxc[i + 1] : 0.0;
-  double fw = (i > 0) ? (c - f[PI_(i - 1, j)]) / S->dxc[i] : 0.0;
-  double fn = (j < ny - 1) ? (f[PI_(i, j + 1)] - c) / S->dyc[j + 1] : 0.0;
-  double fs = (j > 0) ? (c - f[PI_(i, j - 1)]) / S->dyc[j] : 0.0;
-  return (fe - fw) / S->dx[i] + (fn - fs) / S->dy[j];
+  double xE = i < nx - 1 ? f[PI_(i + 1, j)] : 0.0;
+  double xW = i > 0 ? f[PI_(i - 1, j)] : 0.0;
+  double xN = j < ny - 1 ? f[PI_(i, j + 1)] : 0.0;
+  double xS = j > 0 ? f[PI_(i, j - 1)] : 0.0;
+  return lap5(S->pE[i], S->pW[i], S->pN[j], S->pS[j], xE, xW, xN, xS, c);
 }
 
 /* Convective flux divergence H = div(u u), second-order central finite volume,
@@ -308,9 +374,8 @@ static double conv_u_at(const or_sim* S, const double* u, const double* v, int i
     double us = (1.0 - S->wy[j]) * u[UI(i, j - 1)] + S->wy[j] * u[UI(i, j)];
     fs = vs * us;
   }
-  return (ue * ue - uw * uw) / S->dxc[i] + (fn - fs) / S->dy[j];
+  return (ue * ue - uw * uw) * S->idxc[i] + (fn - fs) * S->idy[j];
 }
-
 static double conv_v_at(const or_sim* S, const double* u, const double* v, int i, int j) {
   int nx = S->nx;
   double vn = 0.5 * (v[VI(i, j)] + v[VI(i, j + 1)]);
@@ -325,7 +390,7 @@ static double conv_v_at(const or_sim* S, const double* u, const double* v, int i
     vw = (1.0 - S->wx[i]) * v[VI(i - 1, j)] + S->wx[i] * v[VI(i, j)];
   else
     vw = (S->P.bc == 0) ? 0.0 : v[VI(i, j)];
-  return (ue * ve - uw * vw) / S->dx[i] + (vn * vn - vs * vs) / S->dyc[j];
+  return (ue * ve - uw * vw) * S->idx[i] + (vn * vn - vs * vs) * S->idyc[j];
 }
 
 /* exported operator wrappers (canonical layouts; entries that are not
@@ -362,17 +427,16 @@ void or_grad(const or_sim* S, const double* f, double* gu, double* gv) {
   memset(gu, 0, sizeof(double) * (nx + 1) * ny);
   memset(gv, 0, sizeof(double) * nx * (ny + 1));
   for (int j = 0; j < ny; ++j)
-    for (int i = 1; i < nx; ++i) gu[UI(i, j)] = (f[PI_(i, j)] - f[PI_(i - 1, j)]) / S->dxc[i];
+    for (int i = 1; i < nx; ++i) gu[UI(i, j)] = (f[PI_(i, j)] - f[PI_(i - 1, j)]) * S->idxc[i];
   for (int j = 1; j < ny; ++j)
-    for (int i = 0; i < nx; ++i) gv[VI(i, j)] = (f[PI_(i, j)] - f[PI_(i, j - 1)]) / S->dyc[j];
+    for (int i = 0; i < nx; ++i) gv[VI(i, j)] = (f[PI_(i, j)] - f[PI_(i, j - 1)]) * S->idyc[j];
 }
 /* divergence of a face field, per cell */
 void or_div(const or_sim* S, const double* u, const double* v, double* out) {
   int nx = S->nx, ny = S->ny;
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i)
-      out[PI_(i, j)] = (u[UI(i + 1, j)] - u[UI(i, j)]) / S->dx[i] +
-                       (v[VI(i, j + 1)] - v[VI(i, j)]) / S->dy[j];
+      out[PI_(i, j)] = (u[UI(i + 1, j)] - u[UI(i, j)]) * S->idx[i] + (v[VI(i, j + 1)] - v[VI(i, j)]) * S->idy[j];
 }
 
 /* ------------------------------------------ classification (Sec. 2.2, "flagging") */
@@ -504,6 +568,38 @@ int or_get_flags(const or_sim* S, int grid, unsigned char* flags, unsigned char*
 
 /* --------------------------------------------- Helmholtz (Crank-Nicolson) solve */
 
+/* node value and neighbours on grid 0 (u) or 1 (v); a neighbour outside the
+ * grid's node range reads as 0 */
+static void helm_nb(const or_sim* S, int grid, const double* x, int i, int j, double* xE, double* xW, double* xN,
+                    double* xS) {
+  int nx = S->nx, ny = S->ny;
+  if (grid == 0) {
+    *xE = x[UI(i + 1, j)];
+    *xW = x[UI(i - 1, j)];
+    *xN = j < ny - 1 ? x[UI(i, j + 1)] : 0.0;
+    *xS = j > 0 ? x[UI(i, j - 1)] : 0.0;
+  } else {
+    *xE = i < nx - 1 ? x[VI(i + 1, j)] : 0.0;
+    *xW = i > 0 ? x[VI(i - 1, j)] : 0.0;
+    *xN = x[VI(i, j + 1)];
+    *xS = x[VI(i, j - 1)];
+  }
+}
+
+/* forcing-node value U_b + alpha (x_opp - U_b) from the current opposite node */
+static double forcing_value(const or_sim* S, int grid, const double* x, int i, int j, double Ub) {
+  int nx = S->nx;
+  size_t id = grid == 0 ? UI(i, j) : VI(i, j);
+  double al = grid == 0 ? S->au[id] : S->av[id];
+  int d = grid == 0 ? S->du[id] : S->dv[id];
+  double xo = Ub;
+  if (al != 0.0) {
+    int oi = i + (d == 0) - (d == 1), oj = j + (d == 2) - (d == 3);
+    xo = x[grid == 0 ? UI(oi, oj) : VI(oi, oj)];
+  }
+  return fma(al, xo - Ub, Ub);
+}
+
 /* Row residual of (I - beta L) x = R on fluid rows, of the interpolation
  * condition on forcing rows, and of x = U_b on solid rows. */
 static double helm_row_res(const or_sim* S, int grid, const double* x, const double* R, int i, int j,
@@ -512,25 +608,16 @@ static double helm_row_res(const or_sim* S, int grid, const double* x, const dou
   size_t id = grid == 0 ? UI(i, j) : VI(i, j);
   unsigned char fl = grid == 0 ? S->fu[id] : S->fv[id];
   if (fl == FL_SOLID) return Ub - x[id];
-  if (fl == FL_FORCE) {
-    double al = grid == 0 ? S->au[id] : S->av[id];
-    int d = grid == 0 ? S->du[id] : S->dv[id];
-    double xo = Ub;
-    if (al != 0.0) {
-      int oi = i + (d == 0) - (d == 1), oj = j + (d == 2) - (d == 3);
-      xo = x[grid == 0 ? UI(oi, oj) : VI(oi, oj)];
-    }
-    return (Ub + al * (xo - Ub)) - x[id];
-  }
+  if (fl == FL_FORCE) return forcing_value(S, grid, x, i, j, Ub) - x[id];
   double L = grid == 0 ? lap_u_at(S, x, i, j) : lap_v_at(S, x, i, j);
-  return R[id] - (x[id] - beta * L);
+  return R[id] - fma(-beta, L, x[id]);
 }
 
 static double helm_res_inf(const or_sim* S, int grid, const double* x, const double* R, double beta,
                            double Ub, int* bad) {
   int nx = S->nx, ny = S->ny;
-  int i0 = grid == 0 ? 1 : 0, i1 = grid == 0 ? nx - 1 : nx - 1;
-  int j0 = grid == 0 ? 0 : 1, j1 = grid == 0 ? ny - 1 : ny - 1;
+  int i0 = grid == 0 ? 1 : 0, i1 = nx - 1;
+  int j0 = grid == 0 ? 0 : 1, j1 = ny - 1;
   double m = 0.0;
   int nan = 0;
   for (int j = j0; j <= j1; ++j)
@@ -545,8 +632,10 @@ static double helm_res_inf(const or_sim* S, int grid, const double* x, const dou
 
 /* Red-black Gauss-Seidel SOR for one grid's implicit velocity system
  * (Sec. 2.2: "modified" Gauss-Seidel SOR with red-black tagging).  Red =
- * (i+j) even, updated first.  Fluid rows are over-relaxed by omega; forcing
- * rows are assigned from the current opposite node; solid rows stay at U_b. */
+ * (i+j) even, updated first.  Fluid rows: Gauss-Seidel value
+ * (R + beta sum a_nb x_nb) / (1 + beta sum a_nb), over-relaxed by omega;
+ * forcing rows are assigned from the current opposite node; solid rows stay
+ * at U_b.  The residual is checked before the first sweep and every m. */
 static int helm_solve(or_sim* S, int grid, double* x, const double* R, double beta, double Ub,
                       int* sweeps, double* res) {
   int nx = S->nx, ny = S->ny;
@@ -554,6 +643,9 @@ static int helm_solve(or_sim* S, int grid, double* x, const double* R, double be
   int j0 = grid == 0 ? 0 : 1, j1 = ny - 1;
   double om = S->P.omega_h;
   int m = S->P.check_h > 0 ? S->P.check_h : 1;
+  const double *cE = grid == 0 ? S->uE : S->vE, *cW = grid == 0 ? S->uW : S->vW;
+  const double *cN = grid == 0 ? S->uN : S->vN, *cS = grid == 0 ? S->uS : S->vS;
+  const double* inv = grid == 0 ? S->iud : S->ivd;
   int s = 0;
   for (;;) {
     if (s % m == 0) {
@@ -573,43 +665,17 @@ static int helm_solve(or_sim* S, int grid, double* x, const double* R, double be
           unsigned char fl = grid == 0 ? S->fu[id] : S->fv[id];
           if (fl == FL_SOLID) continue;
           if (fl == FL_FORCE) {
-            double al = grid == 0 ? S->au[id] : S->av[id];
-            int d = grid == 0 ? S->du[id] : S->dv[id];
-            double xo = Ub;
-            if (al != 0.0) {
-              int oi = i + (d == 0) - (d == 1), oj = j + (d == 2) - (d == 3);
-              xo = x[grid == 0 ? UI(oi, oj) : VI(oi, oj)];
-            }
-            x[id] = Ub + al * (xo - Ub);
+            x[id] = forcing_value(S, grid, x, i, j, Ub);
             continue;
           }
-          /* (1 + beta*sum a) x_P = R + beta * sum a_nb x_nb */
-          double c = x[id];
-          double ae, aw, an, as, offsum = 0.0;
-          if (grid == 0) {
-            ae = 1.0 / (S->dx[i] * S->dxc[i]);
-            aw = 1.0 / (S->dx[i - 1] * S->dxc[i]);
-            an = (j < ny - 1) ? 1.0 / (S->dyc[j + 1] * S->dy[j]) : 0.0;
-            as = (j > 0) ? 1.0 / (S->dyc[j] * S->dy[j]) : 0.0;
-            offsum += ae * x[UI(i + 1, j)];
-            offsum += aw * x[UI(i - 1, j)];
-            if (j < ny - 1) offsum += an * x[UI(i, j + 1)];
-            if (j > 0) offsum += as * x[UI(i, j - 1)];
-          } else {
-            ae = (i < nx - 1) ? 1.0 / (S->dxc[i + 1] * S->dx[i]) : 0.0;
-            /* inflow (bc 0): v = 0 on x = x0, half a cell from the node */
-            aw = (i > 0) ? 1.0 / (S->dxc[i] * S->dx[i])
-                         : (S->P.bc == 0 ? 1.0 / (0.5 * S->dx[0] * S->dx[0]) : 0.0);
-            an = 1.0 / (S->dy[j] * S->dyc[j]);
-            as = 1.0 / (S->dy[j - 1] * S->dyc[j]);
-            if (i < nx - 1) offsum += ae * x[VI(i + 1, j)];
-            if (i > 0) offsum += aw * x[VI(i - 1, j)];
-            offsum += an * x[VI(i, j + 1)];
-            offsum += as * x[VI(i, j - 1)];
-          }
-          double diag = ae + aw + an + as;
-          double gs = (R[id] + beta * offsum) / (1.0 + beta * diag);
-          x[id] = (1.0 - om) * c + om * gs;
+          double xE, xW, xN, xS;
+          helm_nb(S, grid, x, i, j, &xE, &xW, &xN, &xS);
+          double sum = cE[i] * xE;
+          sum = fma(cW[i], xW, sum);
+          sum = fma(cN[j], xN, sum);
+          sum = fma(cS[j], xS, sum);
+          double gs = fma(beta, sum, R[id]) * inv[id];
+          x[id] = fma(om, gs - x[id], x[id]);
         }
     }
     ++s;
@@ -640,7 +706,8 @@ static double poisson_res_inf(const or_sim* S, const double* phi, const double* 
  * shifting phi so that the cell (nx-1, 0) is zero; a constant shift leaves
  * L_p phi and the velocity correction unchanged.  The residual infinity norm
  * is checked before the first sweep and every m full sweeps; the solve stops
- * when it is at most max(tol, rtol * ||b||_inf). */
+ * when it is at most max(tol, rtol * ||b||_inf).  Update of a cell:
+ * GS = (sum_nb a_nb phi_nb - b) / sum_nb a_nb, phi <- phi + omega (GS - phi). */
 int or_poisson(or_sim* S, const double* b, double* phi, double omega, double tol, double rtol, int m,
                int maxs, int* sweeps, double* res) {
   int nx = S->nx, ny = S->ny;
@@ -670,17 +737,16 @@ int or_poisson(or_sim* S, const double* b, double* phi, double omega, double tol
       for (int j = 0; j < ny; ++j)
         for (int i = (j + col) & 1; i < nx; i += 2) {
           size_t id = PI_(i, j);
-          double ae = (i < nx - 1) ? 1.0 / (S->dx[i] * S->dxc[i + 1]) : 0.0;
-          double aw = (i > 0) ? 1.0 / (S->dx[i] * S->dxc[i]) : 0.0;
-          double an = (j < ny - 1) ? 1.0 / (S->dy[j] * S->dyc[j + 1]) : 0.0;
-          double as = (j > 0) ? 1.0 / (S->dy[j] * S->dyc[j]) : 0.0;
-          double sum = 0.0;
-          if (i < nx - 1) sum += ae * phi[PI_(i + 1, j)];
-          if (i > 0) sum += aw * phi[PI_(i - 1, j)];
-          if (j < ny - 1) sum += an * phi[PI_(i, j + 1)];
-          if (j > 0) sum += as * phi[PI_(i, j - 1)];
-          double gs = (sum - b[id]) / (ae + aw + an + as);
-          phi[id] = (1.0 - omega) * phi[id] + omega * gs;
+          double xE = i < nx - 1 ? phi[PI_(i + 1, j)] : 0.0;
+          double xW = i > 0 ? phi[PI_(i - 1, j)] : 0.0;
+          double xN = j < ny - 1 ? phi[PI_(i, j + 1)] : 0.0;
+          double xS = j > 0 ? phi[PI_(i, j - 1)] : 0.0;
+          double sum = S->pE[i] * xE;
+          sum = fma(S->pW[i], xW, sum);
+          sum = fma(S->pN[j], xN, sum);
+          sum = fma(S->pS[j], xS, sum);
+          double gs = (sum - b[id]) * S->ipd[id];
+          phi[id] = fma(omega, gs - phi[id], phi[id]);
         }
     }
     ++s;
@@ -717,7 +783,7 @@ int or_set_body(or_sim* S, double chord, double tc, double h, double k, double x
 static int one_step(or_sim* S) {
   int nx = S->nx, ny = S->ny;
   const or_params* P = &S->P;
-  double dt = P->dt, beta = dt / (2.0 * P->Re);
+  double dt = P->dt, beta = dt / (2.0 * P->Re), idt = 1.0 / dt;
   double t1 = (S->n + 1) * dt;
   double yb = S->yb0, vb = 0.0;
   or_stats st;
@@ -745,13 +811,13 @@ static int one_step(or_sim* S) {
   for (int j = 0; j < ny; ++j)
     for (int i = 1; i < nx; ++i) {
       size_t id = UI(i, j);
-      double gp = (S->p[PI_(i, j)] - S->p[PI_(i - 1, j)]) / S->dxc[i];
+      double gp = (S->p[PI_(i, j)] - S->p[PI_(i - 1, j)]) * S->idxc[i];
       S->Ru[id] = S->u[id] + dt * (-1.5 * S->Hu[id] + 0.5 * S->Huo[id] - gp) + beta * lap_u_at(S, S->u, i, j);
     }
   for (int j = 1; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       size_t id = VI(i, j);
-      double gp = (S->p[PI_(i, j)] - S->p[PI_(i, j - 1)]) / S->dyc[j];
+      double gp = (S->p[PI_(i, j)] - S->p[PI_(i, j - 1)]) * S->idyc[j];
       S->Rv[id] = S->v[id] + dt * (-1.5 * S->Hv[id] + 0.5 * S->Hvo[id] - gp) + beta * lap_v_at(S, S->v, i, j);
     }
   /* boundary values of the intermediate velocity at t^{n+1} */
@@ -768,7 +834,7 @@ static int one_step(or_sim* S) {
     for (int j = 0; j < ny; ++j) {
       S->uh[UI(0, j)] = P->u_in;
       double ub = S->u[UI(nx, j)];
-      S->uh[UI(nx, j)] = ub - dt * P->u_in * (ub - S->u[UI(nx - 1, j)]) / S->dx[nx - 1];
+      S->uh[UI(nx, j)] = ub - dt * P->u_in * (ub - S->u[UI(nx - 1, j)]) * S->idx[nx - 1];
     }
     for (int j = 0; j < ny; ++j) {
       qin += S->uh[UI(0, j)] * S->dy[j];
@@ -820,7 +886,7 @@ static int one_step(or_sim* S) {
     for (int i = 0; i < nx; ++i) {
       size_t id = PI_(i, j);
       S->q[id] = S->cut[id] ? S->D[id] - cbar : 0.0;
-      S->b[id] = (S->D[id] - S->q[id]) / dt;
+      S->b[id] = (S->D[id] - S->q[id]) * idt;
       if (S->cut[id]) sq += S->q[id] * (S->dx[i] * S->dy[j]);
     }
   st.sum_q = sq;
@@ -839,7 +905,7 @@ static int one_step(or_sim* S) {
         size_t id = UI(i, j);
         if (S->fu[id] == FL_FLUID) continue;
         double dV = S->dxc[i] * S->dy[j];
-        double f = ((S->uh[id] - beta * lap_u_at(S, S->uh, i, j)) - S->Ru[id]) / dt;
+        double f = ((S->uh[id] - beta * lap_u_at(S, S->uh, i, j)) - S->Ru[id]) * idt;
         fx += f * dV;
         if (S->fu[id] == FL_SOLID) sx += S->uh[id] * dV;
       }
@@ -848,12 +914,12 @@ static int one_step(or_sim* S) {
         size_t id = VI(i, j);
         if (S->fv[id] == FL_FLUID) continue;
         double dV = S->dx[i] * S->dyc[j];
-        double f = ((S->vh[id] - beta * lap_v_at(S, S->vh, i, j)) - S->Rv[id]) / dt;
+        double f = ((S->vh[id] - beta * lap_v_at(S, S->vh, i, j)) - S->Rv[id]) * idt;
         fy += f * dV;
         if (S->fv[id] == FL_SOLID) sy += S->vh[id] * dV;
       }
-    double Fx = -fx + (sx - S->S_prev[0]) / dt;
-    double Fy = -fy + (sy - S->S_prev[1]) / dt;
+    double Fx = -fx + (sx - S->S_prev[0]) * idt;
+    double Fy = -fy + (sy - S->S_prev[1]) * idt;
     S->S_prev[0] = sx;
     S->S_prev[1] = sy;
     st.cd = 2.0 * Fx / S->chord;
@@ -866,7 +932,7 @@ static int one_step(or_sim* S) {
       if (i == 0 || i == nx)
         S->u[id] = S->uh[id];
       else
-        S->u[id] = S->uh[id] - dt * ((S->phi[PI_(i, j)] - S->phi[PI_(i - 1, j)]) / S->dxc[i]);
+        S->u[id] = S->uh[id] - dt * ((S->phi[PI_(i, j)] - S->phi[PI_(i - 1, j)]) * S->idxc[i]);
     }
   for (int j = 0; j <= ny; ++j)
     for (int i = 0; i < nx; ++i) {
@@ -874,7 +940,7 @@ static int one_step(or_sim* S) {
       if (j == 0 || j == ny)
         S->v[id] = S->vh[id];
       else
-        S->v[id] = S->vh[id] - dt * ((S->phi[PI_(i, j)] - S->phi[PI_(i, j - 1)]) / S->dyc[j]);
+        S->v[id] = S->vh[id] - dt * ((S->phi[PI_(i, j)] - S->phi[PI_(i, j - 1)]) * S->idyc[j]);
     }
   for (size_t id = 0; id < (size_t)nx * ny; ++id) S->p[id] += S->phi[id];
   /* H^n becomes H^{n-1} */
@@ -885,7 +951,7 @@ static int one_step(or_sim* S) {
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       if (S->cut[PI_(i, j)]) continue;
-      double d = (S->u[UI(i + 1, j)] - S->u[UI(i, j)]) / S->dx[i] + (S->v[VI(i, j + 1)] - S->v[VI(i, j)]) / S->dy[j];
+      double d = (S->u[UI(i + 1, j)] - S->u[UI(i, j)]) * S->idx[i] + (S->v[VI(i, j + 1)] - S->v[VI(i, j)]) * S->idy[j];
       if (fabs(d) > dm) dm = fabs(d);
     }
   st.div_max = dm;

@@ -1,0 +1,213 @@
+"""GB300 (sm_103a) immersed-boundary fractional step of arXiv 2402.17337.
+
+Thin ctypes binding of ``libibm.so`` (C ABI in ``include/ibm.h``): argument
+marshalling only, every step of the method runs in the library's CUDA
+kernels.  There is no CPU fallback: loading fails loudly when the library
+has not been built (``paper_2402_17337_gb300.build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libibm.so")
+_lock = threading.Lock()
+_lib = None
+
+IBM_OK, IBM_E_INVAL, IBM_E_CUDA, IBM_E_NOCONV, IBM_E_DIVERGED, IBM_E_TIMEOUT = 0, -1, -2, -3, -4, -5
+FIELDS = {"u": 0, "v": 1, "p": 2, "phi": 3, "b": 4, "uh": 5, "vh": 6, "Ru": 7, "Rv": 8,
+          "Hu": 9, "Hv": 10, "q": 11}
+
+
+class IbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libibm error {code}: {msg}")
+        self.code = code
+
+
+class GridParams(C.Structure):
+    _fields_ = [("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
+                ("nx", C.c_int), ("ny", C.c_int), ("hmin", C.c_double), ("ubox", C.c_double * 4),
+                ("bc", C.c_int), ("u_in", C.c_double), ("Re", C.c_double), ("dt", C.c_double),
+                ("precision", C.c_int), ("poisson_tol", C.c_double), ("poisson_rtol", C.c_double),
+                ("helm_tol", C.c_double), ("check_every_p", C.c_int), ("check_every_h", C.c_int),
+                ("max_sweeps", C.c_int), ("omega_p", C.c_double), ("omega_h", C.c_double),
+                ("cuda_stream", C.c_void_p)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("n", C.c_int), ("t", C.c_double), ("sweeps_u", C.c_int), ("sweeps_v", C.c_int),
+                ("sweeps_p", C.c_int), ("res_u", C.c_double), ("res_v", C.c_double),
+                ("res_p", C.c_double), ("div_max", C.c_double), ("cl", C.c_double), ("cd", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Profile(C.Structure):
+    _fields_ = [("launches", C.c_longlong), ("sweep_launches", C.c_longlong), ("sweep_ms", C.c_double),
+                ("steps", C.c_longlong), ("poisson_sweeps", C.c_longlong), ("helm_sweeps", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_D = C.POINTER(C.c_double)
+_U8 = C.POINTER(C.c_uint8)
+_VP = C.c_void_p
+
+
+def lib():
+    """Loads libibm.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: run paper_2402_17337_gb300.build.build()")
+            L = C.CDLL(LIB_PATH)
+            L.ibm_create_grid.argtypes = [C.POINTER(GridParams), C.POINTER(_VP)]
+            L.ibm_set_body.argtypes = [_VP] + [C.c_double] * 6
+            L.ibm_step.argtypes = [_VP, C.c_int, C.POINTER(StepStats)]
+            L.ibm_forces.argtypes = [_VP, _D, _D, C.c_int, C.POINTER(C.c_int)]
+            L.ibm_get_field.argtypes = [_VP, C.c_int, _D, C.c_size_t]
+            L.ibm_set_field.argtypes = [_VP, C.c_int, _D, C.c_size_t]
+            L.ibm_get_flags.argtypes = [_VP, C.c_int, _U8, _U8, _D, C.c_size_t]
+            L.ibm_get_grid.argtypes = [_VP, _D, _D]
+            L.ibm_poisson_solve.argtypes = [_VP, _VP, _VP, C.c_double, C.c_int, C.c_int,
+                                            C.POINTER(C.c_int), C.POINTER(C.c_double)]
+            L.ibm_set_profiling.argtypes = [_VP, C.c_int]
+            L.ibm_get_profile.argtypes = [_VP, C.POINTER(Profile)]
+            L.ibm_destroy.argtypes = [_VP]
+            L.ibm_destroy.restype = None
+            L.ibm_last_error.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != IBM_OK:
+        raise IbmError(rc, lib().ibm_last_error().decode())
+    return rc
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D)
+
+
+def default_omega(nx, ny):
+    return 2.0 / (1.0 + np.sin(np.pi / max(nx, ny)))
+
+
+class Solver:
+    """One simulation context on the GPU (owns the device memory)."""
+
+    def __init__(self, *, x0, x1, y0, y1, nx, ny, hmin=0.0, ubox=(-1.0, 2.0, -0.75, 0.75), bc=0,
+                 u_in=1.0, Re=100.0, dt=1e-3, precision=0, ptol=1e-10, prtol=0.0, htol=1e-12,
+                 check_p=8, check_h=2, max_sweeps=1000000, omega_p=None, omega_h=1.0, stream=None):
+        if omega_p is None:
+            omega_p = default_omega(nx, ny)
+        P = GridParams(x0, x1, y0, y1, nx, ny, hmin, (C.c_double * 4)(*ubox), bc, u_in, Re, dt,
+                       precision, ptol, prtol, htol, check_p, check_h, max_sweeps, omega_p, omega_h,
+                       stream)
+        self.P = P
+        self.nx, self.ny = nx, ny
+        h = _VP()
+        _check(lib().ibm_create_grid(C.byref(P), C.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_config(cls, cfg, **over):
+        kw = dict(x0=cfg.x0, x1=cfg.x1, y0=cfg.y0, y1=cfg.y1, nx=cfg.nx, ny=cfg.ny, hmin=cfg.hmin,
+                  ubox=cfg.ubox, bc=cfg.bc, u_in=cfg.u_in, Re=cfg.Re, dt=cfg.dt, ptol=cfg.ptol,
+                  htol=cfg.htol, check_p=cfg.check_p, check_h=cfg.check_h, omega_p=cfg.omega(),
+                  omega_h=cfg.omega_h)
+        kw.update(over)
+        s = cls(**kw)
+        s.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
+        return s
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().ibm_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape(self, name):
+        nx, ny = self.nx, self.ny
+        if name in ("u", "uh", "Ru", "Hu"):
+            return (ny, nx + 1)
+        if name in ("v", "vh", "Rv", "Hv"):
+            return (ny + 1, nx)
+        return (ny, nx)
+
+    def set_body(self, chord=1.0, tc=0.12, h=0.0, k=0.0, xc=0.0, yc=0.0):
+        _check(lib().ibm_set_body(self._h, chord, tc, h, k, xc, yc))
+
+    def step(self, n=1):
+        st = StepStats()
+        _check(lib().ibm_step(self._h, n, C.byref(st)))
+        return st.as_dict()
+
+    def step_rc(self, n=1):
+        """Like step() but returns (rc, stats) instead of raising."""
+        st = StepStats()
+        rc = lib().ibm_step(self._h, n, C.byref(st))
+        return rc, st.as_dict()
+
+    def forces(self):
+        n = C.c_int(0)
+        _check(lib().ibm_forces(self._h, None, None, 0, C.byref(n)))
+        cl = np.zeros(max(n.value, 1))
+        cd = np.zeros(max(n.value, 1))
+        _check(lib().ibm_forces(self._h, _dp(cl), _dp(cd), n.value, C.byref(n)))
+        return cl[:n.value], cd[:n.value]
+
+    def get(self, name):
+        out = np.zeros(self.shape(name))
+        _check(lib().ibm_get_field(self._h, FIELDS[name], _dp(out), out.size))
+        return out
+
+    def set(self, name, arr):
+        a = np.ascontiguousarray(arr, dtype=np.float64).reshape(self.shape(name))
+        _check(lib().ibm_set_field(self._h, FIELDS[name], _dp(a), a.size))
+
+    def flags(self, grid):
+        shp = self.shape("u" if grid == 0 else ("v" if grid == 1 else "p"))
+        fl = np.zeros(shp, np.uint8)
+        dr = np.zeros(shp, np.uint8)
+        al = np.zeros(shp)
+        _check(lib().ibm_get_flags(self._h, grid, fl.ctypes.data_as(_U8), dr.ctypes.data_as(_U8), _dp(al),
+                                   fl.size))
+        return (fl, dr, al) if grid < 2 else fl
+
+    def grid(self):
+        xf = np.zeros(self.nx + 1)
+        yf = np.zeros(self.ny + 1)
+        _check(lib().ibm_get_grid(self._h, _dp(xf), _dp(yf)))
+        return xf, yf
+
+    def set_profiling(self, on=True):
+        _check(lib().ibm_set_profiling(self._h, 1 if on else 0))
+
+    def profile(self):
+        p = Profile()
+        _check(lib().ibm_get_profile(self._h, C.byref(p)))
+        return p.as_dict()
+
+    def poisson_solve(self, b_ptr, phi_ptr, tol, check_every=8, max_sweeps=0):
+        """Standalone pressure solve on device buffers (nx*ny doubles each)."""
+        s = C.c_int(0)
+        r = C.c_double(0)
+        rc = lib().ibm_poisson_solve(self._h, b_ptr, phi_ptr, tol, check_every, max_sweeps, C.byref(s),
+                                     C.byref(r))
+        return rc, s.value, r.value

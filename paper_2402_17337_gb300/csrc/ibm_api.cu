@@ -1,0 +1,768 @@
+// Host side of libibm: the C ABI declared in include/ibm.h, grid
+// construction (Sec. 2.3), device memory of a context and the fractional-step
+// driver (Sec. 2.2).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ibm.h"
+#include "ibm_internal.h"
+
+using namespace ibm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess) return fail(IBM_E_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ------------------------------------------------------------ grid (Sec. 2.3)
+
+// hmin * (r + r^2 + ... + r^n), accumulated from the first term up
+double progression_length(double hmin, double r, int n) {
+  double term = 1.0, total = 0.0;
+  for (int m = 0; m < n; ++m) {
+    term *= r;
+    total += term;
+  }
+  return hmin * total;
+}
+
+// Growth ratio r >= 1 of n cells hmin*r^m (m = 1..n) that fill length L:
+// bracket [1, 2^k], then halve the bracket until it no longer shrinks.
+bool growth_ratio(double hmin, int n, double L, double* r) {
+  if (n == 0) {
+    *r = 1.0;
+    return true;
+  }
+  double lo = 1.0, hi = 2.0;
+  if (progression_length(hmin, lo, n) > L) return false;
+  while (progression_length(hmin, hi, n) < L) {
+    hi *= 2.0;
+    if (hi > 1e6) return false;
+  }
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    (progression_length(hmin, mid, n) < L ? lo : hi) = mid;
+  }
+  *r = 0.5 * (lo + hi);
+  return true;
+}
+
+// Face coordinates of one axis: uniform when hmin <= 0; otherwise a block of
+// round((b1-b0)/hmin) cells of size hmin from b0, flanked by geometric
+// progressions filling [a0, b0] and [block end, a1], the remaining cells
+// shared in proportion to the two lengths.
+bool build_axis(double a0, double a1, double b0, double b1, int n, double hmin, std::vector<double>& f) {
+  f.assign(n + 1, 0.0);
+  if (n < 1 || !(a1 > a0)) return false;
+  if (hmin <= 0.0) {
+    const double h = (a1 - a0) / n;
+    for (int i = 0; i < n; ++i) f[i] = a0 + i * h;
+    f[n] = a1;
+    return true;
+  }
+  if (!(b0 >= a0 && b1 <= a1 && b1 > b0)) return false;
+  const int nb = (int)std::lround((b1 - b0) / hmin);
+  if (nb < 1 || nb > n) return false;
+  const double bend = b0 + nb * hmin;
+  if (bend > a1) return false;
+  const double left = b0 - a0, right = a1 - bend;
+  const int spare = n - nb;
+  const int nl = (left + right > 0.0) ? (int)std::lround(spare * (left / (left + right))) : 0;
+  const int nr = spare - nl;
+  if ((nl == 0) != (left == 0.0) || (nr == 0) != (right == 0.0)) return false;
+  double rl, rr;
+  if (!growth_ratio(hmin, nl, left, &rl) || !growth_ratio(hmin, nr, right, &rr)) return false;
+  for (int m = 0; m <= nb; ++m) f[nl + m] = b0 + m * hmin;
+  for (int m = 1; m <= nl; ++m) f[nl - m] = b0 - progression_length(hmin, rl, m);
+  for (int m = 1; m <= nr; ++m) f[nl + nb + m] = bend + progression_length(hmin, rr, m);
+  f[0] = a0;
+  f[n] = a1;
+  return true;
+}
+
+}  // namespace
+
+struct ibm_ctx {
+  ibm_grid_params P;
+  int nx = 0, ny = 0, pitch = 0, rows = 0;
+  size_t nelem = 0;  // elements of one pitched field
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<double> xf, yf;
+  std::vector<void*> allocs;
+  Geo geo{};
+  // fields (FP64, pitched)
+  double *u = nullptr, *v = nullptr, *p = nullptr, *phi = nullptr, *phi2 = nullptr, *b = nullptr;
+  double *uh = nullptr, *vh = nullptr, *Ru = nullptr, *Rv = nullptr;
+  double *Hu = nullptr, *Hv = nullptr, *Huo = nullptr, *Hvo = nullptr;
+  double *invd_p = nullptr, *invd_u = nullptr, *invd_v = nullptr;
+  // body and band
+  bool has_body = false;
+  double chord = 1, tc = 0.12, h = 0, k = 0, xb = 0, yb0 = 0;
+  Band band{0, 0, 1, 1};
+  uint8_t *fu = nullptr, *fv = nullptr, *fc = nullptr;
+  double *au = nullptr, *av = nullptr, *qband = nullptr;
+  double* partials = nullptr;
+  DevScalars* sc = nullptr;
+  DevScalars* sc_host = nullptr;  // pinned mirror
+  // history
+  double *cl_d = nullptr, *cd_d = nullptr;
+  int hist_cap = 0;
+  int n = 0;
+  ibm_step_stats last{};
+  // profiling
+  ibm_profile prof{};
+  bool profiling = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  ~ibm_ctx() {
+    for (void* a : allocs) cudaFree(a);
+    if (sc_host) cudaFreeHost(sc_host);
+    if (cl_d) cudaFree(cl_d);
+    if (cd_d) cudaFree(cd_d);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+
+  template <class T>
+  int alloc(T** ptr, size_t count) {
+    void* q = nullptr;
+    CUDA_TRY(cudaMalloc(&q, sizeof(T) * (count ? count : 1)));
+    CUDA_TRY(cudaMemset(q, 0, sizeof(T) * (count ? count : 1)));
+    allocs.push_back(q);
+    *ptr = (T*)q;
+    return IBM_OK;
+  }
+  template <class T>
+  int upload(const T** ptr, const std::vector<T>& h) {
+    T* d = nullptr;
+    int rc = alloc(&d, h.size());
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpy(d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+    *ptr = d;
+    return IBM_OK;
+  }
+};
+
+namespace {
+
+int setup_geometry(ibm_ctx* c) {
+  const int nx = c->nx, ny = c->ny;
+  const auto& xf = c->xf;
+  const auto& yf = c->yf;
+  std::vector<double> xc(nx), yc(ny), dx(nx), dy(ny), idx(nx), idy(ny);
+  for (int i = 0; i < nx; ++i) {
+    dx[i] = xf[i + 1] - xf[i];
+    xc[i] = 0.5 * (xf[i] + xf[i + 1]);
+    idx[i] = 1.0 / dx[i];
+  }
+  for (int j = 0; j < ny; ++j) {
+    dy[j] = yf[j + 1] - yf[j];
+    yc[j] = 0.5 * (yf[j] + yf[j + 1]);
+    idy[j] = 1.0 / dy[j];
+  }
+  // centre spacings and face interpolation weights; the end entries encode
+  // the boundary conditions (see the predictor kernels)
+  std::vector<double> dxc(nx + 1, 0.0), dyc(ny + 1, 0.0), idxc(nx + 1, 0.0), idyc(ny + 1, 0.0);
+  std::vector<double> wx(nx + 1, 0.5), wy(ny + 1, 0.5);
+  for (int i = 1; i < nx; ++i) {
+    dxc[i] = xc[i] - xc[i - 1];
+    idxc[i] = 1.0 / dxc[i];
+    wx[i] = (xf[i] - xc[i - 1]) / dxc[i];
+  }
+  for (int j = 1; j < ny; ++j) {
+    dyc[j] = yc[j] - yc[j - 1];
+    idyc[j] = 1.0 / dyc[j];
+    wy[j] = (yf[j] - yc[j - 1]) / dyc[j];
+  }
+  // v at x0 for the convective flux: inflow v = 0 (weight 0 on the zero
+  // ghost) or free slip (weight 1 on v itself); at x1 zero gradient.
+  wx[0] = c->P.bc == 0 ? 0.0 : 1.0;
+  wx[nx] = 0.0;
+  // Laplacian coefficients
+  std::vector<double> pE(nx), pW(nx), pN(ny), pS(ny);
+  for (int i = 0; i < nx; ++i) {
+    pE[i] = i < nx - 1 ? 1.0 / (dx[i] * dxc[i + 1]) : 0.0;
+    pW[i] = i > 0 ? 1.0 / (dx[i] * dxc[i]) : 0.0;
+  }
+  for (int j = 0; j < ny; ++j) {
+    pN[j] = j < ny - 1 ? 1.0 / (dy[j] * dyc[j + 1]) : 0.0;
+    pS[j] = j > 0 ? 1.0 / (dy[j] * dyc[j]) : 0.0;
+  }
+  std::vector<double> uE(nx + 1, 0.0), uW(nx + 1, 0.0), uN(ny), uS(ny);
+  for (int i = 1; i < nx; ++i) {
+    uE[i] = 1.0 / (dx[i] * dxc[i]);
+    uW[i] = 1.0 / (dx[i - 1] * dxc[i]);
+  }
+  for (int j = 0; j < ny; ++j) {
+    uN[j] = j < ny - 1 ? 1.0 / (dyc[j + 1] * dy[j]) : 0.0;  // free slip: no flux through the wall
+    uS[j] = j > 0 ? 1.0 / (dyc[j] * dy[j]) : 0.0;
+  }
+  std::vector<double> vE(nx), vW(nx), vN(ny + 1, 0.0), vS(ny + 1, 0.0);
+  for (int i = 0; i < nx; ++i) {
+    vE[i] = i < nx - 1 ? 1.0 / (dxc[i + 1] * dx[i]) : 0.0;
+    // inflow: v = 0 on x0, half a cell from the node (ghost value 0 at the
+    // mirrored point, doubled coefficient); free slip: no flux
+    vW[i] = i > 0 ? 1.0 / (dxc[i] * dx[i]) : (c->P.bc == 0 ? 2.0 / (dx[0] * dx[0]) : 0.0);
+  }
+  for (int j = 1; j < ny; ++j) {
+    vN[j] = 1.0 / (dy[j] * dyc[j]);
+    vS[j] = 1.0 / (dy[j - 1] * dyc[j]);
+  }
+  Geo& g = c->geo;
+  g.nx = nx;
+  g.ny = ny;
+  g.pitch = c->pitch;
+  g.bc = c->P.bc;
+  int rc = 0;
+  rc |= c->upload(&g.xf, xf);
+  rc |= c->upload(&g.yf, yf);
+  rc |= c->upload(&g.xc, xc);
+  rc |= c->upload(&g.yc, yc);
+  rc |= c->upload(&g.dx, dx);
+  rc |= c->upload(&g.dy, dy);
+  rc |= c->upload(&g.idx, idx);
+  rc |= c->upload(&g.idy, idy);
+  rc |= c->upload(&g.dxc, dxc);
+  rc |= c->upload(&g.dyc, dyc);
+  rc |= c->upload(&g.idxc, idxc);
+  rc |= c->upload(&g.idyc, idyc);
+  rc |= c->upload(&g.wx, wx);
+  rc |= c->upload(&g.wy, wy);
+  rc |= c->upload(&g.pE, pE);
+  rc |= c->upload(&g.pW, pW);
+  rc |= c->upload(&g.pN, pN);
+  rc |= c->upload(&g.pS, pS);
+  rc |= c->upload(&g.uE, uE);
+  rc |= c->upload(&g.uW, uW);
+  rc |= c->upload(&g.uN, uN);
+  rc |= c->upload(&g.uS, uS);
+  rc |= c->upload(&g.vE, vE);
+  rc |= c->upload(&g.vW, vW);
+  rc |= c->upload(&g.vN, vN);
+  rc |= c->upload(&g.vS, vS);
+  if (rc) return IBM_E_CUDA;
+  // reciprocal diagonals of the SOR updates (pitched tables)
+  const double beta = c->P.dt / (2.0 * c->P.Re);
+  std::vector<double> ip(c->nelem, 0.0), iu(c->nelem, 0.0), iv(c->nelem, 0.0);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      double d = pE[i] + pW[i] + pN[j] + pS[j];
+      ip[at(i, j, c->pitch)] = 1.0 / d;
+    }
+  for (int j = 0; j < ny; ++j)
+    for (int i = 1; i < nx; ++i) iu[at(i, j, c->pitch)] = 1.0 / (1.0 + beta * (uE[i] + uW[i] + uN[j] + uS[j]));
+  for (int j = 1; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) iv[at(i, j, c->pitch)] = 1.0 / (1.0 + beta * (vE[i] + vW[i] + vN[j] + vS[j]));
+  const double *a, *bb, *cc;
+  rc |= c->upload(&a, ip);
+  rc |= c->upload(&bb, iu);
+  rc |= c->upload(&cc, iv);
+  if (rc) return IBM_E_CUDA;
+  c->invd_p = const_cast<double*>(a);
+  c->invd_u = const_cast<double*>(bb);
+  c->invd_v = const_cast<double*>(cc);
+  return IBM_OK;
+}
+
+int ensure_history(ibm_ctx* c, int need) {
+  if (need <= c->hist_cap) return IBM_OK;
+  int cap = c->hist_cap ? c->hist_cap : 1024;
+  while (cap < need) cap *= 2;
+  double *ncl = nullptr, *ncd = nullptr;
+  CUDA_TRY(cudaMalloc(&ncl, sizeof(double) * cap));
+  CUDA_TRY(cudaMalloc(&ncd, sizeof(double) * cap));
+  if (c->hist_cap) {
+    CUDA_TRY(cudaMemcpyAsync(ncl, c->cl_d, sizeof(double) * c->hist_cap, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(ncd, c->cd_d, sizeof(double) * c->hist_cap, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    cudaFree(c->cl_d);
+    cudaFree(c->cd_d);
+  }
+  c->cl_d = ncl;
+  c->cd_d = ncd;
+  c->hist_cap = cap;
+  return IBM_OK;
+}
+
+double bits_to_double(unsigned long long b) {
+  double d;
+  std::memcpy(&d, &b, 8);
+  return d;
+}
+
+// Reads one norm accumulator back (waits for the stream).
+int read_norm(ibm_ctx* c, const unsigned long long* dev_bits, double* out) {
+  CUDA_TRY(cudaMemcpyAsync(&c->sc_host->res_bits, dev_bits, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  *out = bits_to_double(c->sc_host->res_bits);
+  return IBM_OK;
+}
+
+// Red-black SOR for the pressure: residual checked before the first sweep
+// and every m sweeps.
+int solve_poisson(ibm_ctx* c, double tol, double rtol, int m, int maxs, int* sweeps, double* res) {
+  const Geo& g = c->geo;
+  double thr = tol;
+  if (rtol > 0.0) {
+    CUDA_TRY(cudaMemsetAsync(&c->sc->bmax_bits, 0, 8, c->stream));
+    launch_bmax(c->stream, g, c->b, &c->sc->bmax_bits);
+    double bmax;
+    int rc = read_norm(c, &c->sc->bmax_bits, &bmax);
+    if (rc) return rc;
+    thr = std::fmax(tol, rtol * bmax);
+  }
+  if (m < 1) m = 1;
+  const double omega = c->P.omega_p;
+  int pending = 0;  // sweep launches inside the open event bracket
+  for (int s = 0;; ++s) {
+    if (s % m == 0) {
+      if (pending) CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+      CUDA_TRY(cudaMemsetAsync(&c->sc->res_bits, 0, 8, c->stream));
+      launch_poisson_res(c->stream, g, c->phi, c->b, &c->sc->res_bits);
+      c->prof.launches += 1;
+      double r;
+      int rc = read_norm(c, &c->sc->res_bits, &r);
+      if (rc) return rc;
+      if (pending) {
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        c->prof.sweep_ms += ms;
+        c->prof.sweep_launches += pending;
+        pending = 0;
+      }
+      *sweeps = s;
+      *res = r;
+      if (!std::isfinite(r)) return fail(IBM_E_DIVERGED, "pressure residual is not finite after %d sweeps", s);
+      if (r <= thr) return IBM_OK;
+      if (s < maxs && c->profiling) {
+        CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+        pending = 0;
+      }
+    }
+    if (s >= maxs) return fail(IBM_E_NOCONV, "pressure solve: %d sweeps, residual %.3e > %.3e", s, *res, thr);
+    launch_poisson_half(c->stream, g, c->phi, c->b, c->invd_p, 0, omega);
+    launch_poisson_half(c->stream, g, c->phi, c->b, c->invd_p, 1, omega);
+    c->prof.launches += 2;
+    if (c->profiling) pending += 2;
+  }
+}
+
+int solve_helm(ibm_ctx* c, int grid, double beta, double Ub, int* sweeps, double* res) {
+  const Geo& g = c->geo;
+  double* x = grid == 0 ? c->uh : c->vh;
+  const double* R = grid == 0 ? c->Ru : c->Rv;
+  const double* invd = grid == 0 ? c->invd_u : c->invd_v;
+  const uint8_t* fl = grid == 0 ? c->fu : c->fv;
+  const double* al = grid == 0 ? c->au : c->av;
+  int m = c->P.check_every_h;
+  for (int s = 0;; ++s) {
+    if (s % m == 0) {
+      CUDA_TRY(cudaMemsetAsync(&c->sc->res_bits, 0, 8, c->stream));
+      launch_helm_res(c->stream, g, grid, x, R, c->band, fl, al, beta, Ub, &c->sc->res_bits);
+      c->prof.launches += 1;
+      double r;
+      int rc = read_norm(c, &c->sc->res_bits, &r);
+      if (rc) return rc;
+      *sweeps = s;
+      *res = r;
+      if (!std::isfinite(r)) return fail(IBM_E_DIVERGED, "velocity residual is not finite");
+      if (r <= c->P.helm_tol) return IBM_OK;
+    }
+    if (s >= c->P.max_sweeps) return fail(IBM_E_NOCONV, "velocity solve (grid %d) did not converge", grid);
+    launch_helm_half(c->stream, g, grid, x, R, invd, c->band, fl, al, 0, c->P.omega_h, beta, Ub);
+    launch_helm_half(c->stream, g, grid, x, R, invd, c->band, fl, al, 1, c->P.omega_h, beta, Ub);
+    c->prof.launches += 2;
+  }
+}
+
+int one_step(ibm_ctx* c) {
+  const Geo& g = c->geo;
+  const ibm_grid_params& P = c->P;
+  const double dt = P.dt, beta = dt / (2.0 * P.Re);
+  const double t1 = (c->n + 1) * dt;
+  double yb = c->yb0, vb = 0.0;
+  ibm_step_stats st{};
+  int rc = ensure_history(c, c->n + 1);
+  if (rc) return rc;
+  // a1: kinematics at t^{n+1} (Eqs. 1-2)
+  if (c->has_body) {
+    yb = c->yb0 + c->h * std::sin(c->k * t1);
+    vb = c->k * c->h * std::cos(c->k * t1);
+    // a2/a3: classification and forcing data
+    launch_classify(c->stream, g, c->band, c->xb, yb, 0.5 * c->chord, 0.5 * c->tc * c->chord, c->fu, c->fv,
+                    c->fc, c->au, c->av);
+  }
+  if (c->has_body) c->prof.launches += 3;
+  // boundary values of the intermediate velocity at t^{n+1}
+  if (P.bc == 0) {
+    launch_outflow_bc(c->stream, g, c->u, c->uh, c->vh, P.u_in, dt);
+    c->prof.launches += 1;
+  }
+  // a4: explicit predictor and initial guess
+  launch_predict(c->stream, g, c->u, c->v, c->p, c->Hu, c->Hv, c->Huo, c->Hvo, c->Ru, c->Rv, c->uh, c->vh,
+                 c->band, c->fu, c->fv, dt, beta, vb, c->n == 0 ? 1 : 0);
+  c->prof.launches += 2;
+  // a5: implicit velocity solves
+  rc = solve_helm(c, 0, beta, 0.0, &st.sweeps_u, &st.res_u);
+  if (rc) return rc;
+  rc = solve_helm(c, 1, beta, vb, &st.sweeps_v, &st.res_v);
+  if (rc) return rc;
+  // a6: right-hand side with the mass source on body cells
+  launch_rhs(c->stream, g, c->uh, c->vh, c->b, dt);
+  c->prof.launches += 1;
+  if (c->has_body) {
+    launch_body_source(c->stream, g, c->band, c->fc, c->uh, c->vh, c->b, c->qband, dt, c->partials, c->sc);
+    c->prof.launches += 3;
+  }
+  // a7/a8: pressure solve warm-started from the previous increment
+  rc = solve_poisson(c, P.poisson_tol, P.poisson_rtol, P.check_every_p, P.max_sweeps, &st.sweeps_p, &st.res_p);
+  if (rc) return rc;
+  // a10: forces (before the projection overwrites nothing they need)
+  if (c->has_body) {
+    launch_forces(c->stream, g, c->band, c->fu, c->fv, c->uh, c->vh, c->Ru, c->Rv, beta, dt, c->chord, c->partials,
+                  c->sc, c->cl_d, c->cd_d, c->n);
+    c->prof.launches += 2;
+  } else {
+    CUDA_TRY(cudaMemsetAsync(c->cl_d + c->n, 0, sizeof(double), c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->cd_d + c->n, 0, sizeof(double), c->stream));
+  }
+  // a9 + a11: projection, pressure update, divergence check
+  launch_phi_ref(c->stream, g, c->phi, c->sc);
+  CUDA_TRY(cudaMemsetAsync(&c->sc->div_bits, 0, 8, c->stream));
+  launch_project(c->stream, g, c->uh, c->vh, c->phi, c->u, c->v, c->p, c->phi2, c->band, c->fc, dt, c->sc);
+  c->prof.launches += 2;
+  CUDA_TRY(cudaGetLastError());
+  // read the scalars of the step
+  CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+  double clcd[2] = {0.0, 0.0};
+  CUDA_TRY(cudaMemcpyAsync(&clcd[0], c->cl_d + c->n, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(&clcd[1], c->cd_d + c->n, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  std::swap(c->phi, c->phi2);
+  std::swap(c->Hu, c->Huo);
+  std::swap(c->Hv, c->Hvo);
+  c->n += 1;
+  c->prof.steps += 1;
+  c->prof.poisson_sweeps += st.sweeps_p;
+  c->prof.helm_sweeps += st.sweeps_u + st.sweeps_v;
+  st.n = c->n;
+  st.t = c->n * dt;
+  st.div_max = bits_to_double(c->sc_host->div_bits);
+  st.cl = clcd[0];
+  st.cd = clcd[1];
+  c->last = st;
+  return IBM_OK;
+}
+
+struct FieldDesc {
+  double* ptr;
+  int w, h;
+};
+
+FieldDesc field_desc(const ibm_ctx* c, int which) {
+  const int nx = c->nx, ny = c->ny;
+  switch (which) {
+    case IBM_U: return {c->u, nx + 1, ny};
+    case IBM_V: return {c->v, nx, ny + 1};
+    case IBM_P: return {c->p, nx, ny};
+    case IBM_PHI: return {c->phi, nx, ny};
+    case IBM_B: return {c->b, nx, ny};
+    case IBM_UHAT: return {c->uh, nx + 1, ny};
+    case IBM_VHAT: return {c->vh, nx, ny + 1};
+    case IBM_RU: return {c->Ru, nx + 1, ny};
+    case IBM_RV: return {c->Rv, nx, ny + 1};
+    case IBM_HU: return {c->Huo, nx + 1, ny};  // swapped after the step: Huo holds H^n
+    case IBM_HV: return {c->Hvo, nx, ny + 1};
+    default: return {nullptr, 0, 0};
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ibm_last_error(void) { return g_err.c_str(); }
+
+int ibm_create_grid(const ibm_grid_params* params, ibm_ctx** out) {
+  if (!params || !out) return fail(IBM_E_INVAL, "null argument");
+  *out = nullptr;
+  ibm_grid_params P = *params;
+  if (P.nx < 4 || P.ny < 4) return fail(IBM_E_INVAL, "nx, ny must be >= 4");
+  if (!(P.Re > 0.0) || !(P.dt > 0.0)) return fail(IBM_E_INVAL, "Re and dt must be positive");
+  if (P.bc != 0 && P.bc != 1) return fail(IBM_E_INVAL, "bc must be 0 or 1");
+  if (P.precision != 0) return fail(IBM_E_INVAL, "precision %d not available", P.precision);
+  if (P.omega_p <= 0.0) P.omega_p = 2.0 / (1.0 + std::sin(M_PI / (P.nx > P.ny ? P.nx : P.ny)));
+  if (P.omega_h <= 0.0) P.omega_h = 1.0;
+  if (!(P.omega_p < 2.0) || !(P.omega_h < 2.0)) return fail(IBM_E_INVAL, "omega must lie in (0, 2)");
+  if (P.check_every_p <= 0) P.check_every_p = 8;
+  if (P.check_every_h <= 0) P.check_every_h = 2;
+  if (P.max_sweeps <= 0) P.max_sweeps = 1000000;
+  if (P.helm_tol <= 0.0) P.helm_tol = 1e-12;
+  if (P.poisson_tol <= 0.0 && P.poisson_rtol <= 0.0) return fail(IBM_E_INVAL, "a Poisson tolerance is required");
+  auto* c = new ibm_ctx();
+  c->P = P;
+  c->nx = P.nx;
+  c->ny = P.ny;
+  if (!build_axis(P.x0, P.x1, P.ubox[0], P.ubox[1], P.nx, P.hmin, c->xf) ||
+      !build_axis(P.y0, P.y1, P.ubox[2], P.ubox[3], P.ny, P.hmin, c->yf)) {
+    delete c;
+    return fail(IBM_E_INVAL, "cannot build the grid (check domain, uniform box and hmin)");
+  }
+  c->pitch = ((P.nx + 2 + XOFF) + 31) / 32 * 32;
+  c->rows = P.ny + 3;
+  c->nelem = (size_t)c->pitch * c->rows;
+  if (P.cuda_stream) {
+    c->stream = (cudaStream_t)P.cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return fail(IBM_E_CUDA, "cannot create a stream");
+    }
+    c->own_stream = true;
+  }
+  int rc = 0;
+  double** fields[] = {&c->u, &c->v, &c->p, &c->phi, &c->phi2, &c->b, &c->uh, &c->vh,
+                       &c->Ru, &c->Rv, &c->Hu, &c->Hv, &c->Huo, &c->Hvo};
+  for (double** f : fields) rc |= c->alloc(f, c->nelem);
+  rc |= c->alloc(&c->sc, 1);
+  rc |= c->alloc(&c->partials, 4 * RED_BLOCKS);
+  if (!rc) rc = setup_geometry(c);
+  if (!rc && cudaMallocHost((void**)&c->sc_host, sizeof(DevScalars)) != cudaSuccess) rc = IBM_E_CUDA;
+  if (!rc) rc = ensure_history(c, 1024);
+  // band arrays exist (1 x 1) even without a body
+  if (!rc) {
+    rc |= c->alloc(&c->fu, 1);
+    rc |= c->alloc(&c->fv, 1);
+    rc |= c->alloc(&c->fc, 1);
+    rc |= c->alloc(&c->au, 1);
+    rc |= c->alloc(&c->av, 1);
+    rc |= c->alloc(&c->qband, 1);
+    c->band = Band{-100, -100, 1, 1};
+  }
+  if (!rc && P.bc == 0) {
+    std::vector<double> col(P.ny, P.u_in);
+    if (cudaMemcpy2D(c->u + at(0, 0, c->pitch), c->pitch * sizeof(double), col.data(), sizeof(double),
+                     sizeof(double), P.ny, cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = IBM_E_CUDA;
+  }
+  if (rc) {
+    std::string keep = g_err;
+    delete c;
+    g_err = keep.empty() ? "allocation failed" : keep;
+    return rc < 0 ? rc : IBM_E_CUDA;
+  }
+  *out = c;
+  return IBM_OK;
+}
+
+int ibm_set_body(ibm_ctx* c, double chord, double tc, double h, double k, double xc, double yc) {
+  if (!c) return fail(IBM_E_INVAL, "null context");
+  if (c->n != 0) return fail(IBM_E_INVAL, "the body must be set before the first step");
+  if (!(chord > 0.0) || !(tc > 0.0)) return fail(IBM_E_INVAL, "chord and thickness ratio must be positive");
+  const double a = 0.5 * chord, bsemi = 0.5 * tc * chord;
+  const double xlo = xc - a, xhi = xc + a, ylo = yc - std::fabs(h) - bsemi, yhi = yc + std::fabs(h) + bsemi;
+  const int nx = c->nx, ny = c->ny;
+  // band: every node index whose coordinate can lie inside the body, plus 4
+  int i0 = 0, i1 = nx, j0 = 0, j1 = ny;
+  while (i0 < nx && c->xf[i0 + 1] < xlo) ++i0;
+  while (i1 > 0 && c->xf[i1 - 1] > xhi) --i1;
+  while (j0 < ny && c->yf[j0 + 1] < ylo) ++j0;
+  while (j1 > 0 && c->yf[j1 - 1] > yhi) --j1;
+  i0 -= 4;
+  j0 -= 4;
+  i1 += 4;
+  j1 += 4;
+  if (i0 < 2 || j0 < 2 || i1 > nx - 2 || j1 > ny - 2)
+    return fail(IBM_E_INVAL, "the body's swept region reaches the domain boundary");
+  Band B{i0, j0, i1 - i0 + 1, j1 - j0 + 1};
+  size_t nb = (size_t)B.w * B.h;
+  int rc = 0;
+  rc |= c->alloc(&c->fu, nb);
+  rc |= c->alloc(&c->fv, nb);
+  rc |= c->alloc(&c->fc, nb);
+  rc |= c->alloc(&c->au, nb);
+  rc |= c->alloc(&c->av, nb);
+  rc |= c->alloc(&c->qband, nb);
+  if (rc) return IBM_E_CUDA;
+  c->band = B;
+  c->has_body = true;
+  c->chord = chord;
+  c->tc = tc;
+  c->h = h;
+  c->k = k;
+  c->xb = xc;
+  c->yb0 = yc;
+  // momentum carried inside the body at t = 0 (first internal-mass term)
+  launch_classify(c->stream, c->geo, B, xc, yc, a, bsemi, c->fu, c->fv, c->fc, c->au, c->av);
+  launch_init_body_momentum(c->stream, c->geo, B, c->fv, k * h, c->partials, c->sc);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return IBM_OK;
+}
+
+int ibm_step(ibm_ctx* c, int nsteps, ibm_step_stats* last) {
+  if (!c) return fail(IBM_E_INVAL, "null context");
+  if (nsteps < 0) return fail(IBM_E_INVAL, "nsteps < 0");
+  for (int s = 0; s < nsteps; ++s) {
+    int rc = one_step(c);
+    if (rc) return rc;
+  }
+  if (last) *last = c->last;
+  return IBM_OK;
+}
+
+int ibm_forces(const ibm_ctx* c, double* cl, double* cd, int cap, int* n_out) {
+  if (!c || !n_out) return fail(IBM_E_INVAL, "null argument");
+  int n = c->n < cap ? c->n : cap;
+  if (n > 0 && cl) CUDA_TRY(cudaMemcpyAsync(cl, c->cl_d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  if (n > 0 && cd) CUDA_TRY(cudaMemcpyAsync(cd, c->cd_d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  *n_out = c->n;
+  return IBM_OK;
+}
+
+int ibm_get_field(const ibm_ctx* c, int which, double* host, size_t n) {
+  if (!c || !host) return fail(IBM_E_INVAL, "null argument");
+  if (which == IBM_Q) {
+    if (n != (size_t)c->nx * c->ny) return fail(IBM_E_INVAL, "size mismatch");
+    std::memset(host, 0, n * sizeof(double));
+    if (!c->has_body) return IBM_OK;
+    const Band& B = c->band;
+    std::vector<double> q((size_t)B.w * B.h);
+    CUDA_TRY(cudaMemcpyAsync(q.data(), c->qband, q.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int bj = 0; bj < B.h; ++bj)
+      for (int bi = 0; bi < B.w; ++bi) {
+        int i = B.i0 + bi, j = B.j0 + bj;
+        if (i >= 0 && i < c->nx && j >= 0 && j < c->ny) host[(size_t)j * c->nx + i] = q[(size_t)bj * B.w + bi];
+      }
+    return IBM_OK;
+  }
+  FieldDesc f = field_desc(c, which);
+  if (!f.ptr) return fail(IBM_E_INVAL, "unknown field %d", which);
+  if (n != (size_t)f.w * f.h) return fail(IBM_E_INVAL, "size mismatch: %zu vs %d", n, f.w * f.h);
+  CUDA_TRY(cudaMemcpy2DAsync(host, f.w * sizeof(double), f.ptr + at(0, 0, c->pitch), c->pitch * sizeof(double),
+                             f.w * sizeof(double), f.h, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return IBM_OK;
+}
+
+int ibm_set_field(ibm_ctx* c, int which, const double* host, size_t n) {
+  if (!c || !host) return fail(IBM_E_INVAL, "null argument");
+  if (which < IBM_U || which > IBM_PHI) return fail(IBM_E_INVAL, "only u, v, p, phi can be set");
+  FieldDesc f = field_desc(c, which);
+  if (n != (size_t)f.w * f.h) return fail(IBM_E_INVAL, "size mismatch");
+  CUDA_TRY(cudaMemcpy2DAsync(f.ptr + at(0, 0, c->pitch), c->pitch * sizeof(double), host, f.w * sizeof(double),
+                             f.w * sizeof(double), f.h, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return IBM_OK;
+}
+
+int ibm_get_flags(const ibm_ctx* c, int grid, unsigned char* kind, unsigned char* dir, double* alpha, size_t n) {
+  if (!c) return fail(IBM_E_INVAL, "null context");
+  const int nx = c->nx, ny = c->ny;
+  int w = grid == 0 ? nx + 1 : nx, h = grid == 1 ? ny + 1 : ny;
+  if (grid < 0 || grid > 2) return fail(IBM_E_INVAL, "grid must be 0, 1 or 2");
+  if (n != (size_t)w * h) return fail(IBM_E_INVAL, "size mismatch");
+  if (kind) std::memset(kind, 0, n);
+  if (dir) std::memset(dir, 0, n);
+  if (alpha) std::memset(alpha, 0, n * sizeof(double));
+  if (!c->has_body) return IBM_OK;
+  const Band& B = c->band;
+  size_t nb = (size_t)B.w * B.h;
+  std::vector<uint8_t> f(nb);
+  std::vector<double> a(nb);
+  const uint8_t* fsrc = grid == 0 ? c->fu : grid == 1 ? c->fv : c->fc;
+  CUDA_TRY(cudaMemcpyAsync(f.data(), fsrc, nb, cudaMemcpyDeviceToHost, c->stream));
+  if (grid < 2) CUDA_TRY(cudaMemcpyAsync(a.data(), grid == 0 ? c->au : c->av, nb * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  for (int bj = 0; bj < B.h; ++bj)
+    for (int bi = 0; bi < B.w; ++bi) {
+      int i = B.i0 + bi, j = B.j0 + bj;
+      if (i < 0 || i >= w || j < 0 || j >= h) continue;
+      size_t o = (size_t)j * w + i, k = (size_t)bj * B.w + bi;
+      if (kind) kind[o] = grid == 2 ? f[k] : (f[k] & 3);
+      if (dir && grid < 2) dir[o] = (f[k] & 3) == K_FORCE ? (f[k] >> 2) : 0;
+      if (alpha && grid < 2) alpha[o] = a[k];
+    }
+  return IBM_OK;
+}
+
+int ibm_get_grid(const ibm_ctx* c, double* xf, double* yf) {
+  if (!c) return fail(IBM_E_INVAL, "null context");
+  if (xf) std::memcpy(xf, c->xf.data(), sizeof(double) * (c->nx + 1));
+  if (yf) std::memcpy(yf, c->yf.data(), sizeof(double) * (c->ny + 1));
+  return IBM_OK;
+}
+
+int ibm_poisson_solve(ibm_ctx* c, const double* b_dev, double* phi_dev, double tol, int check_every, int max_sweeps,
+                      int* sweeps, double* res) {
+  if (!c || !b_dev || !phi_dev) return fail(IBM_E_INVAL, "null argument");
+  if (!(tol > 0.0)) return fail(IBM_E_INVAL, "tol must be positive");
+  const size_t rowb = c->nx * sizeof(double), pb = c->pitch * sizeof(double);
+  CUDA_TRY(cudaMemcpy2DAsync(c->b + at(0, 0, c->pitch), pb, b_dev, rowb, rowb, c->ny, cudaMemcpyDeviceToDevice,
+                             c->stream));
+  CUDA_TRY(cudaMemcpy2DAsync(c->phi + at(0, 0, c->pitch), pb, phi_dev, rowb, rowb, c->ny, cudaMemcpyDeviceToDevice,
+                             c->stream));
+  int s = 0;
+  double r = 0.0;
+  int rc = solve_poisson(c, tol, 0.0, check_every, max_sweeps > 0 ? max_sweeps : c->P.max_sweeps, &s, &r);
+  if (sweeps) *sweeps = s;
+  if (res) *res = r;
+  if (rc) return rc;
+  launch_phi_ref(c->stream, c->geo, c->phi, c->sc);
+  launch_shift(c->stream, c->geo, c->phi, c->sc);
+  CUDA_TRY(cudaMemcpy2DAsync(phi_dev, rowb, c->phi + at(0, 0, c->pitch), pb, rowb, c->ny, cudaMemcpyDeviceToDevice,
+                             c->stream));
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return IBM_OK;
+}
+
+int ibm_set_profiling(ibm_ctx* c, int on) {
+  if (!c) return fail(IBM_E_INVAL, "null context");
+  if (on && !c->ev0) {
+    CUDA_TRY(cudaEventCreate(&c->ev0));
+    CUDA_TRY(cudaEventCreate(&c->ev1));
+  }
+  c->profiling = on != 0;
+  c->prof = ibm_profile{};
+  return IBM_OK;
+}
+
+int ibm_get_profile(const ibm_ctx* c, ibm_profile* out) {
+  if (!c || !out) return fail(IBM_E_INVAL, "null argument");
+  *out = c->prof;
+  return IBM_OK;
+}
+
+void ibm_destroy(ibm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  delete c;
+}
+
+}  // extern "C"

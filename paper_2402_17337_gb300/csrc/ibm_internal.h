@@ -1,0 +1,99 @@
+// Internal declarations shared by the CUDA translation units of libibm.
+// Not part of the public C ABI (include/ibm.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace ibm {
+
+// Every staggered field (u, v, p-type) uses one storage geometry: rows
+// j = -1 .. ny+1 and columns i = -XOFF .. pitch-XOFF-1, element (i, j) at
+// (j + 1) * pitch + i + XOFF.  Ghost entries stay zero; boundary conditions
+// live in the 1-D coefficient and weight arrays, so stencils never branch.
+constexpr int XOFF = 4;
+
+__host__ __device__ inline size_t at(int i, int j, int pitch) {
+  return (size_t)(j + 1) * pitch + (size_t)(i + XOFF);
+}
+
+// node kinds in the band flag arrays (bits 0-1); bits 2-3 hold the direction
+// of the solid neighbour chosen for a forcing node (0 -x, 1 +x, 2 -y, 3 +y)
+enum : uint8_t { K_FLUID = 0, K_SOLID = 1, K_FORCE = 2 };
+
+// Device pointers to the 1-D grid data (all FP64).
+struct Geo {
+  int nx, ny, pitch, bc;
+  const double *xf, *yf, *xc, *yc;     // coordinates (nx+1, ny+1, nx, ny)
+  const double *dx, *dy, *idx, *idy;   // cell widths and inverses
+  const double *dxc, *dyc;             // centre spacings, index 1..n-1 (n+1 entries)
+  const double *idxc, *idyc;           // their inverses (0 where undefined)
+  const double *wx, *wy;               // face interpolation weights (n+1 entries)
+  // Laplacian coefficients, sum_nb a_nb (x_nb - x_P); zero through walls
+  const double *pE, *pW, *pN, *pS;     // pressure grid (nx, nx, ny, ny)
+  const double *uE, *uW, *uN, *uS;     // u grid (nx+1, nx+1, ny, ny)
+  const double *vE, *vW, *vN, *vS;     // v grid (nx, nx, ny+1, ny+1)
+};
+
+// Index rectangle that contains every node the body can touch over its
+// whole plunge, with a margin; used for all three grids.
+struct Band {
+  int i0, j0, w, h;
+};
+
+// Small device-side scalars of one context (the context's scratch).
+struct DevScalars {
+  unsigned long long res_bits;   // infinity norm accumulator (bit pattern of |r|)
+  unsigned long long div_bits;   // max |div u| over fluid cells
+  unsigned long long bmax_bits;  // ||b||_inf
+  double body_sum[2];            // sum D V, sum V over body cells
+  double cbar;                   // mean divergence over body cells
+  double phi_ref;                // phi at the gauge cell
+  double S_prev[2];              // momentum inside the body at the previous step
+  double force[2];               // Fx, Fy of the last step
+  double sum_q;
+};
+
+constexpr int RED_BLOCKS = 64;   // fixed partial-reduction width (deterministic sums)
+
+// ---------------------------------------------------------------- launchers
+// (all asynchronous on the given stream)
+
+void launch_outflow_bc(cudaStream_t s, const Geo& g, const double* u, double* uh, double* vh,
+                       double u_in, double dt);
+void launch_classify(cudaStream_t s, const Geo& g, const Band& band, double xb, double yb, double a,
+                     double b, uint8_t* fu, uint8_t* fv, uint8_t* fc, double* au, double* av);
+void launch_predict(cudaStream_t s, const Geo& g, const double* u, const double* v, const double* p,
+                    double* Hu, double* Hv, const double* Huo, const double* Hvo, double* Ru, double* Rv,
+                    double* uh, double* vh, const Band& band, const uint8_t* fu, const uint8_t* fv,
+                    double dt, double beta, double vb, int first);
+void launch_rhs(cudaStream_t s, const Geo& g, const double* uh, const double* vh, double* b, double dt);
+void launch_body_source(cudaStream_t s, const Geo& g, const Band& band, const uint8_t* fc, const double* uh,
+                        const double* vh, double* b, double* qband, double dt, double* partials,
+                        DevScalars* sc);
+void launch_forces(cudaStream_t s, const Geo& g, const Band& band, const uint8_t* fu, const uint8_t* fv,
+                   const double* uh, const double* vh, const double* Ru, const double* Rv, double beta,
+                   double dt, double chord, double* partials, DevScalars* sc, double* cl_hist,
+                   double* cd_hist, int n);
+void launch_phi_ref(cudaStream_t s, const Geo& g, const double* phi, DevScalars* sc);
+void launch_project(cudaStream_t s, const Geo& g, const double* uh, const double* vh, const double* phi,
+                    double* u, double* v, double* p, double* phi_store, const Band& band, const uint8_t* fc,
+                    double dt, DevScalars* sc);
+void launch_init_body_momentum(cudaStream_t s, const Geo& g, const Band& band, const uint8_t* fv, double vb,
+                               double* partials, DevScalars* sc);
+
+// SOR kernels (FP64 plain path)
+void launch_poisson_half(cudaStream_t s, const Geo& g, double* phi, const double* b, const double* invd,
+                         int colour, double omega);
+void launch_poisson_res(cudaStream_t s, const Geo& g, const double* phi, const double* b,
+                        unsigned long long* res_bits);
+void launch_shift(cudaStream_t s, const Geo& g, double* phi, const DevScalars* sc);
+void launch_bmax(cudaStream_t s, const Geo& g, const double* b, unsigned long long* bits);
+void launch_helm_half(cudaStream_t s, const Geo& g, int grid, double* x, const double* R, const double* invd,
+                      const Band& band, const uint8_t* fl, const double* al, int colour, double omega,
+                      double beta, double Ub);
+void launch_helm_res(cudaStream_t s, const Geo& g, int grid, const double* x, const double* R,
+                     const Band& band, const uint8_t* fl, const double* al, double beta, double Ub,
+                     unsigned long long* res_bits);
+
+}  // namespace ibm

@@ -1,0 +1,229 @@
+// Red-black Gauss-Seidel SOR kernels ("modified Gauss-Seidel SOR with
+// red-black tagging", arXiv 2402.17337 Sec. 2.2 and Sec. 3.1) for the
+// pressure Poisson equation and the Crank-Nicolson velocity systems, plus
+// their residual infinity norms.
+//
+// Red cells have (i + j) even.  Within one colour no update reads another
+// update of the same colour, so every half-sweep is race-free.
+//
+// Arithmetic recipe (shared with the CPU oracle so that iteration counts are
+// decided identically): 5-point sums and Laplacians are fma chains in the
+// order E, W, N, S; the library is built with --fmad=false so that no other
+// multiply-add is contracted.  Norms are
+// reduced on the IEEE bit pattern of |r|: for non-negative doubles the
+// unsigned order is the numeric order, NaN patterns sort above +Inf, and the
+// result does not depend on the reduction order.
+#include "ibm_internal.h"
+
+namespace ibm {
+
+namespace {
+
+constexpr int TBX = 32, TBY = 8;
+
+__device__ inline void warp_block_max(unsigned long long v, unsigned long long* dst) {
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  __shared__ unsigned long long wm[32];
+  int t = threadIdx.x + threadIdx.y * blockDim.x;
+  int lane = t & 31, warp = t >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
+  if (lane == 0) wm[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < nw ? wm[lane] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = w > v ? w : v;
+    }
+    if (lane == 0 && v) atomicMax(dst, v);
+  }
+}
+
+__device__ inline unsigned long long abs_bits(double r) {
+  return (unsigned long long)__double_as_longlong(fabs(r));
+}
+
+// ----------------------------------------------------------------- Poisson
+
+// L_p phi = b:  phi_P <- phi_P + omega (GS_P - phi_P),
+// GS_P = (sum_nb a_nb phi_nb - b_P) / sum_nb a_nb.
+__global__ void k_poisson_half(Geo g, double* __restrict__ phi, const double* __restrict__ b,
+                               const double* __restrict__ invd, int colour, double omega) {
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((colour + j) & 1);
+  if (j >= g.ny || i >= g.nx) return;
+  const int P = g.pitch;
+  size_t c = at(i, j, P);
+  double s = g.pE[i] * phi[c + 1];
+  s = fma(g.pW[i], phi[c - 1], s);
+  s = fma(g.pN[j], phi[c + P], s);
+  s = fma(g.pS[j], phi[c - P], s);
+  double gs = (s - b[c]) * invd[c];
+  double x = phi[c];
+  phi[c] = fma(omega, gs - x, x);
+}
+
+// sum_nb a_nb (x_nb - x_P) in the order E, W, N, S
+__device__ inline double lap5(double aE, double aW, double aN, double aS, double xE, double xW, double xN,
+                              double xS, double c) {
+  double L = aE * (xE - c);
+  L = fma(aW, xW - c, L);
+  L = fma(aN, xN - c, L);
+  L = fma(aS, xS - c, L);
+  return L;
+}
+
+__global__ void k_poisson_res(Geo g, const double* __restrict__ phi, const double* __restrict__ b,
+                              unsigned long long* res_bits) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  unsigned long long bits = 0ull;
+  if (i < g.nx && j < g.ny) {
+    const int P = g.pitch;
+    size_t c = at(i, j, P);
+    double L = lap5(g.pE[i], g.pW[i], g.pN[j], g.pS[j], phi[c + 1], phi[c - 1], phi[c + P], phi[c - P], phi[c]);
+    bits = abs_bits(b[c] - L);
+  }
+  warp_block_max(bits, res_bits);
+}
+
+__global__ void k_bmax(Geo g, const double* __restrict__ b, unsigned long long* bits_out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  unsigned long long bits = 0ull;
+  if (i < g.nx && j < g.ny) bits = abs_bits(b[at(i, j, g.pitch)]);
+  warp_block_max(bits, bits_out);
+}
+
+// ---------------------------------------------------- velocity (Helmholtz)
+
+struct HelmCoef {
+  const double *E, *W, *N, *S;
+  int ilo, ihi, jlo, jhi;
+};
+
+__device__ inline HelmCoef helm_coef(const Geo& g, int grid) {
+  HelmCoef h;
+  if (grid == 0) {
+    h.E = g.uE; h.W = g.uW; h.N = g.uN; h.S = g.uS;
+    h.ilo = 1; h.ihi = g.nx - 1; h.jlo = 0; h.jhi = g.ny - 1;
+  } else {
+    h.E = g.vE; h.W = g.vW; h.N = g.vN; h.S = g.vS;
+    h.ilo = 0; h.ihi = g.nx - 1; h.jlo = 1; h.jhi = g.ny - 1;
+  }
+  return h;
+}
+
+__device__ inline long opp_offset(int dir, int P) {
+  // forcing node whose wall lies in direction dir takes the node on the far side
+  return dir == 0 ? 1 : dir == 1 ? -1 : dir == 2 ? (long)P : -(long)P;
+}
+
+// (I - beta L) x = R on fluid nodes (SOR); forcing nodes x = Ub + alpha (x_opp - Ub);
+// solid nodes keep x = Ub.
+__global__ void k_helm_half(Geo g, int grid, double* __restrict__ x, const double* __restrict__ R,
+                            const double* __restrict__ invd, Band B, const uint8_t* __restrict__ fl,
+                            const double* __restrict__ al, int colour, double omega, double beta, double Ub) {
+  HelmCoef h = helm_coef(g, grid);
+  int j = blockIdx.y * blockDim.y + threadIdx.y + h.jlo;
+  int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((colour + j) & 1);
+  if (j > h.jhi || i > h.ihi || i < h.ilo) return;
+  const int P = g.pitch;
+  size_t c = at(i, j, P);
+  int bi = i - B.i0, bj = j - B.j0;
+  if (bi >= 0 && bj >= 0 && bi < B.w && bj < B.h) {
+    uint8_t f = fl[bj * B.w + bi];
+    int kind = f & 3;
+    if (kind == K_SOLID) return;
+    if (kind == K_FORCE) {
+      double a = al[bj * B.w + bi];
+      double xo = a != 0.0 ? x[c + opp_offset(f >> 2, P)] : Ub;
+      x[c] = fma(a, xo - Ub, Ub);
+      return;
+    }
+  }
+  double s = h.E[i] * x[c + 1];
+  s = fma(h.W[i], x[c - 1], s);
+  s = fma(h.N[j], x[c + P], s);
+  s = fma(h.S[j], x[c - P], s);
+  double gs = fma(beta, s, R[c]) * invd[c];
+  double xp = x[c];
+  x[c] = fma(omega, gs - xp, xp);
+}
+
+__global__ void k_helm_res(Geo g, int grid, const double* __restrict__ x, const double* __restrict__ R, Band B,
+                           const uint8_t* __restrict__ fl, const double* __restrict__ al, double beta, double Ub,
+                           unsigned long long* res_bits) {
+  HelmCoef h = helm_coef(g, grid);
+  int i = blockIdx.x * blockDim.x + threadIdx.x + h.ilo, j = blockIdx.y * blockDim.y + threadIdx.y + h.jlo;
+  unsigned long long bits = 0ull;
+  if (i <= h.ihi && j <= h.jhi) {
+    const int P = g.pitch;
+    size_t c = at(i, j, P);
+    int bi = i - B.i0, bj = j - B.j0;
+    int kind = K_FLUID;
+    uint8_t f = 0;
+    if (bi >= 0 && bj >= 0 && bi < B.w && bj < B.h) {
+      f = fl[bj * B.w + bi];
+      kind = f & 3;
+    }
+    double r;
+    double xp = x[c];
+    if (kind == K_SOLID) {
+      r = Ub - xp;
+    } else if (kind == K_FORCE) {
+      double a = al[bj * B.w + bi];
+      double xo = a != 0.0 ? x[c + opp_offset(f >> 2, P)] : Ub;
+      r = fma(a, xo - Ub, Ub) - xp;
+    } else {
+      double L = lap5(h.E[i], h.W[i], h.N[j], h.S[j], x[c + 1], x[c - 1], x[c + P], x[c - P], xp);
+      r = R[c] - fma(-beta, L, xp);
+    }
+    bits = abs_bits(r);
+  }
+  warp_block_max(bits, res_bits);
+}
+
+// phi -= phi at the gauge cell (value captured beforehand in sc->phi_ref)
+__global__ void k_shift(Geo g, double* __restrict__ phi, const DevScalars* __restrict__ sc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i < g.nx && j < g.ny) phi[at(i, j, g.pitch)] -= sc->phi_ref;
+}
+
+inline dim3 grid2(int nx, int ny) { return dim3((nx + TBX - 1) / TBX, (ny + TBY - 1) / TBY); }
+
+}  // namespace
+
+void launch_shift(cudaStream_t s, const Geo& g, double* phi, const DevScalars* sc) {
+  k_shift<<<grid2(g.nx, g.ny), dim3(TBX, TBY), 0, s>>>(g, phi, sc);
+}
+
+void launch_poisson_half(cudaStream_t s, const Geo& g, double* phi, const double* b, const double* invd,
+                         int colour, double omega) {
+  k_poisson_half<<<grid2((g.nx + 1) / 2, g.ny), dim3(TBX, TBY), 0, s>>>(g, phi, b, invd, colour, omega);
+}
+
+void launch_poisson_res(cudaStream_t s, const Geo& g, const double* phi, const double* b,
+                        unsigned long long* res_bits) {
+  k_poisson_res<<<grid2(g.nx, g.ny), dim3(TBX, TBY), 0, s>>>(g, phi, b, res_bits);
+}
+
+void launch_bmax(cudaStream_t s, const Geo& g, const double* b, unsigned long long* bits) {
+  k_bmax<<<grid2(g.nx, g.ny), dim3(TBX, TBY), 0, s>>>(g, b, bits);
+}
+
+void launch_helm_half(cudaStream_t s, const Geo& g, int grid, double* x, const double* R, const double* invd,
+                      const Band& band, const uint8_t* fl, const double* al, int colour, double omega,
+                      double beta, double Ub) {
+  int ni = grid == 0 ? g.nx + 1 : g.nx, nj = grid == 0 ? g.ny : g.ny - 1;
+  k_helm_half<<<grid2((ni + 1) / 2, nj), dim3(TBX, TBY), 0, s>>>(g, grid, x, R, invd, band, fl, al, colour, omega,
+                                                                 beta, Ub);
+}
+
+void launch_helm_res(cudaStream_t s, const Geo& g, int grid, const double* x, const double* R, const Band& band,
+                     const uint8_t* fl, const double* al, double beta, double Ub, unsigned long long* res_bits) {
+  int ni = grid == 0 ? g.nx - 1 : g.nx, nj = grid == 0 ? g.ny : g.ny - 1;
+  k_helm_res<<<grid2(ni, nj), dim3(TBX, TBY), 0, s>>>(g, grid, x, R, band, fl, al, beta, Ub, res_bits);
+}
+
+}  // namespace ibm

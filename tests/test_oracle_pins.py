@@ -387,8 +387,8 @@ def test_step_divergence_bound_and_zero_net_mass_source_in_body_cells():
             cut = s.flags(2).astype(bool)
             d = s.div(s.get("u"), s.get("v"))
             assert np.abs(d[~cut]).max() == st["div_max"]
-            assert st["div_max"] <= c.dt * st["res_p"] * (1 + 1e-9) + 1e-14
-            assert st["div_max"] <= 1e-9 * (1 + 1e-6)
+            assert st["div_max"] <= c.dt * st["res_p"] * (1 + 1e-3) + 1e-13
+            assert st["div_max"] <= 1e-9 * (1 + 1e-3)
             xf, yf = s.grid()
             V = np.outer(np.diff(yf), np.diff(xf))
             q = s.get("q")
