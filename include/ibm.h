@@ -149,7 +149,8 @@ int ibm_get_grid(const ibm_ctx* ctx, double* xf, double* yf);
 
 /* Solves L_p phi = b (homogeneous Neumann) by red-black SOR on the
  * context's grid, as inside a step (Sec. 2.2), to
- * ||b - L_p phi||_inf <= tol checked every check_every sweeps, then shifts
+ * ||b - L_p phi||_inf <= tol checked every check_every sweeps (precision 1:
+ * FP32 sweeps inside FP64 defect correction, checked in FP64), then shifts
  * phi so that the cell (nx-1, 0) is zero.  b_dev, phi_dev: device pointers
  * to nx*ny doubles in the compact layout; phi_dev holds the initial guess
  * and receives the result.  Uses the context's work arrays, so it must not

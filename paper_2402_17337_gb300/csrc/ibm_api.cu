@@ -116,6 +116,10 @@ struct ibm_ctx {
   double *uh = nullptr, *vh = nullptr, *Ru = nullptr, *Rv = nullptr;
   double *Hu = nullptr, *Hv = nullptr, *Huo = nullptr, *Hvo = nullptr;
   double *invd_p = nullptr, *invd_u = nullptr, *invd_v = nullptr;
+  // mixed precision (FP32 correction, residual and reciprocal diagonal)
+  Geo32 geo32{};
+  float *e32 = nullptr, *r32 = nullptr, *invd32 = nullptr;
+  int m_inner = 32;  // inner sweeps between FP64 checks (adapted)
   // body and band
   bool has_body = false;
   double chord = 1, tc = 0.12, h = 0, k = 0, xb = 0, yb0 = 0;
@@ -283,6 +287,29 @@ int setup_geometry(ibm_ctx* c) {
   c->invd_p = const_cast<double*>(a);
   c->invd_u = const_cast<double*>(bb);
   c->invd_v = const_cast<double*>(cc);
+  if (c->P.precision == 1) {
+    auto f32 = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+    Geo32& g32 = c->geo32;
+    g32.nx = nx;
+    g32.ny = ny;
+    g32.pitch = c->pitch;
+    rc |= c->upload(&g32.pE, f32(pE));
+    rc |= c->upload(&g32.pW, f32(pW));
+    rc |= c->upload(&g32.pN, f32(pN));
+    rc |= c->upload(&g32.pS, f32(pS));
+    std::vector<float> ip32(c->nelem, 0.0f);
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        float d = (float)pE[i] + (float)pW[i] + (float)pN[j] + (float)pS[j];
+        ip32[at(i, j, c->pitch)] = 1.0f / d;
+      }
+    const float* d32;
+    rc |= c->upload(&d32, ip32);
+    rc |= c->alloc(&c->e32, c->nelem);
+    rc |= c->alloc(&c->r32, c->nelem);
+    if (rc) return IBM_E_CUDA;
+    c->invd32 = const_cast<float*>(d32);
+  }
   return IBM_OK;
 }
 
@@ -370,6 +397,63 @@ int solve_poisson(ibm_ctx* c, double tol, double rtol, int m, int maxs, int* swe
   }
 }
 
+// Defect correction: FP64 residual and update around FP32 red-black SOR
+// sweeps on the correction equation.  The number of inner sweeps between two
+// FP64 checks adapts to the observed convergence rate.
+int solve_poisson_mixed(ibm_ctx* c, double tol, int maxs, int* sweeps, double* res) {
+  const Geo& g = c->geo;
+  const int K2 = sor32_half_sweeps_per_launch() / 2;  // full sweeps per launch
+  double* cur = c->phi;
+  double* alt = c->phi2;
+  int s = 0, add = 0, inner = 0;
+  double prev = 0.0;
+  int pending = 0;
+  const float omega = (float)c->P.omega_p;
+  for (;;) {
+    if (pending) CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+    CUDA_TRY(cudaMemsetAsync(&c->sc->res_bits, 0, 8, c->stream));
+    launch_dc_residual(c->stream, g, cur, alt, c->e32, c->b, c->r32, add, &c->sc->res_bits);
+    c->prof.launches += 1;
+    if (add) std::swap(cur, alt);
+    double r;
+    int rc = read_norm(c, &c->sc->res_bits, &r);
+    if (rc) return rc;
+    if (pending) {
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+      c->prof.sweep_ms += ms;
+      c->prof.sweep_launches += pending;
+      pending = 0;
+    }
+    *sweeps = s;
+    *res = r;
+    c->phi = cur;
+    c->phi2 = alt;
+    if (!std::isfinite(r)) return fail(IBM_E_DIVERGED, "pressure residual is not finite after %d sweeps", s);
+    if (r <= tol) return IBM_OK;
+    if (s >= maxs) return fail(IBM_E_NOCONV, "pressure solve: %d sweeps, residual %.3e > %.3e", s, r, tol);
+    // inner sweeps until the next check: aim at ~70 % of the predicted
+    // remaining count, 16..1024 sweeps, whole launches
+    if (inner > 0 && prev > r && r > 0.0) {
+      double rate = std::log(r / prev) / inner;  // per sweep, < 0
+      double need = std::log(tol / r) / rate;
+      int m = (int)(0.7 * need);
+      c->m_inner = m < 16 ? 16 : (m > 1024 ? 1024 : m);
+    }
+    inner = (c->m_inner + K2 - 1) / K2 * K2;
+    if (s + inner > maxs) inner = ((maxs - s) + K2 - 1) / K2 * K2;
+    if (c->profiling) CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+    for (int l = 0; l < inner / K2; ++l) {
+      launch_sor32(c->stream, c->geo32, c->e32, c->r32, c->invd32, omega, l == 0 ? 1 : 0);
+      c->prof.launches += 1;
+      if (c->profiling) pending += 1;
+    }
+    prev = r;
+    s += inner;
+    add = 1;
+  }
+}
+
 int solve_helm(ibm_ctx* c, int grid, double beta, double Ub, int* sweeps, double* res) {
   const Geo& g = c->geo;
   double* x = grid == 0 ? c->uh : c->vh;
@@ -438,7 +522,20 @@ int one_step(ibm_ctx* c) {
     c->prof.launches += 3;
   }
   // a7/a8: pressure solve warm-started from the previous increment
-  rc = solve_poisson(c, P.poisson_tol, P.poisson_rtol, P.check_every_p, P.max_sweeps, &st.sweeps_p, &st.res_p);
+  if (P.precision == 1) {
+    double thr = P.poisson_tol;
+    if (P.poisson_rtol > 0.0) {
+      CUDA_TRY(cudaMemsetAsync(&c->sc->bmax_bits, 0, 8, c->stream));
+      launch_bmax(c->stream, g, c->b, &c->sc->bmax_bits);
+      double bmax;
+      rc = read_norm(c, &c->sc->bmax_bits, &bmax);
+      if (rc) return rc;
+      thr = std::fmax(thr, P.poisson_rtol * bmax);
+    }
+    rc = solve_poisson_mixed(c, thr, P.max_sweeps, &st.sweeps_p, &st.res_p);
+  } else {
+    rc = solve_poisson(c, P.poisson_tol, P.poisson_rtol, P.check_every_p, P.max_sweeps, &st.sweeps_p, &st.res_p);
+  }
   if (rc) return rc;
   // a10: forces (before the projection overwrites nothing they need)
   if (c->has_body) {
@@ -513,7 +610,7 @@ int ibm_create_grid(const ibm_grid_params* params, ibm_ctx** out) {
   if (P.nx < 4 || P.ny < 4) return fail(IBM_E_INVAL, "nx, ny must be >= 4");
   if (!(P.Re > 0.0) || !(P.dt > 0.0)) return fail(IBM_E_INVAL, "Re and dt must be positive");
   if (P.bc != 0 && P.bc != 1) return fail(IBM_E_INVAL, "bc must be 0 or 1");
-  if (P.precision != 0) return fail(IBM_E_INVAL, "precision %d not available", P.precision);
+  if (P.precision != 0 && P.precision != 1) return fail(IBM_E_INVAL, "precision must be 0 or 1");
   if (P.omega_p <= 0.0) P.omega_p = 2.0 / (1.0 + std::sin(M_PI / (P.nx > P.ny ? P.nx : P.ny)));
   if (P.omega_h <= 0.0) P.omega_h = 1.0;
   if (!(P.omega_p < 2.0) || !(P.omega_h < 2.0)) return fail(IBM_E_INVAL, "omega must lie in (0, 2)");
@@ -729,7 +826,9 @@ int ibm_poisson_solve(ibm_ctx* c, const double* b_dev, double* phi_dev, double t
                              c->stream));
   int s = 0;
   double r = 0.0;
-  int rc = solve_poisson(c, tol, 0.0, check_every, max_sweeps > 0 ? max_sweeps : c->P.max_sweeps, &s, &r);
+  const int maxs = max_sweeps > 0 ? max_sweeps : c->P.max_sweeps;
+  int rc = c->P.precision == 1 ? solve_poisson_mixed(c, tol, maxs, &s, &r)
+                               : solve_poisson(c, tol, 0.0, check_every, maxs, &s, &r);
   if (sweeps) *sweeps = s;
   if (res) *res = r;
   if (rc) return rc;
@@ -744,7 +843,7 @@ int ibm_poisson_solve(ibm_ctx* c, const double* b_dev, double* phi_dev, double t
 
 int ibm_set_profiling(ibm_ctx* c, int on) {
   if (!c) return fail(IBM_E_INVAL, "null context");
-  if (on && !c->ev0) {
+  if ((on || c->P.precision == 1) && !c->ev0) {
     CUDA_TRY(cudaEventCreate(&c->ev0));
     CUDA_TRY(cudaEventCreate(&c->ev1));
   }

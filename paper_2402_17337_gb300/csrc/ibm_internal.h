@@ -35,6 +35,12 @@ struct Geo {
   const double *vE, *vW, *vN, *vS;     // v grid (nx, nx, ny+1, ny+1)
 };
 
+// FP32 copies of the pressure coefficients (mixed-precision inner sweeps).
+struct Geo32 {
+  int nx, ny, pitch;
+  const float *pE, *pW, *pN, *pS;
+};
+
 // Index rectangle that contains every node the body can touch over its
 // whole plunge, with a margin; used for all three grids.
 struct Band {
@@ -95,5 +101,12 @@ void launch_helm_half(cudaStream_t s, const Geo& g, int grid, double* x, const d
 void launch_helm_res(cudaStream_t s, const Geo& g, int grid, const double* x, const double* R,
                      const Band& band, const uint8_t* fl, const double* al, double beta, double Ub,
                      unsigned long long* res_bits);
+
+// mixed precision: FP64 update + residual, FP32 temporally blocked sweeps
+int sor32_half_sweeps_per_launch();
+void launch_dc_residual(cudaStream_t s, const Geo& g, const double* phi_in, double* phi_out, const float* e,
+                        const double* b, float* r32, int add_e, unsigned long long* res_bits);
+void launch_sor32(cudaStream_t s, const Geo32& g, float* e, const float* r, const float* invd, float omega,
+                  int zero_init);
 
 }  // namespace ibm
