@@ -159,6 +159,42 @@ int ibm_get_grid(const ibm_ctx* ctx, double* xf, double* yf);
 int ibm_poisson_solve(ibm_ctx* ctx, const double* b_dev, double* phi_dev, double tol, int check_every,
                       int max_sweeps, int* sweeps, double* res);
 
+/* Pressure solve for callers that cannot allocate device memory.
+ *
+ * No counterpart in the paper: this is a packaging variant of
+ * ibm_poisson_solve for callers that cannot call cudaMalloc, such as an
+ * application whose device memory belongs to its own allocator or to a pool
+ * sized up front, a framework that forbids allocation on its hot path, or a
+ * real-time loop that cannot take the device-wide synchronisation an
+ * allocation may cause.  It needs no context: the caller passes the grid's
+ * face coordinates and its own buffers, and every scratch value (the 1-D
+ * coefficients and the residual-norm accumulator) lives in one fixed-size
+ * static device array of the library, which each GPU that loads the library
+ * holds (256 KB) until the process exits.
+ *
+ * Solves L_p phi = b on the grid with face coordinates xf (nx+1 host
+ * doubles) and yf (ny+1 host doubles), homogeneous Neumann, by red-black SOR
+ * with factor omega, checking ||b - L_p phi||_inf <= tol every check_every
+ * sweeps (<= 0: 8), at most max_sweeps sweeps (<= 0: 1e6), then shifts phi
+ * so that cell (nx-1, 0) is zero; the iterates equal those of
+ * ibm_poisson_solve on the same grid.  b_dev and phi_dev are device pointers
+ * to nx*ny doubles in the compact layout; phi_dev holds the initial guess
+ * and receives the result.  stream is a cudaStream_t (NULL: the default
+ * stream); the call returns after the stream has finished its work.
+ * *sweeps and *res (may be NULL) receive the sweep count and final residual.
+ *
+ * Limits and sharing: nx and ny must be at most 8192, larger sizes fail
+ * with IBM_E_INVAL and a message in ibm_last_error().  The first call on a
+ * device performs a one-time set-up: it looks up the device address of the
+ * scratch array (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture begins.  Every call on a device uses
+ * the same scratch array, which keeps the last call's contents; each call
+ * clears what it needs before use.  Calls whose GPU work overlaps (two host
+ * threads, or two streams of one device) race on the scratch: serialise them. */
+int ibm_poisson_solve_noalloc(int nx, int ny, const double* xf, const double* yf, const double* b_dev,
+                              double* phi_dev, double omega, double tol, int check_every, int max_sweeps,
+                              void* stream, int* sweeps, double* res);
+
 /* Counters of a context.  With profiling on, each run of pressure SOR
  * launches between two residual checks is bracketed by CUDA events on the
  * context's stream; sweep_ms is the summed device time of those runs and

@@ -599,6 +599,11 @@ FieldDesc field_desc(const ibm_ctx* c, int which) {
 
 }  // namespace
 
+namespace ibm {
+// records the message returned by ibm_last_error() on this thread
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace ibm
+
 extern "C" {
 
 const char* ibm_last_error(void) { return g_err.c_str(); }

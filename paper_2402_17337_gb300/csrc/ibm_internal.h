@@ -102,6 +102,9 @@ void launch_helm_res(cudaStream_t s, const Geo& g, int grid, const double* x, co
                      const Band& band, const uint8_t* fl, const double* al, double beta, double Ub,
                      unsigned long long* res_bits);
 
+// message for ibm_last_error() on the calling thread
+void set_last_error(const char* msg);
+
 // mixed precision: FP64 update + residual, FP32 temporally blocked sweeps
 int sor32_half_sweeps_per_launch();
 void launch_dc_residual(cudaStream_t s, const Geo& g, const double* phi_in, double* phi_out, const float* e,
