@@ -11,6 +11,9 @@ stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The value is the mixed path (FP32 sweeps inside FP64 defect correction);
+the plain FP64 path is timed on the same steps and reported beside it.
+
 --impl reference times the FP64 CPU oracle (the slow, plain restatement of
 the method) on the host cores with the same metric; under torchrun only rank
 0 runs it.  N > 1 runs independent replicas, one per GPU.
@@ -30,6 +33,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_FLOPS_PER_CLK_SM = 4.0   # 2 FP64 FMA per clock per SM on GB300 (sm_103)
+FP32_FLOPS_PER_CLK_SM = 256.0  # 128 FP32 FMA per clock per SM
+SOR32_HALF_SWEEPS = 8          # half-sweeps fused per FP32 tile launch
+SOR32_BYTES_PER_CELL_LAUNCH = 12  # read e, r; write e (FP32) once per launch
 SOR_FLOPS_PER_UPDATE = 12     # 4 products + 3 adds, minus b, times 1/d, relaxation (2)
 SOR_BYTES_PER_CELL_HALF = 16  # read phi (8, all cells), read b (4), write phi (4) per half-sweep
 
@@ -176,9 +182,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed",
+                    help="mixed: FP32 sweeps inside FP64 defect correction (the value); fp64: plain FP64")
+    ap.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true", help="no nvidia-smi sampling (for profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
@@ -207,12 +216,6 @@ def main():
     B.build()
 
     stream = torch.cuda.Stream()
-    precision = 0
-    s = ibm.Solver(**solver_kwargs(cfg, precision), stream=stream.cuda_stream)
-    s.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
-    s.set("u", cfg.initial_u(s.shape("u")))
-    for _ in range(args.warmup):
-        s.step(1)
 
     def barrier():
         torch.cuda.synchronize()
@@ -220,53 +223,83 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # --------------------------------------------------- device-timed window
-    start_state = {n: s.get(n) for n in ("u", "v", "p", "phi")} if rank == 0 else None
-    s.set_profiling(True)
-    prof0 = s.profile()
-    clocks = ClockSampler(local)
-    barrier()
-    clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    stats = []
-    for _ in range(args.steps):
-        stats.append(s.step(1))
-    e1.record(stream)
-    barrier()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    prof = s.profile()
-    ok_steps = sum(1 for st in stats if st["div_max"] < cfg.div_tol)
-    t_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda")
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        okt = torch.tensor([ok_steps], device="cuda")
-        dist.all_reduce(okt)
-        total_ok = int(okt.item())
-    else:
-        total_ok = ok_steps
-    value = cfg.cells * total_ok / (t_max / 1e3)
-    launches = prof["launches"] - prof0["launches"]
+        return float(t.item())
 
-    # roofline of the dominant kernel (FP64 red-black SOR half-sweep)
+    def sum_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t)
+        return float(t.item())
+
+    def timed_run(precision, sample_clocks):
+        """W untimed steps, then K steps timed with CUDA events on the solver's stream."""
+        s = ibm.Solver(**solver_kwargs(cfg, precision), stream=stream.cuda_stream)
+        s.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
+        s.set("u", cfg.initial_u(s.shape("u")))
+        for _ in range(args.warmup):
+            s.step(1)
+        state = {n: s.get(n) for n in ("u", "v", "p", "phi")} if rank == 0 else None
+        s.set_profiling(True)
+        prof0 = s.profile()
+        clocks = ClockSampler(local)
+        barrier()
+        if sample_clocks:
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = [s.step(1) for _ in range(args.steps)]
+        e1.record(stream)
+        barrier()
+        clk = clocks.stop() if sample_clocks else None
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        prof = s.profile()
+        ok = sum_over_ranks(sum(1 for st in stats if st["div_max"] < cfg.div_tol))
+        s.close()
+        return {"value": cfg.cells * ok / (ms / 1e3), "ms": ms, "stats": stats, "ok": int(ok), "clocks": clk,
+                "launches": prof["launches"] - prof0["launches"], "prof": prof, "state": state}
+
+    precision = 1 if args.precision == "mixed" else 0
+    main_run = timed_run(precision, not args.no_clocks)
+    value, t_max, stats, total_ok = main_run["value"], main_run["ms"], main_run["stats"], main_run["ok"]
+    prof, clk, launches, start_state = main_run["prof"], main_run["clocks"], main_run["launches"], main_run["state"]
+    fp64_run = timed_run(0, False) if (precision == 1 and not args.no_fp64_compare) else None
+
+    # roofline of the dominant kernel
     peaks, peak_src = load_peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     fp64_peak = n_sm * FP64_FLOPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    fp32_peak = n_sm * FP32_FLOPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
     roof = None
     if prof["sweep_launches"] > 0:
         t_launch = prof["sweep_ms"] / prof["sweep_launches"] / 1e3
-        flops = SOR_FLOPS_PER_UPDATE * cfg.cells / 2
-        achieved = flops / t_launch / 1e12
-        roof = {"bound": "alu", "kernel": "k_poisson_half (FP64 red-black SOR half-sweep)",
-                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                "traffic": None, "launch_us": t_launch * 1e6,
-                "hbm_gbs": SOR_BYTES_PER_CELL_HALF * cfg.cells / t_launch / 1e9,
-                "peak_note": f"FP64: {n_sm} SMs x 4 flop/clk x {sm_mhz:.0f} MHz; HBM peak "
-                             f"{peaks.get('hbm_gbs')} GB/s ({peak_src})"}
+        if precision == 0:
+            flops = SOR_FLOPS_PER_UPDATE * cfg.cells / 2
+            achieved = flops / t_launch / 1e12
+            roof = {"bound": "alu", "kernel": "k_poisson_half (FP64 red-black SOR half-sweep)",
+                    "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                    "traffic": None, "launch_us": t_launch * 1e6,
+                    "hbm_gbs": SOR_BYTES_PER_CELL_HALF * cfg.cells / t_launch / 1e9,
+                    "peak_note": f"FP64: {n_sm} SMs x 4 flop/clk x {sm_mhz:.0f} MHz (derived)"}
+        else:
+            nbytes = SOR32_BYTES_PER_CELL_LAUNCH * cfg.cells
+            achieved = nbytes / t_launch / 1e9
+            sweeps_per_launch = SOR32_HALF_SWEEPS / 2
+            roof = {"bound": "hbm", "kernel": f"k_sor32_tile (FP32 red-black SOR, {SOR32_HALF_SWEEPS} half-sweeps "
+                                              f"per launch)",
+                    "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": None, "launch_us": t_launch * 1e6,
+                    "fp32_tflops": SOR_FLOPS_PER_UPDATE * cfg.cells * sweeps_per_launch / t_launch / 1e12,
+                    "fp32_peak_tflops": fp32_peak,
+                    "peak_note": f"HBM {peaks['hbm_gbs']} GB/s ({peak_src}); algorithmic bytes: read e and r, "
+                                 f"write e once per launch ({SOR32_BYTES_PER_CELL_LAUNCH} B/cell); working set "
+                                 f"fits in L2"}
 
     # ------------------------------------------------------------- end to end
     # A second context runs the same warm-up and the same window of steps
@@ -320,13 +353,19 @@ def main():
 
     if rank == 0:
         sweeps = [st["sweeps_p"] for st in stats]
+        fp64 = None
+        if fp64_run:
+            fp64 = {"value": fp64_run["value"], "ms_per_step": fp64_run["ms"] / args.steps,
+                    "poisson_sweeps_per_step": statistics.mean(st["sweeps_p"] for st in fp64_run["stats"]),
+                    "speedup_of_value": value / fp64_run["value"]}
         line = {
             "metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 sweeps, f64 residual/update/norms" if precision == 1 else "f64",
             "data": "synthetic",
             "config": {"workload": cfg.name, "nx": cfg.nx, "ny": cfg.ny, "global_batch": world,
-                       "parallelism": f"replicas x{world}", "path": "fp64",
+                       "parallelism": f"replicas x{world}", "path": args.precision, "plain_fp64": fp64,
                        "steps_counted": total_ok, "poisson_sweeps_per_step": statistics.mean(sweeps),
                        "helm_sweeps_per_step": statistics.mean(st["sweeps_u"] + st["sweeps_v"] for st in stats),
                        "l2": "state 14 FP64 fields x 17 MB > L2; no flush",
@@ -338,7 +377,6 @@ def main():
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
-    s.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()

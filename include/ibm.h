@@ -153,7 +153,8 @@ int ibm_get_grid(const ibm_ctx* ctx, double* xf, double* yf);
  * FP32 sweeps inside FP64 defect correction, checked in FP64), then shifts
  * phi so that the cell (nx-1, 0) is zero.  b_dev, phi_dev: device pointers
  * to nx*ny doubles in the compact layout; phi_dev holds the initial guess
- * and receives the result.  Uses the context's work arrays, so it must not
+ * and receives the result (on IBM_E_NOCONV: the last iterate, unshifted).
+ * Uses the context's work arrays, so it must not
  * overlap a step of the same context.  *sweeps and *res (may be NULL)
  * receive the sweep count and the final residual norm. */
 int ibm_poisson_solve(ibm_ctx* ctx, const double* b_dev, double* phi_dev, double tol, int check_every,

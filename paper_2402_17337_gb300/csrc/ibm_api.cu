@@ -118,7 +118,7 @@ struct ibm_ctx {
   double *invd_p = nullptr, *invd_u = nullptr, *invd_v = nullptr;
   // mixed precision (FP32 correction, residual and reciprocal diagonal)
   Geo32 geo32{};
-  float *e32 = nullptr, *r32 = nullptr, *invd32 = nullptr;
+  float *e32 = nullptr, *e32b = nullptr, *r32 = nullptr, *invd32 = nullptr;  // e32/e32b: ping-pong
   int m_inner = 32;  // inner sweeps between FP64 checks (adapted)
   // body and band
   bool has_body = false;
@@ -288,25 +288,36 @@ int setup_geometry(ibm_ctx* c) {
   c->invd_u = const_cast<double*>(bb);
   c->invd_v = const_cast<double*>(cc);
   if (c->P.precision == 1) {
-    auto f32 = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+    // colour-split FP32 data of the inner sweeps (Geo32)
     Geo32& g32 = c->geo32;
+    const int pk = ((nx + 1) / 2 + 31) / 32 * 32;
     g32.nx = nx;
     g32.ny = ny;
-    g32.pitch = c->pitch;
-    rc |= c->upload(&g32.pE, f32(pE));
-    rc |= c->upload(&g32.pW, f32(pW));
-    rc |= c->upload(&g32.pN, f32(pN));
-    rc |= c->upload(&g32.pS, f32(pS));
-    std::vector<float> ip32(c->nelem, 0.0f);
+    g32.pk = pk;
+    std::vector<float> ce0(pk, 0.f), ce1(pk, 0.f), cw0(pk, 0.f), cw1(pk, 0.f), pn(ny), ps(ny);
+    for (int k = 0; k < pk; ++k) {
+      if (2 * k < nx) ce0[k] = (float)pE[2 * k], cw0[k] = (float)pW[2 * k];
+      if (2 * k + 1 < nx) ce1[k] = (float)pE[2 * k + 1], cw1[k] = (float)pW[2 * k + 1];
+    }
+    for (int j = 0; j < ny; ++j) pn[j] = (float)pN[j], ps[j] = (float)pS[j];
+    rc |= c->upload(&g32.cE0, ce0);
+    rc |= c->upload(&g32.cE1, ce1);
+    rc |= c->upload(&g32.cW0, cw0);
+    rc |= c->upload(&g32.cW1, cw1);
+    rc |= c->upload(&g32.pN, pn);
+    rc |= c->upload(&g32.pS, ps);
+    const size_t n32 = (size_t)2 * ny * pk;
+    std::vector<float> ip32(n32, 0.0f);
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         float d = (float)pE[i] + (float)pW[i] + (float)pN[j] + (float)pS[j];
-        ip32[at(i, j, c->pitch)] = 1.0f / d;
+        ip32[rb_at(i, j, ny, pk)] = 1.0f / d;
       }
     const float* d32;
     rc |= c->upload(&d32, ip32);
-    rc |= c->alloc(&c->e32, c->nelem);
-    rc |= c->alloc(&c->r32, c->nelem);
+    rc |= c->alloc(&c->e32, n32);
+    rc |= c->alloc(&c->e32b, n32);
+    rc |= c->alloc(&c->r32, n32);
     if (rc) return IBM_E_CUDA;
     c->invd32 = const_cast<float*>(d32);
   }
@@ -412,7 +423,7 @@ int solve_poisson_mixed(ibm_ctx* c, double tol, int maxs, int* sweeps, double* r
   for (;;) {
     if (pending) CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
     CUDA_TRY(cudaMemsetAsync(&c->sc->res_bits, 0, 8, c->stream));
-    launch_dc_residual(c->stream, g, cur, alt, c->e32, c->b, c->r32, add, &c->sc->res_bits);
+    launch_dc_residual(c->stream, g, c->geo32.pk, cur, alt, c->e32, c->b, c->r32, add, &c->sc->res_bits);
     c->prof.launches += 1;
     if (add) std::swap(cur, alt);
     double r;
@@ -444,7 +455,9 @@ int solve_poisson_mixed(ibm_ctx* c, double tol, int maxs, int* sweeps, double* r
     if (s + inner > maxs) inner = ((maxs - s) + K2 - 1) / K2 * K2;
     if (c->profiling) CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
     for (int l = 0; l < inner / K2; ++l) {
-      launch_sor32(c->stream, c->geo32, c->e32, c->r32, c->invd32, omega, l == 0 ? 1 : 0);
+      // read e32, write e32b, swap: the final correction ends in e32
+      launch_sor32(c->stream, c->geo32, c->e32, c->e32b, c->r32, c->invd32, omega, l == 0 ? 1 : 0);
+      std::swap(c->e32, c->e32b);
       c->prof.launches += 1;
       if (c->profiling) pending += 1;
     }
@@ -836,14 +849,16 @@ int ibm_poisson_solve(ibm_ctx* c, const double* b_dev, double* phi_dev, double t
                                : solve_poisson(c, tol, 0.0, check_every, maxs, &s, &r);
   if (sweeps) *sweeps = s;
   if (res) *res = r;
-  if (rc) return rc;
-  launch_phi_ref(c->stream, c->geo, c->phi, c->sc);
-  launch_shift(c->stream, c->geo, c->phi, c->sc);
+  if (rc && rc != IBM_E_NOCONV) return rc;
+  if (!rc) {
+    launch_phi_ref(c->stream, c->geo, c->phi, c->sc);
+    launch_shift(c->stream, c->geo, c->phi, c->sc);
+  }
   CUDA_TRY(cudaMemcpy2DAsync(phi_dev, rowb, c->phi + at(0, 0, c->pitch), pb, rowb, c->ny, cudaMemcpyDeviceToDevice,
                              c->stream));
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(c->stream));
-  return IBM_OK;
+  return rc;
 }
 
 int ibm_set_profiling(ibm_ctx* c, int on) {

@@ -35,11 +35,20 @@ struct Geo {
   const double *vE, *vW, *vN, *vS;     // v grid (nx, nx, ny+1, ny+1)
 };
 
-// FP32 copies of the pressure coefficients (mixed-precision inner sweeps).
+// FP32 data of the mixed-precision inner sweeps.  The correction e, its
+// right-hand side r and the reciprocal diagonal are stored split by colour:
+// cell (i, j) of colour c = (i + j) & 1 lives at [(c ny + j) pk + (i >> 1)],
+// so the cells of one colour in a row are contiguous and the neighbours of
+// a cell of the other colour are contiguous too.
 struct Geo32 {
-  int nx, ny, pitch;
-  const float *pE, *pW, *pN, *pS;
+  int nx, ny, pk;
+  const float *cE0, *cE1, *cW0, *cW1;  // pE, pW at i = 2k + s for s = 0, 1 (pk entries)
+  const float *pN, *pS;                // ny entries
 };
+
+__host__ __device__ inline size_t rb_at(int i, int j, int ny, int pk) {
+  return (size_t)(((i + j) & 1) * ny + j) * pk + (size_t)(i >> 1);
+}
 
 // Index rectangle that contains every node the body can touch over its
 // whole plunge, with a margin; used for all three grids.
@@ -107,9 +116,9 @@ void set_last_error(const char* msg);
 
 // mixed precision: FP64 update + residual, FP32 temporally blocked sweeps
 int sor32_half_sweeps_per_launch();
-void launch_dc_residual(cudaStream_t s, const Geo& g, const double* phi_in, double* phi_out, const float* e,
-                        const double* b, float* r32, int add_e, unsigned long long* res_bits);
-void launch_sor32(cudaStream_t s, const Geo32& g, float* e, const float* r, const float* invd, float omega,
-                  int zero_init);
+void launch_dc_residual(cudaStream_t s, const Geo& g, int pk, const double* phi_in, double* phi_out,
+                        const float* e, const double* b, float* r32, int add_e, unsigned long long* res_bits);
+void launch_sor32(cudaStream_t s, const Geo32& g, const float* e_in, float* e_out, const float* r, const float* invd,
+                  float omega, int zero_init);
 
 }  // namespace ibm

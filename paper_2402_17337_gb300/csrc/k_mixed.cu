@@ -3,14 +3,20 @@
 // The red-black SOR of the pressure equation (arXiv 2402.17337, Sec. 2.2,
 // Sec. 3.1) is split into
 //   outer (FP64):  phi <- phi + e,  r = b - L_p phi,  ||r||_inf  (k_dc_residual)
-//   inner (FP32):  red-black SOR sweeps on L_p e = r from e = 0   (k_sor32_tile)
+//   inner (FP32):  red-black SOR sweeps on L_p e = r from e = 0   (k_sor32_rb)
 // so the residual, the pressure update and the norm stay in FP64 while the
-// sweeps, which carry the work, run at the FP32 rate.  Each inner launch
-// performs K half-sweeps on a shared-memory tile that carries a halo of K
-// cells, so the tile is read and written once for K/2 full sweeps; the halo
-// cells are recomputed by the neighbouring tiles (temporal blocking).  The
-// inner iterates are exactly those of red-black SOR applied to the
-// correction equation.
+// sweeps, which carry the work, run at the FP32 rate.  The inner iterates
+// are exactly those of red-black SOR applied to the correction equation.
+//
+// k_sor32_rb performs K half-sweeps per launch on a tile that carries a halo
+// of K cells (temporal blocking): the tile is read and written once for K/2
+// full sweeps and the halo is recomputed by the neighbouring tiles.  The
+// FP32 arrays are stored split by colour (Geo32), so a half-sweep reads its
+// neighbours contiguously; each thread keeps its own cells' correction,
+// right-hand side and reciprocal diagonal in registers for the whole launch
+// and shared memory only carries the values the neighbours read.
+#include <type_traits>
+
 #include "ibm_internal.h"
 
 namespace ibm {
@@ -43,23 +49,24 @@ __device__ inline void block_max_bits(unsigned long long v, unsigned long long* 
 
 // FP64 update and residual.  With add_e the increment e of the last inner
 // solve is added (phi_out = phi_in + e, neighbours included on the fly, so
-// phi_out must differ from phi_in); r is stored in FP32 as the next inner
-// right-hand side.
-__global__ void k_dc_residual(Geo g, const double* __restrict__ phi_in, double* __restrict__ phi_out,
+// phi_out must differ from phi_in); r is stored in FP32, split by colour, as
+// the next inner right-hand side.
+__global__ void k_dc_residual(Geo g, int pk, const double* __restrict__ phi_in, double* __restrict__ phi_out,
                               const float* __restrict__ e, const double* __restrict__ b, float* __restrict__ r32,
                               int add_e, unsigned long long* __restrict__ res_bits) {
   int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   unsigned long long bits = 0ull;
-  if (i < g.nx && j < g.ny) {
+  const int nx = g.nx, ny = g.ny;
+  if (i < nx && j < ny) {
     const int P = g.pitch;
     size_t c = at(i, j, P);
     double fP = phi_in[c], fE = phi_in[c + 1], fW = phi_in[c - 1], fN = phi_in[c + P], fS = phi_in[c - P];
     if (add_e) {
-      fP += (double)e[c];
-      fE += (double)e[c + 1];
-      fW += (double)e[c - 1];
-      fN += (double)e[c + P];
-      fS += (double)e[c - P];
+      fP += (double)e[rb_at(i, j, ny, pk)];
+      if (i < nx - 1) fE += (double)e[rb_at(i + 1, j, ny, pk)];
+      if (i > 0) fW += (double)e[rb_at(i - 1, j, ny, pk)];
+      if (j < ny - 1) fN += (double)e[rb_at(i, j + 1, ny, pk)];
+      if (j > 0) fS += (double)e[rb_at(i, j - 1, ny, pk)];
       phi_out[c] = fP;
     }
     double L = g.pE[i] * (fE - fP);
@@ -67,114 +74,140 @@ __global__ void k_dc_residual(Geo g, const double* __restrict__ phi_in, double* 
     L = fma(g.pN[j], fN - fP, L);
     L = fma(g.pS[j], fS - fP, L);
     double r = b[c] - L;
-    r32[c] = (float)r;
+    r32[rb_at(i, j, ny, pk)] = (float)r;
     bits = abs_bits(r);
   }
   block_max_bits(bits, res_bits);
 }
 
-// K half-sweeps of FP32 red-black SOR on L_p e = r over a TX x TY tile.
-// Loaded region: the tile plus a halo of K cells; after half-sweep h the
-// values are exact for cells at least h+1 cells inside the loaded region, so
-// after K half-sweeps the tile itself is exact.  Cells outside the domain
-// are loaded as zero and never updated; boundary cells have zero
-// coefficients towards them (homogeneous Neumann).
-template <int TX, int TY, int K>
-__global__ void __launch_bounds__(256) k_sor32_tile(const Geo32 g, float* __restrict__ e, const float* __restrict__ r,
-                                                    const float* __restrict__ invd, float omega, int zero_init) {
-  constexpr int H = K, LX = TX + 2 * H, LY = TY + 2 * H;
-  extern __shared__ float smem[];
-  float* se = smem;                 // LY x LX
-  float* sr = se + LX * LY;         // LY x LX
-  float* sd = sr + LX * LY;         // LY x LX
-  float* cE = sd + LX * LY;         // LX
-  float* cW = cE + LX;              // LX
-  float* cN = cW + LX;              // LY
-  float* cS = cN + LY;              // LY
-  const int nx = g.nx, ny = g.ny, P = g.pitch;
-  const int gx0 = blockIdx.x * TX - H, gy0 = blockIdx.y * TY - H;
-  const int tid = threadIdx.x, nth = blockDim.x;
-  for (int t = tid; t < LX * LY; t += nth) {
-    int lx = t % LX, ly = t / LX, i = gx0 + lx, j = gy0 + ly;
-    bool in = i >= 0 && i < nx && j >= 0 && j < ny;
-    size_t c = in ? at(i, j, P) : 0;
-    se[t] = (in && !zero_init) ? e[c] : 0.f;
-    sr[t] = in ? r[c] : 0.f;
-    sd[t] = in ? invd[c] : 0.f;
+// K half-sweeps (red first) of FP32 red-black SOR on L_p e = r, from e_in
+// into e_out.  The two buffers must differ: a tile's halo is read from cells
+// that neighbouring tiles write, and tiles of later waves would otherwise
+// read values that are already K half-sweeps ahead.
+// Block (32, NY); the loaded region is LY = TY + 2K rows by LK = 64 colour
+// columns (k) per colour, i.e. 128 cells in x; the written tile is TY rows
+// by TK = LK - 2 HK colour columns, HK = ceil(K/2).  Thread (tx, ty) owns
+// colour columns tx and tx + 32 of rows ty, ty + NY, ... for both colours.
+// After half-sweep h the values are exact for cells at least h + 1 cells
+// inside the loaded region, so after K half-sweeps the tile is exact.
+// Cells outside the domain are never updated and hold zero; boundary cells
+// have zero coefficients towards them (homogeneous Neumann).
+template <int TY, int K, int NY>
+__global__ void __launch_bounds__(32 * NY) k_sor32_rb(const Geo32 g, const float* __restrict__ e_in,
+                                                       float* __restrict__ e_out, const float* __restrict__ r,
+                                                       const float* __restrict__ invd, float omega, int zero_init) {
+  constexpr int LK = 64, HK = (K + 1) / 2, TK = LK - 2 * HK, LY = TY + 2 * K;
+  constexpr int RPT = (LY + NY - 1) / NY;
+  __shared__ float sh[2][LY][LK];
+  const int nx = g.nx, ny = g.ny, pk = g.pk;
+  const int k0 = blockIdx.x * TK - HK, j0 = blockIdx.y * TY - K;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  float ev[2][RPT][2], rv[2][RPT][2], dv[2][RPT][2];
+  float cE[2][2], cW[2][2], cN[RPT], cS[RPT];
+  unsigned live = 0u;  // bit (c, q, m): cell inside the domain
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    int k = k0 + tx + 32 * m;
+    bool ok = k >= 0 && k < pk;
+    cE[m][0] = ok ? g.cE0[k] : 0.f;
+    cE[m][1] = ok ? g.cE1[k] : 0.f;
+    cW[m][0] = ok ? g.cW0[k] : 0.f;
+    cW[m][1] = ok ? g.cW1[k] : 0.f;
   }
-  for (int t = tid; t < LX; t += nth) {
-    int i = gx0 + t;
-    bool in = i >= 0 && i < nx;
-    cE[t] = in ? g.pE[i] : 0.f;
-    cW[t] = in ? g.pW[i] : 0.f;
-  }
-  for (int t = tid; t < LY; t += nth) {
-    int j = gy0 + t;
-    bool in = j >= 0 && j < ny;
-    cN[t] = in ? g.pN[j] : 0.f;
-    cS[t] = in ? g.pS[j] : 0.f;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int ly = ty + NY * q, j = j0 + ly;
+    const bool rowok = ly < LY && j >= 0 && j < ny;
+    cN[q] = rowok ? g.pN[j] : 0.f;
+    cS[q] = rowok ? g.pS[j] : 0.f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int kk = tx + 32 * m, k = k0 + kk, i = 2 * k + ((c + j) & 1);
+        const bool in = rowok && k >= 0 && i < nx;
+        const size_t o = (size_t)(c * ny + j) * pk + k;
+        ev[c][q][m] = (in && !zero_init) ? e_in[o] : 0.f;
+        rv[c][q][m] = in ? r[o] : 0.f;
+        dv[c][q][m] = in ? invd[o] : 0.f;
+        if (in) live |= 1u << ((c * RPT + q) * 2 + m);
+        if (ly < LY) sh[c][ly][kk] = ev[c][q][m];
+      }
   }
   __syncthreads();
-  // parity of the loaded origin: colour of local (lx, ly) = (gx0 + gy0 + lx + ly) & 1
-  const int par0 = (gx0 + gy0) & 1;
-#pragma unroll 1
-  for (int h = 0; h < K; ++h) {
-    const int colour = h & 1;  // red first
-    const int lo = h + 1, hx = LX - 2 - h, hy = LY - 2 - h;
-    const int w2 = (hx - lo + 2) / 2;  // cells of one colour per row (upper bound)
-    const int rows = hy - lo + 1;
-    for (int t = tid; t < w2 * rows; t += nth) {
-      int ly = lo + t / w2;
-      int k = t % w2;
-      // first lx >= lo with the right colour
-      int lx = lo + ((colour + par0 + lo + ly) & 1) + 2 * k;
-      if (lx > hx) continue;
-      int i = gx0 + lx, j = gy0 + ly;
-      if (i < 0 || i >= nx || j < 0 || j >= ny) continue;
-      int q = ly * LX + lx;
-      float s = cE[lx] * se[q + 1];
-      s = fmaf(cW[lx], se[q - 1], s);
-      s = fmaf(cN[ly], se[q + LX], s);
-      s = fmaf(cS[ly], se[q - LX], s);
-      float gs = (s - sr[q]) * sd[q];
-      float x = se[q];
-      se[q] = fmaf(omega, gs - x, x);
+  // one half-sweep of colour C (compile-time, so the register arrays are
+  // indexed statically); h counts half-sweeps done
+  auto half = [&](auto colour, int h) {
+    constexpr int c = decltype(colour)::value, oc = c ^ 1;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int ly = ty + NY * q;
+      if (ly < h + 1 || ly > LY - 2 - h) continue;
+      const int s = (c + j0 + ly) & 1;  // colour c sits at i = 2k + s in this row
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int kk = tx + 32 * m;
+        const int li = 2 * kk + s;  // cell index within the loaded 2 LK cells
+        if (li < h + 1 || li > 2 * LK - 2 - h) continue;
+        if (!(live >> ((c * RPT + q) * 2 + m) & 1u)) continue;
+        // neighbours of the other colour: W and E in this row, N and S
+        const float xW = sh[oc][ly][kk - 1 + s], xE = sh[oc][ly][kk + s];
+        const float xN = sh[oc][ly + 1][kk], xS = sh[oc][ly - 1][kk];
+        const float ce = s ? cE[m][1] : cE[m][0], cw = s ? cW[m][1] : cW[m][0];
+        float sum = ce * xE;
+        sum = fmaf(cw, xW, sum);
+        sum = fmaf(cN[q], xN, sum);
+        sum = fmaf(cS[q], xS, sum);
+        const float gs = (sum - rv[c][q][m]) * dv[c][q][m];
+        const float x = ev[c][q][m];
+        const float nxv = fmaf(omega, gs - x, x);
+        ev[c][q][m] = nxv;
+        sh[c][ly][kk] = nxv;
+      }
     }
     __syncthreads();
+  };
+#pragma unroll 1
+  for (int h = 0; h < K; h += 2) {
+    half(std::integral_constant<int, 0>{}, h);      // red
+    half(std::integral_constant<int, 1>{}, h + 1);  // black
   }
-  for (int t = tid; t < TX * TY; t += nth) {
-    int lx = H + t % TX, ly = H + t / TX, i = gx0 + lx, j = gy0 + ly;
-    if (i < nx && j < ny) e[at(i, j, P)] = se[ly * LX + lx];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int ly = ty + NY * q;
+    if (ly < K || ly >= K + TY) continue;
+    const int j = j0 + ly;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int kk = tx + 32 * m;
+        if (kk < HK || kk >= HK + TK) continue;
+        if (!(live >> ((c * RPT + q) * 2 + m) & 1u)) continue;
+        e_out[(size_t)(c * ny + j) * pk + (k0 + kk)] = ev[c][q][m];
+      }
   }
 }
 
-template <int TX, int TY, int K>
-constexpr size_t tile_smem() {
-  return sizeof(float) * (3 * (TX + 2 * K) * (TY + 2 * K) + 2 * (TX + 2 * K) + 2 * (TY + 2 * K));
-}
-
-constexpr int STX = 64, STY = 32, SK = 8;  // tile and half-sweeps per launch
+constexpr int S_TY = 32, S_K = 8, S_NY = 16;  // rows per tile, half-sweeps per launch (even), thread rows
+static_assert(S_K % 2 == 0, "half-sweeps come in red-black pairs");
 
 }  // namespace
 
-int sor32_half_sweeps_per_launch() { return SK; }
+int sor32_half_sweeps_per_launch() { return S_K; }
 
-void launch_dc_residual(cudaStream_t s, const Geo& g, const double* phi_in, double* phi_out, const float* e,
+void launch_dc_residual(cudaStream_t s, const Geo& g, int pk, const double* phi_in, double* phi_out, const float* e,
                         const double* b, float* r32, int add_e, unsigned long long* res_bits) {
   dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
-  k_dc_residual<<<grd, blk, 0, s>>>(g, phi_in, phi_out, e, b, r32, add_e, res_bits);
+  k_dc_residual<<<grd, blk, 0, s>>>(g, pk, phi_in, phi_out, e, b, r32, add_e, res_bits);
 }
 
-void launch_sor32(cudaStream_t s, const Geo32& g, float* e, const float* r, const float* invd, float omega,
-                  int zero_init) {
-  constexpr size_t sm = tile_smem<STX, STY, SK>();
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_sor32_tile<STX, STY, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
-  }
-  dim3 grd((g.nx + STX - 1) / STX, (g.ny + STY - 1) / STY);
-  k_sor32_tile<STX, STY, SK><<<grd, 256, sm, s>>>(g, e, r, invd, omega, zero_init);
+void launch_sor32(cudaStream_t s, const Geo32& g, const float* e_in, float* e_out, const float* r, const float* invd,
+                  float omega, int zero_init) {
+  constexpr int LK = 64, HK = (S_K + 1) / 2, TK = LK - 2 * HK;
+  const int ncol = (g.nx + 1) / 2;  // colour columns
+  dim3 grd((ncol + TK - 1) / TK, (g.ny + S_TY - 1) / S_TY);
+  k_sor32_rb<S_TY, S_K, S_NY><<<grd, dim3(32, S_NY), 0, s>>>(g, e_in, e_out, r, invd, omega, zero_init);
 }
 
 }  // namespace ibm

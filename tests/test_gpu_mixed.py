@@ -77,3 +77,35 @@ def test_mixed_poisson_solve_matches_oracle():
         assert np.abs(pd.cpu().numpy() - phio).max() <= A_inv_bound * 2e-9
         # the FP32 inner sweeps do not slow the iteration down much
         assert sg <= 1.5 * so + 64, (sg, so)
+
+
+@pytest.mark.parametrize("nx,ny,hmin", [(301, 97, 0.0), (517, 263, 0.05), (2001, 1201, 0.006)])
+def test_fp32_sweeps_reproduce_sor_iterates(nx, ny, hmin):
+    """32 FP32 red-black sweeps on the correction equation (temporally
+    blocked, 8 half-sweeps per launch on tiles with halos) equal 32 FP64
+    red-black SOR sweeps of the oracle from the same start, to FP32 rounding.
+    Grids span several tiles in both directions with ragged last tiles; the
+    largest needs several waves of tiles, so a tile that read a neighbour's
+    already-updated halo would show here."""
+    import torch
+    from paper_2402_17337_gb300 import Solver, build
+    build.build()
+    kw = dict(x0=-7.5, x1=24.0, y0=-12.5, y1=12.5, nx=nx, ny=ny, hmin=hmin, ubox=(-1.0, 2.0, -0.8, 0.8), dt=1.0)
+    o = oracle.Sim(**kw)
+    g = Solver(**kw, precision=1)
+    b = W.random_field((ny, nx), seed=nx + 5 * ny)
+    xf, yf = o.grid()
+    V = np.outer(np.diff(yf), np.diff(xf))
+    b -= np.sum(b * V) / np.sum(V)
+    phi0 = W.random_field((ny, nx), seed=9, scale=0.3)
+    rc, phio, so, _ = o.poisson(b, phi0=phi0, tol=1e-300, check=32, maxs=32)
+    assert rc == -3 and so == 32
+    bd = torch.tensor(b, device="cuda")
+    pd = torch.tensor(phi0, device="cuda")
+    torch.cuda.synchronize()
+    rc, sg, _ = g.poisson_solve(bd.data_ptr(), pd.data_ptr(), 1e-300, 8, 32)
+    assert rc == -3 and sg == 32
+    d = pd.cpu().numpy() - phio
+    change = phio - phi0
+    # FP32 rounding of the correction, relative to how far the iterate moved
+    assert np.abs(d).max() <= 1e-4 * np.abs(change).max(), np.abs(d).max() / np.abs(change).max()
