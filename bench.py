@@ -34,7 +34,6 @@ sys.path.insert(0, ROOT)
 
 FP64_FLOPS_PER_CLK_SM = 4.0   # 2 FP64 FMA per clock per SM on GB300 (sm_103)
 FP32_FLOPS_PER_CLK_SM = 256.0  # 128 FP32 FMA per clock per SM
-SOR32_HALF_SWEEPS = 8          # half-sweeps fused per FP32 tile launch
 SOR32_BYTES_PER_CELL_LAUNCH = 12  # read e, r; write e (FP32) once per launch
 SOR_FLOPS_PER_UPDATE = 12     # 4 products + 3 adds, minus b, times 1/d, relaxation (2)
 SOR_BYTES_PER_CELL_HALF = 16  # read phi (8, all cells), read b (4), write phi (4) per half-sweep
@@ -290,9 +289,10 @@ def main():
         else:
             nbytes = SOR32_BYTES_PER_CELL_LAUNCH * cfg.cells
             achieved = nbytes / t_launch / 1e9
-            sweeps_per_launch = SOR32_HALF_SWEEPS / 2
-            roof = {"bound": "hbm", "kernel": f"k_sor32_tile (FP32 red-black SOR, {SOR32_HALF_SWEEPS} half-sweeps "
-                                              f"per launch)",
+            rows, half, _ = prof["sor_shape"]
+            sweeps_per_launch = half / 2
+            roof = {"bound": "hbm", "kernel": f"k_sor32_rb (FP32 red-black SOR, tile {rows} rows x 128 cells, "
+                                              f"{half} half-sweeps per launch, chosen by the autotuner)",
                     "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "launch_us": t_launch * 1e6,
                     "fp32_tflops": SOR_FLOPS_PER_UPDATE * cfg.cells * sweeps_per_launch / t_launch / 1e12,

@@ -49,7 +49,7 @@ typedef struct ibm_ctx ibm_ctx;
 
 /* Grid, flow and solver parameters (Sec. 2.1-2.3).
  *   x0,x1,y0,y1  rectangular domain; the paper uses [-7.5,24] x [-12.5,12.5]
- *   nx,ny        number of cells (>= 4 each)
+ *   nx,ny        number of cells (>= 4 each, ny <= 8192)
  *   hmin         <= 0: uniform grid; otherwise the spacing of the uniform block
  *                ubox = [bx0,bx1] x [by0,by1]; outside it the spacing grows
  *                geometrically to the domain edge (Sec. 2.3)
@@ -150,7 +150,9 @@ int ibm_get_grid(const ibm_ctx* ctx, double* xf, double* yf);
 /* Solves L_p phi = b (homogeneous Neumann) by red-black SOR on the
  * context's grid, as inside a step (Sec. 2.2), to
  * ||b - L_p phi||_inf <= tol checked every check_every sweeps (precision 1:
- * FP32 sweeps inside FP64 defect correction, checked in FP64), then shifts
+ * FP32 sweeps inside FP64 defect correction, checked in FP64 after whole
+ * launches of the tuned tile, so sweep counts and the max_sweeps cap are
+ * rounded up to a multiple of the sweeps per launch), then shifts
  * phi so that the cell (nx-1, 0) is zero.  b_dev, phi_dev: device pointers
  * to nx*ny doubles in the compact layout; phi_dev holds the initial guess
  * and receives the result (on IBM_E_NOCONV: the last iterate, unshifted).
@@ -207,7 +209,16 @@ typedef struct {
   long long steps;           /* steps completed */
   long long poisson_sweeps;  /* pressure sweeps over all steps */
   long long helm_sweeps;     /* velocity sweeps over all steps (u and v) */
+  int sor_shape[3];          /* FP32 sweep tile chosen by the autotuner: rows per tile,
+                                half-sweeps per launch, thread rows (0 if not tuned) */
+  double sor_us_per_sweep;   /* its measured time per full sweep, microseconds */
 } ibm_profile;
+
+/* Autotuner of the FP32 sweep kernel (precision 1): times each tile shape on
+ * this context's grid and keeps the fastest per sweep.  Runs by itself
+ * before the first mixed-precision solve; calling it re-tunes.  A no-op for
+ * precision 0.  Uses the context's work arrays: not during a step. */
+int ibm_tune(ibm_ctx* ctx);
 
 /* Turns the event timing of pressure sweeps on (1) or off (0); counters are
  * reset.  Timing adds one event pair per run of sweeps. */
@@ -215,6 +226,44 @@ int ibm_set_profiling(ibm_ctx* ctx, int on);
 
 /* Copies the counters. */
 int ibm_get_profile(const ibm_ctx* ctx, ibm_profile* out);
+
+/* ---------------------------------------------------------------- U-Net
+ * Learned warm start of the pressure solve: a 4-level convolutional U-Net
+ * with BF16 weights and activations and FP32 accumulation (tensor cores),
+ * trained on the GPU by the library's own forward and backward kernels on
+ * samples the solver generates.  widths: channels of the four levels
+ * (multiples of 16).  Inputs are 4 FP32 feature channels [H][W][4], the
+ * output one FP32 channel [H][W]; H and W must be multiples of 8.  Device
+ * pointers; stream may be NULL. */
+typedef struct ibm_unet ibm_unet;
+int ibm_unet_create(const int widths[4], unsigned long long seed, ibm_unet** out);
+void ibm_unet_destroy(ibm_unet* net);
+long long ibm_unet_num_params(const ibm_unet* net);
+/* copies the FP32 master parameters to (set = 0) or from (set = 1) host */
+int ibm_unet_params(ibm_unet* net, float* host, long long n, int set);
+/* gradient of the last ibm_unet_train_step, to host */
+int ibm_unet_grads(const ibm_unet* net, float* host, long long n);
+int ibm_unet_forward(ibm_unet* net, const float* feat_dev, int H, int W, float* out_dev, void* stream);
+/* one Adam step (apply = 1) on the mean squared error of output channel 0
+ * against target_dev [H][W]; apply = 0 only computes the gradient.
+ * *loss (may be NULL) receives the loss. */
+int ibm_unet_train_step(ibm_unet* net, const float* feat_dev, const float* target_dev, int H, int W, float lr,
+                        int apply, double* loss, void* stream);
+
+/* Warm start of the pressure solve of each step (Sec. 2.2 solves it by SOR
+ * from a starting guess): mode 0, the previous increment; mode 1, the
+ * previous increment plus the U-Net's prediction of its change (the net is
+ * borrowed, not owned); mode 2, the previous increment and, every step, a
+ * training sample recorded for ibm_get_sample.  The network works on the
+ * grid coarsened 2x (nx, ny must be divisible by 16) with four features per
+ * coarse cell (initial residual b - L_p phi^n, b, body-cell fraction, p^n,
+ * each over its infinity norm) and predicts (phi^{n+1} - phi^n) / (s0 c_T),
+ * s0 the norm of the residual feature and c_T = target_scale. */
+int ibm_set_warmstart(ibm_ctx* ctx, int mode, ibm_unet* net, double target_scale);
+
+/* Last recorded sample (mode 2): feat [Hc][Wc][4] and target [Hc][Wc]
+ * (host, FP32); either may be NULL; *Hc, *Wc receive the coarse sizes. */
+int ibm_get_sample(const ibm_ctx* ctx, float* feat, float* target, int* Hc, int* Wc);
 
 /* Frees the context and its device memory. */
 void ibm_destroy(ibm_ctx* ctx);

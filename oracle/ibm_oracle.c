@@ -34,8 +34,10 @@
  * so both follow one recipe: divisions by grid spacings are multiplications
  * by reciprocals computed once, the 5-point operators are fused
  * multiply-add chains in the order E, W, N, S (fma() below), and the two
- * sums that feed back into the flow (outflow flux, body-cell source) are
- * accumulated in index order.  Everything else is a plain expression.
+ * sums that feed back into the flow are accumulated in a fixed two-level
+ * index order (outflow flux: rows within chunks of 32, then the chunks;
+ * body-cell source: along each row, then the rows).  Everything else is a
+ * plain expression.
  */
 #include <math.h>
 #include <stdint.h>
@@ -836,10 +838,17 @@ static int one_step(or_sim* S) {
       double ub = S->u[UI(nx, j)];
       S->uh[UI(nx, j)] = ub - dt * P->u_in * (ub - S->u[UI(nx - 1, j)]) * S->idx[nx - 1];
     }
-    for (int j = 0; j < ny; ++j) {
-      qin += S->uh[UI(0, j)] * S->dy[j];
-      qout += S->uh[UI(nx, j)] * S->dy[j];
-      ly += S->dy[j];
+    /* fluxes: in row order within chunks of 32 rows, then the chunk sums in order */
+    for (int j0 = 0; j0 < ny; j0 += 32) {
+      double a = 0.0, b = 0.0, c = 0.0;
+      for (int j = j0; j < j0 + 32 && j < ny; ++j) {
+        a += S->uh[UI(0, j)] * S->dy[j];
+        b += S->uh[UI(nx, j)] * S->dy[j];
+        c += S->dy[j];
+      }
+      qin += a;
+      qout += b;
+      ly += c;
     }
     double corr = (qin - qout) / ly;
     for (int j = 0; j < ny; ++j) S->uh[UI(nx, j)] += corr;
@@ -872,14 +881,19 @@ static int one_step(or_sim* S) {
    * so the faces a moving body pushes through still drive the pressure.
    * b = (D(uhat) - q)/dt. */
   or_div(S, S->uh, S->vh, S->D);
+  /* sums over body cells: along each row in order, then the row sums in order */
   double sdv = 0.0, sv = 0.0;
-  for (int j = 0; j < ny; ++j)
+  for (int j = 0; j < ny; ++j) {
+    double a = 0.0, b = 0.0;
     for (int i = 0; i < nx; ++i)
       if (S->cut[PI_(i, j)]) {
         double V = S->dx[i] * S->dy[j];
-        sdv += S->D[PI_(i, j)] * V;
-        sv += V;
+        a += S->D[PI_(i, j)] * V;
+        b += V;
       }
+    sdv += a;
+    sv += b;
+  }
   double cbar = sv > 0.0 ? sdv / sv : 0.0;
   double sq = 0.0;
   for (int j = 0; j < ny; ++j)

@@ -50,10 +50,13 @@ class StepStats(C.Structure):
 
 class Profile(C.Structure):
     _fields_ = [("launches", C.c_longlong), ("sweep_launches", C.c_longlong), ("sweep_ms", C.c_double),
-                ("steps", C.c_longlong), ("poisson_sweeps", C.c_longlong), ("helm_sweeps", C.c_longlong)]
+                ("steps", C.c_longlong), ("poisson_sweeps", C.c_longlong), ("helm_sweeps", C.c_longlong),
+                ("sor_shape", C.c_int * 3), ("sor_us_per_sweep", C.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["sor_shape"] = list(self.sor_shape)
+        return d
 
 
 _D = C.POINTER(C.c_double)
@@ -80,7 +83,21 @@ def lib():
             L.ibm_poisson_solve.argtypes = [_VP, _VP, _VP, C.c_double, C.c_int, C.c_int,
                                             C.POINTER(C.c_int), C.POINTER(C.c_double)]
             L.ibm_set_profiling.argtypes = [_VP, C.c_int]
+            L.ibm_tune.argtypes = [_VP]
             L.ibm_get_profile.argtypes = [_VP, C.POINTER(Profile)]
+            L.ibm_unet_create.argtypes = [C.POINTER(C.c_int), C.c_ulonglong, C.POINTER(_VP)]
+            L.ibm_unet_destroy.argtypes = [_VP]
+            L.ibm_unet_destroy.restype = None
+            L.ibm_unet_num_params.argtypes = [_VP]
+            L.ibm_unet_num_params.restype = C.c_longlong
+            L.ibm_unet_params.argtypes = [_VP, C.POINTER(C.c_float), C.c_longlong, C.c_int]
+            L.ibm_unet_grads.argtypes = [_VP, C.POINTER(C.c_float), C.c_longlong]
+            L.ibm_unet_forward.argtypes = [_VP, _VP, C.c_int, C.c_int, _VP, _VP]
+            L.ibm_unet_train_step.argtypes = [_VP, _VP, _VP, C.c_int, C.c_int, C.c_float, C.c_int,
+                                              C.POINTER(C.c_double), _VP]
+            L.ibm_set_warmstart.argtypes = [_VP, C.c_int, _VP, C.c_double]
+            L.ibm_get_sample.argtypes = [_VP, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_int),
+                                         C.POINTER(C.c_int)]
             L.ibm_destroy.argtypes = [_VP]
             L.ibm_destroy.restype = None
             L.ibm_last_error.restype = C.c_char_p
@@ -196,6 +213,11 @@ class Solver:
         _check(lib().ibm_get_grid(self._h, _dp(xf), _dp(yf)))
         return xf, yf
 
+    def tune(self):
+        """Re-runs the autotuner of the FP32 sweep tile (precision 1)."""
+        _check(lib().ibm_tune(self._h))
+        return self.profile()
+
     def set_profiling(self, on=True):
         _check(lib().ibm_set_profiling(self._h, 1 if on else 0))
 
@@ -204,6 +226,21 @@ class Solver:
         _check(lib().ibm_get_profile(self._h, C.byref(p)))
         return p.as_dict()
 
+    def set_warmstart(self, mode, net=None, target_scale=1.0):
+        """0: previous increment; 1: learned (U-Net net); 2: previous increment + samples."""
+        self._ws_net = net  # keep the network alive while the context uses it
+        _check(lib().ibm_set_warmstart(self._h, mode, net._h if net is not None else None, target_scale))
+
+    def sample(self):
+        """(features [Hc][Wc][4], target [Hc][Wc]) recorded by the last step (mode 2)."""
+        hc, wc = C.c_int(0), C.c_int(0)
+        _check(lib().ibm_get_sample(self._h, None, None, C.byref(hc), C.byref(wc)))
+        f = np.zeros((hc.value, wc.value, 4), np.float32)
+        t = np.zeros((hc.value, wc.value), np.float32)
+        _F = C.POINTER(C.c_float)
+        _check(lib().ibm_get_sample(self._h, f.ctypes.data_as(_F), t.ctypes.data_as(_F), C.byref(hc), C.byref(wc)))
+        return f, t
+
     def poisson_solve(self, b_ptr, phi_ptr, tol, check_every=8, max_sweeps=0):
         """Standalone pressure solve on device buffers (nx*ny doubles each)."""
         s = C.c_int(0)
@@ -211,3 +248,49 @@ class Solver:
         rc = lib().ibm_poisson_solve(self._h, b_ptr, phi_ptr, tol, check_every, max_sweeps, C.byref(s),
                                      C.byref(r))
         return rc, s.value, r.value
+
+
+class UNet:
+    """The warm-start U-Net (device weights; BF16 tensor-core kernels)."""
+
+    def __init__(self, widths=(32, 64, 128, 128), seed=0):
+        w = (C.c_int * 4)(*widths)
+        h = _VP()
+        _check(lib().ibm_unet_create(w, seed, C.byref(h)))
+        self._h = h
+        self.widths = tuple(widths)
+        self.n = lib().ibm_unet_num_params(h)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ibm_unet_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        a = np.zeros(self.n, np.float32)
+        _check(lib().ibm_unet_params(self._h, a.ctypes.data_as(C.POINTER(C.c_float)), self.n, 0))
+        return a
+
+    def set_params(self, a):
+        a = np.ascontiguousarray(a, np.float32)
+        _check(lib().ibm_unet_params(self._h, a.ctypes.data_as(C.POINTER(C.c_float)), self.n, 1))
+
+    def grads(self):
+        a = np.zeros(self.n, np.float32)
+        _check(lib().ibm_unet_grads(self._h, a.ctypes.data_as(C.POINTER(C.c_float)), self.n))
+        return a
+
+    def forward(self, feat_ptr, H, W, out_ptr, stream=None):
+        _check(lib().ibm_unet_forward(self._h, feat_ptr, H, W, out_ptr, stream))
+
+    def train_step(self, feat_ptr, target_ptr, H, W, lr=1e-3, apply=True, stream=None):
+        loss = C.c_double(0.0)
+        _check(lib().ibm_unet_train_step(self._h, feat_ptr, target_ptr, H, W, lr, 1 if apply else 0,
+                                         C.byref(loss), stream))
+        return loss.value

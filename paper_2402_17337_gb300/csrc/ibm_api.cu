@@ -120,12 +120,14 @@ struct ibm_ctx {
   Geo32 geo32{};
   float *e32 = nullptr, *e32b = nullptr, *r32 = nullptr, *invd32 = nullptr;  // e32/e32b: ping-pong
   int m_inner = 32;  // inner sweeps between FP64 checks (adapted)
+  int sor_cfg = -1;          // tile shape of the FP32 sweeps, -1: not tuned yet
+  double sor_us = 0.0;       // its measured time per full sweep
   // body and band
   bool has_body = false;
   double chord = 1, tc = 0.12, h = 0, k = 0, xb = 0, yb0 = 0;
   Band band{0, 0, 1, 1};
   uint8_t *fu = nullptr, *fv = nullptr, *fc = nullptr;
-  double *au = nullptr, *av = nullptr, *qband = nullptr;
+  double *au = nullptr, *av = nullptr, *qband = nullptr, *rowsum = nullptr;
   double* partials = nullptr;
   DevScalars* sc = nullptr;
   DevScalars* sc_host = nullptr;  // pinned mirror
@@ -134,6 +136,15 @@ struct ibm_ctx {
   int hist_cap = 0;
   int n = 0;
   ibm_step_stats last{};
+  // warm start: 0 previous increment, 1 learned (U-Net), 2 previous increment + sample capture
+  int ws_mode = 0;
+  ibm_unet* ws_net = nullptr;
+  double ws_cT = 1.0;
+  int Hc = 0, Wc = 0;
+  float *ws_feat = nullptr, *ws_out = nullptr, *ws_target = nullptr;
+  double* phi_old = nullptr;
+  unsigned long long* ws_max = nullptr;
+  bool has_sample = false;
   // profiling
   ibm_profile prof{};
   bool profiling = false;
@@ -408,12 +419,59 @@ int solve_poisson(ibm_ctx* c, double tol, double rtol, int m, int maxs, int* swe
   }
 }
 
+// Autotuner of the FP32 sweep kernel: times every tile shape on this
+// context's grid and arrays (CUDA events, a few launches each) and keeps the
+// fastest per full sweep.  Runs before the first mixed solve; the arrays'
+// contents are rewritten by the solve (each inner solve starts from e = 0
+// and the residual kernel rewrites r).
+int tune_sor32(ibm_ctx* c) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  CUDA_TRY(cudaEventCreate(&a));
+  CUDA_TRY(cudaEventCreate(&b));
+  const float omega = (float)c->P.omega_p;
+  double best = 1e300;
+  int best_cfg = 0;
+  for (int cfg = 0; cfg < sor32_num_configs(); ++cfg) {
+    const int reps = 8;
+    for (int w = 0; w < 2; ++w) {
+      launch_sor32(c->stream, cfg, c->geo32, c->e32, c->e32b, c->r32, c->invd32, omega, 1);
+      std::swap(c->e32, c->e32b);
+    }
+    CUDA_TRY(cudaEventRecord(a, c->stream));
+    for (int l = 0; l < reps; ++l) {
+      launch_sor32(c->stream, cfg, c->geo32, c->e32, c->e32b, c->r32, c->invd32, omega, l == 0 ? 1 : 0);
+      std::swap(c->e32, c->e32b);
+    }
+    CUDA_TRY(cudaEventRecord(b, c->stream));
+    CUDA_TRY(cudaEventSynchronize(b));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+    const double us_sweep = 1e3 * ms / (reps * (sor32_half_sweeps(cfg) / 2));
+    c->prof.launches += reps + 2;
+    if (us_sweep < best) {
+      best = us_sweep;
+      best_cfg = cfg;
+    }
+  }
+  CUDA_TRY(cudaGetLastError());
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  c->sor_cfg = best_cfg;
+  c->sor_us = best;
+  return IBM_OK;
+}
+
 // Defect correction: FP64 residual and update around FP32 red-black SOR
 // sweeps on the correction equation.  The number of inner sweeps between two
 // FP64 checks adapts to the observed convergence rate.
 int solve_poisson_mixed(ibm_ctx* c, double tol, int maxs, int* sweeps, double* res) {
   const Geo& g = c->geo;
-  const int K2 = sor32_half_sweeps_per_launch() / 2;  // full sweeps per launch
+  if (c->sor_cfg < 0) {
+    int rc = tune_sor32(c);
+    if (rc) return rc;
+  }
+  const int cfg = c->sor_cfg;
+  const int K2 = sor32_half_sweeps(cfg) / 2;  // full sweeps per launch
   double* cur = c->phi;
   double* alt = c->phi2;
   int s = 0, add = 0, inner = 0;
@@ -456,7 +514,7 @@ int solve_poisson_mixed(ibm_ctx* c, double tol, int maxs, int* sweeps, double* r
     if (c->profiling) CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
     for (int l = 0; l < inner / K2; ++l) {
       // read e32, write e32b, swap: the final correction ends in e32
-      launch_sor32(c->stream, c->geo32, c->e32, c->e32b, c->r32, c->invd32, omega, l == 0 ? 1 : 0);
+      launch_sor32(c->stream, cfg, c->geo32, c->e32, c->e32b, c->r32, c->invd32, omega, l == 0 ? 1 : 0);
       std::swap(c->e32, c->e32b);
       c->prof.launches += 1;
       if (c->profiling) pending += 1;
@@ -531,10 +589,24 @@ int one_step(ibm_ctx* c) {
   launch_rhs(c->stream, g, c->uh, c->vh, c->b, dt);
   c->prof.launches += 1;
   if (c->has_body) {
-    launch_body_source(c->stream, g, c->band, c->fc, c->uh, c->vh, c->b, c->qband, dt, c->partials, c->sc);
+    launch_body_source(c->stream, g, c->band, c->fc, c->uh, c->vh, c->b, c->qband, dt, c->rowsum, c->sc);
     c->prof.launches += 3;
   }
   // a7/a8: pressure solve warm-started from the previous increment
+  // a7: warm start.  The solve starts from the previous increment; the
+  // learned form adds the U-Net's prediction of the change.
+  if (c->ws_mode) {
+    launch_ws_features(c->stream, g, c->Hc, c->Wc, c->b, c->phi, c->p, c->band, c->fc, c->ws_feat, c->ws_max);
+    c->prof.launches += 2;
+    if (c->ws_mode == 2)
+      CUDA_TRY(cudaMemcpyAsync(c->phi_old, c->phi, c->nelem * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (c->ws_mode == 1) {
+      rc = ibm_unet_forward(c->ws_net, c->ws_feat, c->Hc, c->Wc, c->ws_out, c->stream);
+      if (rc) return rc;
+      launch_ws_apply(c->stream, g, c->Hc, c->Wc, c->ws_out, c->ws_cT, c->ws_max, c->phi);
+      c->prof.launches += 16;
+    }
+  }
   if (P.precision == 1) {
     double thr = P.poisson_tol;
     if (P.poisson_rtol > 0.0) {
@@ -550,6 +622,12 @@ int one_step(ibm_ctx* c) {
     rc = solve_poisson(c, P.poisson_tol, P.poisson_rtol, P.check_every_p, P.max_sweeps, &st.sweeps_p, &st.res_p);
   }
   if (rc) return rc;
+  if (c->ws_mode == 2) {
+    launch_phi_ref(c->stream, g, c->phi, c->sc);
+    launch_ws_target(c->stream, g, c->Hc, c->Wc, c->phi, c->phi_old, c->sc, c->ws_cT, c->ws_max, c->ws_target);
+    c->prof.launches += 2;
+    c->has_sample = true;
+  }
   // a10: forces (before the projection overwrites nothing they need)
   if (c->has_body) {
     launch_forces(c->stream, g, c->band, c->fu, c->fv, c->uh, c->vh, c->Ru, c->Rv, beta, dt, c->chord, c->partials,
@@ -626,6 +704,7 @@ int ibm_create_grid(const ibm_grid_params* params, ibm_ctx** out) {
   *out = nullptr;
   ibm_grid_params P = *params;
   if (P.nx < 4 || P.ny < 4) return fail(IBM_E_INVAL, "nx, ny must be >= 4");
+  if (P.ny > 8192) return fail(IBM_E_INVAL, "ny must be <= 8192 (outflow flux reduction)");
   if (!(P.Re > 0.0) || !(P.dt > 0.0)) return fail(IBM_E_INVAL, "Re and dt must be positive");
   if (P.bc != 0 && P.bc != 1) return fail(IBM_E_INVAL, "bc must be 0 or 1");
   if (P.precision != 0 && P.precision != 1) return fail(IBM_E_INVAL, "precision must be 0 or 1");
@@ -721,6 +800,7 @@ int ibm_set_body(ibm_ctx* c, double chord, double tc, double h, double k, double
   rc |= c->alloc(&c->au, nb);
   rc |= c->alloc(&c->av, nb);
   rc |= c->alloc(&c->qband, nb);
+  rc |= c->alloc(&c->rowsum, 2 * (size_t)B.h);
   if (rc) return IBM_E_CUDA;
   c->band = B;
   c->has_body = true;
@@ -875,7 +955,57 @@ int ibm_set_profiling(ibm_ctx* c, int on) {
 int ibm_get_profile(const ibm_ctx* c, ibm_profile* out) {
   if (!c || !out) return fail(IBM_E_INVAL, "null argument");
   *out = c->prof;
+  out->sor_shape[0] = out->sor_shape[1] = out->sor_shape[2] = 0;
+  out->sor_us_per_sweep = c->sor_us;
+  if (c->sor_cfg >= 0) sor32_describe(c->sor_cfg, &out->sor_shape[0], &out->sor_shape[1], &out->sor_shape[2]);
   return IBM_OK;
+}
+
+int ibm_set_warmstart(ibm_ctx* c, int mode, ibm_unet* net, double target_scale) {
+  if (!c) return fail(IBM_E_INVAL, "null context");
+  if (mode < 0 || mode > 2) return fail(IBM_E_INVAL, "warm-start mode must be 0, 1 or 2");
+  if (mode == 1 && !net) return fail(IBM_E_INVAL, "the learned warm start needs a network");
+  if (mode != 0 && (c->nx % 16 || c->ny % 16))
+    return fail(IBM_E_INVAL, "the learned warm start needs nx and ny divisible by 16");
+  if (mode != 0 && !(target_scale > 0.0)) return fail(IBM_E_INVAL, "target_scale must be positive");
+  if (mode != 0 && !c->ws_feat) {
+    c->Hc = c->ny / 2;
+    c->Wc = c->nx / 2;
+    const size_t nc = (size_t)c->Hc * c->Wc;
+    int rc = 0;
+    rc |= c->alloc(&c->ws_feat, 4 * nc);
+    rc |= c->alloc(&c->ws_out, nc);
+    rc |= c->alloc(&c->ws_target, nc);
+    rc |= c->alloc(&c->phi_old, c->nelem);
+    rc |= c->alloc(&c->ws_max, 4);
+    if (rc) return IBM_E_CUDA;
+  }
+  c->ws_mode = mode;
+  c->ws_net = net;
+  c->ws_cT = mode ? target_scale : 1.0;
+  c->has_sample = false;
+  return IBM_OK;
+}
+
+int ibm_get_sample(const ibm_ctx* c, float* feat, float* target, int* Hc, int* Wc) {
+  if (!c) return fail(IBM_E_INVAL, "null context");
+  if (Hc) *Hc = c->Hc;
+  if (Wc) *Wc = c->Wc;
+  if (!feat && !target) return IBM_OK;
+  if (!c->has_sample) return fail(IBM_E_INVAL, "no sample: capture (mode 2) and step first");
+  const size_t nc = (size_t)c->Hc * c->Wc;
+  if (feat) CUDA_TRY(cudaMemcpyAsync(feat, c->ws_feat, 4 * nc * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  if (target) CUDA_TRY(cudaMemcpyAsync(target, c->ws_target, nc * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return IBM_OK;
+}
+
+int ibm_tune(ibm_ctx* c) {
+  if (!c) return fail(IBM_E_INVAL, "null context");
+  if (c->P.precision != 1) return IBM_OK;  // only the FP32 sweeps have shapes to choose
+  int rc = tune_sor32(c);
+  if (!rc) CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return rc;
 }
 
 void ibm_destroy(ibm_ctx* c) {

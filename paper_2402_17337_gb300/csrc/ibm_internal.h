@@ -84,8 +84,8 @@ void launch_predict(cudaStream_t s, const Geo& g, const double* u, const double*
                     double dt, double beta, double vb, int first);
 void launch_rhs(cudaStream_t s, const Geo& g, const double* uh, const double* vh, double* b, double dt);
 void launch_body_source(cudaStream_t s, const Geo& g, const Band& band, const uint8_t* fc, const double* uh,
-                        const double* vh, double* b, double* qband, double dt, double* partials,
-                        DevScalars* sc);
+                        const double* vh, double* b, double* qband, double dt, double* rowsum,
+                        DevScalars* sc);  // rowsum: 2 * band.h doubles
 void launch_forces(cudaStream_t s, const Geo& g, const Band& band, const uint8_t* fu, const uint8_t* fv,
                    const double* uh, const double* vh, const double* Ru, const double* Rv, double beta,
                    double dt, double chord, double* partials, DevScalars* sc, double* cl_hist,
@@ -111,14 +111,25 @@ void launch_helm_res(cudaStream_t s, const Geo& g, int grid, const double* x, co
                      const Band& band, const uint8_t* fl, const double* al, double beta, double Ub,
                      unsigned long long* res_bits);
 
+// learned warm start (k_ws.cu): coarse features, prediction, targets
+void launch_ws_features(cudaStream_t s, const Geo& g, int Hc, int Wc, const double* b, const double* phi,
+                        const double* p, const Band& band, const uint8_t* fc, float* feat,
+                        unsigned long long* ws_max);
+void launch_ws_apply(cudaStream_t s, const Geo& g, int Hc, int Wc, const float* out, double cT,
+                     const unsigned long long* ws_max, double* phi);
+void launch_ws_target(cudaStream_t s, const Geo& g, int Hc, int Wc, const double* phi_new, const double* phi_old,
+                      const DevScalars* sc, double cT, const unsigned long long* ws_max, float* target);
+
 // message for ibm_last_error() on the calling thread
 void set_last_error(const char* msg);
 
 // mixed precision: FP64 update + residual, FP32 temporally blocked sweeps
-int sor32_half_sweeps_per_launch();
+int sor32_num_configs();
+int sor32_half_sweeps(int cfg);  // half-sweeps per launch of tile shape cfg (even)
+void sor32_describe(int cfg, int* rows_per_tile, int* half_sweeps, int* thread_rows);
 void launch_dc_residual(cudaStream_t s, const Geo& g, int pk, const double* phi_in, double* phi_out,
                         const float* e, const double* b, float* r32, int add_e, unsigned long long* res_bits);
-void launch_sor32(cudaStream_t s, const Geo32& g, const float* e_in, float* e_out, const float* r, const float* invd,
-                  float omega, int zero_init);
+void launch_sor32(cudaStream_t s, int cfg, const Geo32& g, const float* e_in, float* e_out, const float* r,
+                  const float* invd, float omega, int zero_init);
 
 }  // namespace ibm

@@ -84,27 +84,42 @@ __global__ void k_dc_residual(Geo g, int pk, const double* __restrict__ phi_in, 
 // into e_out.  The two buffers must differ: a tile's halo is read from cells
 // that neighbouring tiles write, and tiles of later waves would otherwise
 // read values that are already K half-sweeps ahead.
+//
 // Block (32, NY); the loaded region is LY = TY + 2K rows by LK = 64 colour
 // columns (k) per colour, i.e. 128 cells in x; the written tile is TY rows
 // by TK = LK - 2 HK colour columns, HK = ceil(K/2).  Thread (tx, ty) owns
-// colour columns tx and tx + 32 of rows ty, ty + NY, ... for both colours.
-// After half-sweep h the values are exact for cells at least h + 1 cells
-// inside the loaded region, so after K half-sweeps the tile is exact.
-// Cells outside the domain are never updated and hold zero; boundary cells
-// have zero coefficients towards them (homogeneous Neumann).
+// colour columns tx and tx + 32 of rows ty, ty + NY, ... for both colours;
+// it keeps its cells' values in registers, and shared memory holds the
+// values, right-hand side and reciprocal diagonal of the whole region.
+// Every half-sweep updates all cells that have their four neighbours in the
+// region; a value that is wrong because the region is finite moves inwards
+// by one cell per half-sweep, so after K half-sweeps the tile, at least K
+// cells from every edge, is exact.  Cells outside the domain are never
+// updated and hold zero; boundary cells have zero coefficients towards them
+// (homogeneous Neumann).
 template <int TY, int K, int NY>
-__global__ void __launch_bounds__(32 * NY) k_sor32_rb(const Geo32 g, const float* __restrict__ e_in,
-                                                       float* __restrict__ e_out, const float* __restrict__ r,
-                                                       const float* __restrict__ invd, float omega, int zero_init) {
-  constexpr int LK = 64, HK = (K + 1) / 2, TK = LK - 2 * HK, LY = TY + 2 * K;
-  constexpr int RPT = (LY + NY - 1) / NY;
-  __shared__ float sh[2][LY][LK];
+struct Sor32Shape {
+  static constexpr int LK = 64, HK = (K + 1) / 2, TK = LK - 2 * HK, LY = TY + 2 * K;
+  static constexpr int RPT = (LY + NY - 1) / NY;
+  static constexpr size_t smem = sizeof(float) * 3 * 2 * LY * LK;
+};
+
+template <int TY, int K, int NY>
+__global__ void __launch_bounds__(32 * NY, 2)
+    k_sor32_rb(const Geo32 g, const float* __restrict__ e_in, float* __restrict__ e_out, const float* __restrict__ r,
+               const float* __restrict__ invd, float omega, int zero_init) {
+  using S = Sor32Shape<TY, K, NY>;
+  constexpr int LK = S::LK, HK = S::HK, TK = S::TK, LY = S::LY, RPT = S::RPT;
+  extern __shared__ float smem[];
+  float(*se)[LY][LK] = reinterpret_cast<float(*)[LY][LK]>(smem);                    // [2][LY][LK]
+  float(*sr)[LY][LK] = reinterpret_cast<float(*)[LY][LK]>(smem + 2 * LY * LK);      // [2][LY][LK]
+  float(*sd)[LY][LK] = reinterpret_cast<float(*)[LY][LK]>(smem + 4 * LY * LK);      // [2][LY][LK]
   const int nx = g.nx, ny = g.ny, pk = g.pk;
   const int k0 = blockIdx.x * TK - HK, j0 = blockIdx.y * TY - K;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  float ev[2][RPT][2], rv[2][RPT][2], dv[2][RPT][2];
+  float ev[2][RPT][2];
   float cE[2][2], cW[2][2], cN[RPT], cS[RPT];
-  unsigned live = 0u;  // bit (c, q, m): cell inside the domain
+  unsigned live = 0u, upd = 0u;  // bit (c, q, m): inside the domain / updated each half-sweep
 #pragma unroll
   for (int m = 0; m < 2; ++m) {
     int k = k0 + tx + 32 * m;
@@ -124,53 +139,55 @@ __global__ void __launch_bounds__(32 * NY) k_sor32_rb(const Geo32 g, const float
     for (int c = 0; c < 2; ++c)
 #pragma unroll
       for (int m = 0; m < 2; ++m) {
-        const int kk = tx + 32 * m, k = k0 + kk, i = 2 * k + ((c + j) & 1);
+        const int kk = tx + 32 * m, k = k0 + kk, s = (c + j) & 1, i = 2 * k + s;
         const bool in = rowok && k >= 0 && i < nx;
         const size_t o = (size_t)(c * ny + j) * pk + k;
-        ev[c][q][m] = (in && !zero_init) ? e_in[o] : 0.f;
-        rv[c][q][m] = in ? r[o] : 0.f;
-        dv[c][q][m] = in ? invd[o] : 0.f;
-        if (in) live |= 1u << ((c * RPT + q) * 2 + m);
-        if (ly < LY) sh[c][ly][kk] = ev[c][q][m];
+        const float x = (in && !zero_init) ? e_in[o] : 0.f;
+        ev[c][q][m] = x;
+        const int bit = (c * RPT + q) * 2 + m, li = 2 * kk + s;
+        if (in) live |= 1u << bit;
+        if (in && ly >= 1 && ly <= LY - 2 && li >= 1 && li <= 2 * LK - 2) upd |= 1u << bit;
+        if (ly < LY) {
+          se[c][ly][kk] = x;
+          sr[c][ly][kk] = in ? r[o] : 0.f;
+          sd[c][ly][kk] = in ? invd[o] : 0.f;
+        }
       }
   }
   __syncthreads();
   // one half-sweep of colour C (compile-time, so the register arrays are
-  // indexed statically); h counts half-sweeps done
-  auto half = [&](auto colour, int h) {
+  // indexed statically)
+  auto half = [&](auto colour) {
     constexpr int c = decltype(colour)::value, oc = c ^ 1;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
       const int ly = ty + NY * q;
-      if (ly < h + 1 || ly > LY - 2 - h) continue;
       const int s = (c + j0 + ly) & 1;  // colour c sits at i = 2k + s in this row
 #pragma unroll
       for (int m = 0; m < 2; ++m) {
+        if (!(upd >> ((c * RPT + q) * 2 + m) & 1u)) continue;
         const int kk = tx + 32 * m;
-        const int li = 2 * kk + s;  // cell index within the loaded 2 LK cells
-        if (li < h + 1 || li > 2 * LK - 2 - h) continue;
-        if (!(live >> ((c * RPT + q) * 2 + m) & 1u)) continue;
         // neighbours of the other colour: W and E in this row, N and S
-        const float xW = sh[oc][ly][kk - 1 + s], xE = sh[oc][ly][kk + s];
-        const float xN = sh[oc][ly + 1][kk], xS = sh[oc][ly - 1][kk];
+        const float xW = se[oc][ly][kk - 1 + s], xE = se[oc][ly][kk + s];
+        const float xN = se[oc][ly + 1][kk], xS = se[oc][ly - 1][kk];
         const float ce = s ? cE[m][1] : cE[m][0], cw = s ? cW[m][1] : cW[m][0];
         float sum = ce * xE;
         sum = fmaf(cw, xW, sum);
         sum = fmaf(cN[q], xN, sum);
         sum = fmaf(cS[q], xS, sum);
-        const float gs = (sum - rv[c][q][m]) * dv[c][q][m];
+        const float gs = (sum - sr[c][ly][kk]) * sd[c][ly][kk];
         const float x = ev[c][q][m];
         const float nxv = fmaf(omega, gs - x, x);
         ev[c][q][m] = nxv;
-        sh[c][ly][kk] = nxv;
+        se[c][ly][kk] = nxv;
       }
     }
     __syncthreads();
   };
 #pragma unroll 1
   for (int h = 0; h < K; h += 2) {
-    half(std::integral_constant<int, 0>{}, h);      // red
-    half(std::integral_constant<int, 1>{}, h + 1);  // black
+    half(std::integral_constant<int, 0>{});  // red
+    half(std::integral_constant<int, 1>{});  // black
   }
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
@@ -189,12 +206,43 @@ __global__ void __launch_bounds__(32 * NY) k_sor32_rb(const Geo32 g, const float
   }
 }
 
-constexpr int S_TY = 32, S_K = 8, S_NY = 16;  // rows per tile, half-sweeps per launch (even), thread rows
-static_assert(S_K % 2 == 0, "half-sweeps come in red-black pairs");
+// Tile shapes the autotuner chooses from: (rows per tile, half-sweeps per
+// launch, thread rows).
+struct Sor32Config {
+  int TY, K, NY;
+  void (*launch)(cudaStream_t, const Geo32&, const float*, float*, const float*, const float*, float, int);
+};
+
+template <int TY, int K, int NY>
+void launch_shape(cudaStream_t s, const Geo32& g, const float* e_in, float* e_out, const float* r, const float* invd,
+                  float omega, int zero_init) {
+  using S = Sor32Shape<TY, K, NY>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_sor32_rb<TY, K, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
+    attr = true;
+  }
+  const int ncol = (g.nx + 1) / 2;
+  dim3 grd((ncol + S::TK - 1) / S::TK, (g.ny + TY - 1) / TY);
+  k_sor32_rb<TY, K, NY><<<grd, dim3(32, NY), S::smem, s>>>(g, e_in, e_out, r, invd, omega, zero_init);
+}
+
+const Sor32Config kConfigs[] = {
+    {32, 8, 16, launch_shape<32, 8, 16>},  {48, 8, 16, launch_shape<48, 8, 16>},
+    {16, 8, 8, launch_shape<16, 8, 8>},    {32, 4, 8, launch_shape<32, 4, 8>},
+    {64, 16, 16, launch_shape<64, 16, 16>}, {32, 12, 16, launch_shape<32, 12, 16>},
+};
+constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
 }  // namespace
 
-int sor32_half_sweeps_per_launch() { return S_K; }
+int sor32_num_configs() { return kNumConfigs; }
+int sor32_half_sweeps(int cfg) { return kConfigs[cfg].K; }
+void sor32_describe(int cfg, int* ty, int* k, int* ny) {
+  *ty = kConfigs[cfg].TY;
+  *k = kConfigs[cfg].K;
+  *ny = kConfigs[cfg].NY;
+}
 
 void launch_dc_residual(cudaStream_t s, const Geo& g, int pk, const double* phi_in, double* phi_out, const float* e,
                         const double* b, float* r32, int add_e, unsigned long long* res_bits) {
@@ -202,12 +250,9 @@ void launch_dc_residual(cudaStream_t s, const Geo& g, int pk, const double* phi_
   k_dc_residual<<<grd, blk, 0, s>>>(g, pk, phi_in, phi_out, e, b, r32, add_e, res_bits);
 }
 
-void launch_sor32(cudaStream_t s, const Geo32& g, const float* e_in, float* e_out, const float* r, const float* invd,
-                  float omega, int zero_init) {
-  constexpr int LK = 64, HK = (S_K + 1) / 2, TK = LK - 2 * HK;
-  const int ncol = (g.nx + 1) / 2;  // colour columns
-  dim3 grd((ncol + TK - 1) / TK, (g.ny + S_TY - 1) / S_TY);
-  k_sor32_rb<S_TY, S_K, S_NY><<<grd, dim3(32, S_NY), 0, s>>>(g, e_in, e_out, r, invd, omega, zero_init);
+void launch_sor32(cudaStream_t s, int cfg, const Geo32& g, const float* e_in, float* e_out, const float* r,
+                  const float* invd, float omega, int zero_init) {
+  kConfigs[cfg].launch(s, g, e_in, e_out, r, invd, omega, zero_init);
 }
 
 }  // namespace ibm

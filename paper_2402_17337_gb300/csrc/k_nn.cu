@@ -1,0 +1,419 @@
+// Kernels of the learned warm start: a 4-level convolutional U-Net with BF16
+// weights and activations and FP32 accumulation, trained on the GPU.
+//
+// Layout: activations NHWC (channels contiguous), BF16; a layer may read or
+// write a channel slice of a wider buffer (ld = channels per pixel of the
+// buffer, off = first channel), which is how the decoder's concatenations
+// are formed without copies.  Weights of a 3x3 convolution are [Cout][9][Cin]
+// (tap = 3*(dy+1) + (dx+1)), i.e. K-contiguous columns of the GEMM operand B.
+//
+// The convolutions are implicit GEMMs on the tensor cores (mma.sync
+// m16n8k16, BF16 inputs, FP32 accumulators): forward and data-gradient use
+// one kernel (the data gradient is the forward convolution of the output
+// gradient with the tap-flipped, channel-transposed weights), and the weight
+// gradient reduces over pixels with split-K atomics.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "ibm_internal.h"
+
+namespace ibm {
+namespace nn {
+
+using bf16 = __nv_bfloat16;
+
+namespace {
+
+__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline void ldsm_x4(uint32_t (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+__device__ inline void ldsm_x2(uint32_t (&r)[2], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(smem_u32(p)));
+}
+__device__ inline void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+__device__ inline void ldsm_x2_t(uint32_t (&r)[2], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(smem_u32(p)));
+}
+// D = A (16x16, row) * B (16x8, col) + D, BF16 in, FP32 accumulate
+__device__ inline void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+constexpr int CP = 64;        // pixels per CTA (one row segment)
+constexpr int CN = 64;        // output channels per CTA
+constexpr int CK = 16;        // input channels per K chunk
+constexpr int SROW = CK + 8;  // padded smem row (bf16): 48 bytes, conflict-free ldmatrix
+
+// 3x3 convolution, zero padding, Y = act(conv(X, Wt) + bias).
+// Grid (ceil(W/64), H, ceil(Cout/64)), block 128 (4 warps x 16 pixels).
+// Cin must be a multiple of 16.  If yf is non-null the FP32 result is
+// written there too (dense [H][W][Cout]).
+template <bool RELU>
+__global__ void __launch_bounds__(128) k_conv3x3(int H, int W, int Cin, int Cout, const bf16* __restrict__ X, int ldx,
+                                                 int offx, const bf16* __restrict__ Wt, const float* __restrict__ bias,
+                                                 bf16* __restrict__ Y, int ldy, int offy, float* __restrict__ yf) {
+  __shared__ __align__(16) bf16 sA[3][CP + 2][SROW];
+  __shared__ __align__(16) bf16 sB[CN][9][SROW];
+  const int y = blockIdx.y, x0 = blockIdx.x * CP, co0 = blockIdx.z * CN;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float acc[CN / 8][4];
+#pragma unroll
+  for (int n = 0; n < CN / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+  for (int ci0 = 0; ci0 < Cin; ci0 += CK) {
+    // input halo tile: rows y-1..y+1, pixels x0-1..x0+CP, 16 channels (two 16-byte halves)
+    for (int t = tid; t < 3 * (CP + 2) * 2; t += 128) {
+      int half = t & 1, p = (t >> 1) % (CP + 2), r = (t >> 1) / (CP + 2);
+      int yy = y + r - 1, xx = x0 + p - 1;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+        v = *reinterpret_cast<const uint4*>(X + ((size_t)yy * W + xx) * ldx + offx + ci0 + 8 * half);
+      *reinterpret_cast<uint4*>(&sA[r][p][8 * half]) = v;
+    }
+    // weights: CN output channels x 9 taps x 16 input channels
+    for (int t = tid; t < CN * 9 * 2; t += 128) {
+      int half = t & 1, tap = (t >> 1) % 9, n = (t >> 1) / 9;
+      int co = co0 + n;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (co < Cout) v = *reinterpret_cast<const uint4*>(Wt + ((size_t)co * 9 + tap) * Cin + ci0 + 8 * half);
+      *reinterpret_cast<uint4*>(&sB[n][tap][8 * half]) = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3, dx = tap % 3;
+      uint32_t a[4];
+      // rows: pixels warp*16 + (lane & 15), shifted by dx; k half by lane >> 4
+      ldsm_x4(a, &sA[dy][warp * 16 + (lane & 15) + dx][(lane >> 4) * 8]);
+#pragma unroll
+      for (int n = 0; n < CN / 8; ++n) {
+        uint32_t b[2];
+        ldsm_x2(b, &sB[n * 8 + (lane & 7)][tap][((lane >> 3) & 1) * 8]);
+        mma_bf16(acc[n], a, b);
+      }
+    }
+    __syncthreads();
+  }
+  // epilogue: rows (pixels) lane>>2 and +8, columns (channels) 2*(lane&3), +1
+  const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+  for (int n = 0; n < CN / 8; ++n) {
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const int x = x0 + warp * 16 + g + 8 * hr;
+      const int co = co0 + n * 8 + 2 * tq;
+      if (x >= W || co >= Cout) continue;
+      float v0 = acc[n][2 * hr] + (bias ? bias[co] : 0.f);
+      float v1 = acc[n][2 * hr + 1] + (bias && co + 1 < Cout ? bias[co + 1] : 0.f);
+      if (RELU) {
+        v0 = fmaxf(v0, 0.f);
+        v1 = fmaxf(v1, 0.f);
+      }
+      const size_t o = ((size_t)y * W + x);
+      if (co + 1 < Cout) {
+        *reinterpret_cast<__nv_bfloat162*>(Y + o * ldy + offy + co) = __floats2bfloat162_rn(v0, v1);
+        if (yf) {
+          yf[o * Cout + co] = v0;
+          yf[o * Cout + co + 1] = v1;
+        }
+      } else {
+        Y[o * ldy + offy + co] = __float2bfloat16_rn(v0);
+        if (yf) yf[o * Cout + co] = v0;
+      }
+    }
+  }
+}
+
+// Weight gradient of a 3x3 convolution for one tap:
+//   dW[co][tap][ci] += sum_p G[p][co] * X[p + shift(tap)][ci]
+// GEMM with M = co (64 per CTA), N = ci (16 per CTA), K = pixels (64 per
+// chunk, one row segment per chunk).  Grid (pixel chunks / CHUNKS, 9, tiles of
+// (Cout/64) x (Cin/32)), block 128: warp w takes co rows 16 w .. 16 w + 15.
+// G and X are loaded pixel-major, so both fragments come from ldmatrix.trans.
+constexpr int WP = 64;       // pixels per K chunk
+constexpr int WCI = 16;      // input channels per CTA
+constexpr int WCHUNKS = 16;  // K chunks per CTA (split-K, then atomics)
+
+__global__ void __launch_bounds__(128) k_conv3x3_wgrad(int H, int W, int Cin, int Cout, const bf16* __restrict__ G,
+                                                       int ldg, int offg, const bf16* __restrict__ X, int ldx, int offx,
+                                                       float* __restrict__ dW) {
+  __shared__ __align__(16) bf16 sG[WP][CN + 8];   // [pixel][co]
+  __shared__ __align__(16) bf16 sX[WP][WCI + 8];  // [pixel][ci]
+  const int tap = blockIdx.y, dy = tap / 3 - 1, dx = tap % 3 - 1;
+  const int ntile_ci = Cin / WCI;
+  const int co0 = (blockIdx.z / ntile_ci) * CN, ci0 = (blockIdx.z % ntile_ci) * WCI;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wchunks = (W + WP - 1) / WP;
+  const long nchunks = (long)H * wchunks;
+  float acc[WCI / 8][4];
+#pragma unroll
+  for (int n = 0; n < WCI / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+  for (long ch = (long)blockIdx.x * WCHUNKS; ch < nchunks && ch < (long)(blockIdx.x + 1) * WCHUNKS; ++ch) {
+    const int y = (int)(ch / wchunks), x0 = (int)(ch % wchunks) * WP;
+    const int yy = y + dy;
+    for (int t = tid; t < WP * (CN / 8); t += 128) {
+      int p = t / (CN / 8), q = t % (CN / 8);
+      int x = x0 + p, co = co0 + 8 * q;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (x < W && co < Cout) v = *reinterpret_cast<const uint4*>(G + ((size_t)y * W + x) * ldg + offg + co);
+      *reinterpret_cast<uint4*>(&sG[p][8 * q]) = v;
+    }
+    for (int t = tid; t < WP * (WCI / 8); t += 128) {
+      int p = t / (WCI / 8), q = t % (WCI / 8);
+      int x = x0 + p, xx = x + dx;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (x < W && yy >= 0 && yy < H && xx >= 0 && xx < W)
+        v = *reinterpret_cast<const uint4*>(X + ((size_t)yy * W + xx) * ldx + offx + ci0 + 8 * q);
+      *reinterpret_cast<uint4*>(&sX[p][8 * q]) = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k0 = 0; k0 < WP; k0 += 16) {
+      // A (16 co x 16 px, row-major) from the pixel-major tile: 8x8 blocks
+      // (co 0-7 | 8-15) x (px 0-7 | 8-15), each read transposed
+      uint32_t a[4];
+      {
+        const int blk = lane >> 3, r = lane & 7;
+        const int px = k0 + r + ((blk >> 1) & 1) * 8, co = warp * 16 + (blk & 1) * 8;
+        ldsm_x4_t(a, &sG[px][co]);
+      }
+#pragma unroll
+      for (int n = 0; n < WCI / 8; ++n) {
+        uint32_t b[2];
+        const int blk = (lane >> 3) & 1, r = lane & 7;
+        ldsm_x2_t(b, &sX[k0 + r + blk * 8][n * 8]);
+        mma_bf16(acc[n], a, b);
+      }
+    }
+    __syncthreads();
+  }
+  const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+  for (int n = 0; n < WCI / 8; ++n)
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const int co = co0 + warp * 16 + g + 8 * hr, ci = ci0 + n * 8 + 2 * tq;
+      if (co >= Cout) continue;
+      atomicAdd(&dW[((size_t)co * 9 + tap) * Cin + ci], acc[n][2 * hr]);
+      atomicAdd(&dW[((size_t)co * 9 + tap) * Cin + ci + 1], acc[n][2 * hr + 1]);
+    }
+}
+
+// ---------------------------------------------------------- elementwise
+
+// weights for the data gradient: Wt'[ci][tap'][co] = Wt[co][8 - tap'][ci] (BF16)
+__global__ void k_flip_weights(int Cin, int Cout, const bf16* __restrict__ w, bf16* __restrict__ wt) {
+  long n = (long)Cin * 9 * Cout;
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    int co = (int)(k % Cout), tap = (int)((k / Cout) % 9), ci = (int)(k / ((long)Cout * 9));
+    wt[((long)ci * 9 + tap) * Cout + co] = w[((long)co * 9 + (8 - tap)) * Cin + ci];
+  }
+}
+
+// G[p][c] (a slice) *= (Y[p][c] > 0): gradient through ReLU, in place
+__global__ void k_relu_grad(long npix, int C, bf16* __restrict__ G, int ldg, int offg, const bf16* __restrict__ Y,
+                            int ldy, int offy) {
+  long n = npix * C;
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    long p = k / C;
+    int c = (int)(k % C);
+    bf16& g = G[p * ldg + offg + c];
+    if (!(__bfloat162float(Y[p * ldy + offy + c]) > 0.f)) g = __float2bfloat16_rn(0.f);
+  }
+}
+
+// 2x2 average pool (H, W even): out[y][x][c] = mean of the 2x2 block
+__global__ void k_avgpool(int H, int W, int C, const bf16* __restrict__ X, int ldx, int offx, bf16* __restrict__ Y,
+                          int ldy, int offy) {
+  const int H2 = H / 2, W2 = W / 2;
+  long n = (long)H2 * W2 * C;
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    int c = (int)(k % C);
+    long p = k / C;
+    int x = (int)(p % W2), y = (int)(p / W2);
+    auto at = [&](int yy, int xx) { return __bfloat162float(X[((long)yy * W + xx) * ldx + offx + c]); };
+    float v = 0.25f * (at(2 * y, 2 * x) + at(2 * y, 2 * x + 1) + at(2 * y + 1, 2 * x) + at(2 * y + 1, 2 * x + 1));
+    Y[p * ldy + offy + c] = __float2bfloat16_rn(v);
+  }
+}
+
+// gradient of the average pool: dX[2y+a][2x+b][c] (+)= dY[y][x][c] / 4
+__global__ void k_avgpool_grad(int H, int W, int C, const bf16* __restrict__ dY, int ldy, int offy,
+                               bf16* __restrict__ dX, int ldx, int offx, int accumulate) {
+  long n = (long)H * W * C;
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    int c = (int)(k % C);
+    long p = k / C;
+    int x = (int)(p % W), y = (int)(p / W);
+    float g = 0.25f * __bfloat162float(dY[((long)(y / 2) * (W / 2) + x / 2) * ldy + offy + c]);
+    bf16& d = dX[p * ldx + offx + c];
+    d = __float2bfloat16_rn(accumulate ? __bfloat162float(d) + g : g);
+  }
+}
+
+// nearest 2x upsampling of a (H/2 x W/2) map into a (H x W) channel slice
+__global__ void k_upsample(int H, int W, int C, const bf16* __restrict__ X, int ldx, int offx, bf16* __restrict__ Y,
+                           int ldy, int offy) {
+  long n = (long)H * W * C;
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    int c = (int)(k % C);
+    long p = k / C;
+    int x = (int)(p % W), y = (int)(p / W);
+    Y[p * ldy + offy + c] = X[((long)(y / 2) * (W / 2) + x / 2) * ldx + offx + c];
+  }
+}
+
+// gradient of the upsampling: dX[y][x][c] (+)= sum of the 2x2 block of dY
+__global__ void k_upsample_grad(int H, int W, int C, const bf16* __restrict__ dY, int ldy, int offy,
+                                bf16* __restrict__ dX, int ldx, int offx, int accumulate) {
+  const int H2 = H / 2, W2 = W / 2;
+  long n = (long)H2 * W2 * C;
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    int c = (int)(k % C);
+    long p = k / C;
+    int x = (int)(p % W2), y = (int)(p / W2);
+    auto at = [&](int yy, int xx) { return __bfloat162float(dY[((long)yy * W + xx) * ldy + offy + c]); };
+    float g = at(2 * y, 2 * x) + at(2 * y, 2 * x + 1) + at(2 * y + 1, 2 * x) + at(2 * y + 1, 2 * x + 1);
+    bf16& d = dX[p * ldx + offx + c];
+    d = __float2bfloat16_rn(accumulate ? __bfloat162float(d) + g : g);
+  }
+}
+
+// bias gradient: db[c] += sum_p G[p][c] (one block per channel group)
+__global__ void k_bias_grad(long npix, int C, const bf16* __restrict__ G, int ldg, int offg, float* __restrict__ db) {
+  const int c = blockIdx.x;
+  float s = 0.f;
+  for (long p = threadIdx.x + (long)blockIdx.y * blockDim.x; p < npix; p += (long)blockDim.x * gridDim.y)
+    s += __bfloat162float(G[p * ldg + offg + c]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ float ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    atomicAdd(&db[c], t);
+  }
+}
+
+// loss = mean over masked pixels of (out[p][0] - target[p])^2 ; dOut = 2 (out - target) / count
+__global__ void k_mse(long npix, const float* __restrict__ out, int ldo, const float* __restrict__ target,
+                      const float* __restrict__ mask, float inv_count, bf16* __restrict__ dout, int ldd,
+                      double* __restrict__ loss) {
+  double s = 0.0;
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < npix; p += (long)gridDim.x * blockDim.x) {
+    float m = mask ? mask[p] : 1.f;
+    float d = (out[p * ldo] - target[p]) * m;
+    s += (double)d * d;
+    dout[p * ldd] = __float2bfloat16_rn(2.f * d * inv_count);
+    for (int c = 1; c < ldd; ++c) dout[p * ldd + c] = __float2bfloat16_rn(0.f);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, s * inv_count);
+}
+
+// Adam on FP32 master weights, BF16 copy for the kernels
+__global__ void k_adam(long n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, bf16* __restrict__ wb, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    float gk = g[k];
+    float mk = b1 * m[k] + (1.f - b1) * gk, vk = b2 * v[k] + (1.f - b2) * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    float wk = w[k] - lr * (mk * c1) / (sqrtf(vk * c2) + eps);
+    w[k] = wk;
+    if (wb) wb[k] = __float2bfloat16_rn(wk);
+  }
+}
+
+__global__ void k_to_bf16(long n, const float* __restrict__ a, bf16* __restrict__ b) {
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
+    b[k] = __float2bfloat16_rn(a[k]);
+}
+
+// FP32 [H][W][cin] features -> BF16 [H][W][cpad] (zero padded channels)
+__global__ void k_pack_input(long npix, int cin, int cpad, const float* __restrict__ f, bf16* __restrict__ x) {
+  long n = npix * cpad;
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    long p = k / cpad;
+    int c = (int)(k % cpad);
+    x[k] = __float2bfloat16_rn(c < cin ? f[p * cin + c] : 0.f);
+  }
+}
+
+inline int grid1(long n) {
+  long b = (n + 255) / 256;
+  return (int)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
+}
+
+}  // namespace
+
+void conv3x3(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* X, int ldx, int offx, const bf16* Wt,
+             const float* bias, bf16* Y, int ldy, int offy, bool relu, float* yf) {
+  dim3 grd((W + CP - 1) / CP, H, (Cout + CN - 1) / CN);
+  if (relu)
+    k_conv3x3<true><<<grd, 128, 0, s>>>(H, W, Cin, Cout, X, ldx, offx, Wt, bias, Y, ldy, offy, yf);
+  else
+    k_conv3x3<false><<<grd, 128, 0, s>>>(H, W, Cin, Cout, X, ldx, offx, Wt, bias, Y, ldy, offy, yf);
+}
+
+void conv3x3_wgrad(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* G, int ldg, int offg, const bf16* X,
+                   int ldx, int offx, float* dW) {
+  const long nchunks = (long)H * ((W + WP - 1) / WP);
+  dim3 grd((unsigned)((nchunks + WCHUNKS - 1) / WCHUNKS), 9, ((Cout + CN - 1) / CN) * (Cin / WCI));
+  k_conv3x3_wgrad<<<grd, 128, 0, s>>>(H, W, Cin, Cout, G, ldg, offg, X, ldx, offx, dW);
+}
+
+void flip_weights(cudaStream_t s, int Cin, int Cout, const bf16* w, bf16* wt) {
+  k_flip_weights<<<grid1((long)Cin * 9 * Cout), 256, 0, s>>>(Cin, Cout, w, wt);
+}
+void relu_grad(cudaStream_t s, long npix, int C, bf16* G, int ldg, int offg, const bf16* Y, int ldy, int offy) {
+  k_relu_grad<<<grid1(npix * C), 256, 0, s>>>(npix, C, G, ldg, offg, Y, ldy, offy);
+}
+void avgpool(cudaStream_t s, int H, int W, int C, const bf16* X, int ldx, int offx, bf16* Y, int ldy, int offy) {
+  k_avgpool<<<grid1((long)H * W * C / 4), 256, 0, s>>>(H, W, C, X, ldx, offx, Y, ldy, offy);
+}
+void avgpool_grad(cudaStream_t s, int H, int W, int C, const bf16* dY, int ldy, int offy, bf16* dX, int ldx, int offx,
+                  bool acc) {
+  k_avgpool_grad<<<grid1((long)H * W * C), 256, 0, s>>>(H, W, C, dY, ldy, offy, dX, ldx, offx, acc ? 1 : 0);
+}
+void upsample(cudaStream_t s, int H, int W, int C, const bf16* X, int ldx, int offx, bf16* Y, int ldy, int offy) {
+  k_upsample<<<grid1((long)H * W * C), 256, 0, s>>>(H, W, C, X, ldx, offx, Y, ldy, offy);
+}
+void upsample_grad(cudaStream_t s, int H, int W, int C, const bf16* dY, int ldy, int offy, bf16* dX, int ldx, int offx,
+                   bool acc) {
+  k_upsample_grad<<<grid1((long)H * W * C / 4), 256, 0, s>>>(H, W, C, dY, ldy, offy, dX, ldx, offx, acc ? 1 : 0);
+}
+void bias_grad(cudaStream_t s, long npix, int C, const bf16* G, int ldg, int offg, float* db) {
+  dim3 grd(C, 32);
+  k_bias_grad<<<grd, 256, 0, s>>>(npix, C, G, ldg, offg, db);
+}
+void mse(cudaStream_t s, long npix, const float* out, int ldo, const float* target, const float* mask, float inv_count,
+         bf16* dout, int ldd, double* loss) {
+  k_mse<<<grid1(npix), 256, 0, s>>>(npix, out, ldo, target, mask, inv_count, dout, ldd, loss);
+}
+void adam(cudaStream_t s, long n, float* w, const float* g, float* m, float* v, bf16* wb, float lr, float b1, float b2,
+          float eps, float c1, float c2) {
+  k_adam<<<grid1(n), 256, 0, s>>>(n, w, g, m, v, wb, lr, b1, b2, eps, c1, c2);
+}
+void to_bf16(cudaStream_t s, long n, const float* a, bf16* b) { k_to_bf16<<<grid1(n), 256, 0, s>>>(n, a, b); }
+void pack_input(cudaStream_t s, long npix, int cin, int cpad, const float* f, bf16* x) {
+  k_pack_input<<<grid1(npix * cpad), 256, 0, s>>>(npix, cin, cpad, f, x);
+}
+
+}  // namespace nn
+}  // namespace ibm

@@ -8,7 +8,8 @@
 // arithmetic follows the recipe shared with the CPU oracle: reciprocals of
 // the grid spacings, fma chains for the 5-point Laplacian, plain expressions
 // elsewhere (no contraction: the library is built with --fmad=false), and the
-// outflow-flux and body-source sums accumulated sequentially in index order.
+// outflow-flux and body-source sums accumulated in a fixed two-level index
+// order.
 #include "ibm_internal.h"
 
 namespace ibm {
@@ -81,15 +82,30 @@ __global__ void k_outflow_bc(Geo g, const double* __restrict__ u, double* __rest
     uh[at(nx, j, P)] = ub - dt * u_in * (ub - um) * g.idx[nx - 1];
   }
   __syncthreads();
-  // fluxes summed in row order by one thread (the shift feeds back into the
-  // flow, so its rounding is fixed by the order)
+  // fluxes: each thread sums one chunk of 32 rows in row order, then thread 0
+  // sums the chunk sums in order (the shift feeds back into the flow, so the
+  // order of the additions is fixed)
+  __shared__ double part[3][256];
   __shared__ double corr;
+  const int nchunk = (ny + 31) / 32;
+  for (int ch = threadIdx.x; ch < nchunk; ch += blockDim.x) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int j = 32 * ch; j < 32 * ch + 32 && j < ny; ++j) {
+      a += u_in * g.dy[j];
+      b += uh[at(nx, j, P)] * g.dy[j];
+      c += g.dy[j];
+    }
+    part[0][ch] = a;
+    part[1][ch] = b;
+    part[2][ch] = c;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     double qin = 0.0, qout = 0.0, ly = 0.0;
-    for (int j = 0; j < ny; ++j) {
-      qin += u_in * g.dy[j];
-      qout += uh[at(nx, j, P)] * g.dy[j];
-      ly += g.dy[j];
+    for (int ch = 0; ch < nchunk; ++ch) {
+      qin += part[0][ch];
+      qout += part[1][ch];
+      ly += part[2][ch];
     }
     corr = (qin - qout) / ly;
   }
@@ -279,20 +295,31 @@ __device__ inline double cell_div(const Geo& g, const double* uh, const double* 
   return (uh[c + 1] - uh[c]) * g.idx[i] + (vh[c + g.pitch] - vh[c]) * g.idy[j];
 }
 
-// sum of D V and of V over body cells, accumulated by one thread in row-major
-// order (the mean feeds back into the flow, so its rounding is fixed)
+// sum of D V and of V over body cells: one thread per band row sums along
+// the row in order, then one thread sums the row sums in order (the mean
+// feeds back into the flow, so the order of the additions is fixed)
 __global__ void k_body_sums(Geo g, Band B, const uint8_t* __restrict__ fc, const double* __restrict__ uh,
-                            const double* __restrict__ vh, DevScalars* sc) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double sdv = 0.0, sv = 0.0;
-  for (int bj = 0; bj < B.h; ++bj)
+                            const double* __restrict__ vh, double* __restrict__ rowsum, DevScalars* sc) {
+  for (int bj = threadIdx.x; bj < B.h; bj += blockDim.x) {
+    double a = 0.0, b = 0.0;
+    const int j = B.j0 + bj;
     for (int bi = 0; bi < B.w; ++bi) {
       if (!fc[bj * B.w + bi]) continue;
-      int i = B.i0 + bi, j = B.j0 + bj;
+      int i = B.i0 + bi;
       double V = g.dx[i] * g.dy[j];
-      sdv += cell_div(g, uh, vh, i, j) * V;
-      sv += V;
+      a += cell_div(g, uh, vh, i, j) * V;
+      b += V;
     }
+    rowsum[2 * bj] = a;
+    rowsum[2 * bj + 1] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double sdv = 0.0, sv = 0.0;
+  for (int bj = 0; bj < B.h; ++bj) {
+    sdv += rowsum[2 * bj];
+    sv += rowsum[2 * bj + 1];
+  }
   sc->body_sum[0] = sdv;
   sc->body_sum[1] = sv;
   sc->cbar = sv > 0.0 ? sdv / sv : 0.0;
@@ -465,10 +492,9 @@ void launch_rhs(cudaStream_t s, const Geo& g, const double* uh, const double* vh
 }
 
 void launch_body_source(cudaStream_t s, const Geo& g, const Band& band, const uint8_t* fc, const double* uh,
-                        const double* vh, double* b, double* qband, double dt, double* partials,
+                        const double* vh, double* b, double* qband, double dt, double* rowsum,
                         DevScalars* sc) {
-  (void)partials;
-  k_body_sums<<<1, 32, 0, s>>>(g, band, fc, uh, vh, sc);
+  k_body_sums<<<1, 1024, 0, s>>>(g, band, fc, uh, vh, rowsum, sc);
   k_body_fix<<<grid2(band.w, band.h), dim3(TBX, TBY), 0, s>>>(g, band, fc, uh, vh, b, qband, 1.0 / dt, sc);
 }
 

@@ -1,0 +1,125 @@
+// Learned warm start of the pressure solve: features for the U-Net, the
+// prolongation of its prediction onto the pressure increment, and the
+// training targets.
+//
+// The network works on the grid coarsened 2x in each direction (coarse cell
+// (I, J) = fine cells 2I..2I+1 x 2J..2J+1): SOR removes the rough part of an
+// error in a few sweeps, so only the smooth part of the increment is worth
+// predicting, and the coarse grid doubles the network's reach.  Features of a
+// coarse cell (averages over its four fine cells):
+//   0  r0 = b - L_p phi^n   (initial residual of the solve)
+//   1  b                    (right-hand side)
+//   2  fraction of body cells
+//   3  p^n                  (pressure)
+// each divided by its infinity norm over the grid (scale invariance).  The
+// network predicts (phi^{n+1} - phi^n) / (s0 c_T), s0 = ||r0||_inf, c_T a
+// constant of the trained model.
+#include "ibm_internal.h"
+
+namespace ibm {
+
+namespace {
+
+__device__ inline void atomic_max_abs(unsigned long long* dst, double v) {
+  atomicMax(dst, (unsigned long long)__double_as_longlong(fabs(v)));
+}
+
+__device__ inline double lap_p(const Geo& g, const double* f, int i, int j) {
+  const int P = g.pitch;
+  size_t c = at(i, j, P);
+  double x = f[c];
+  double L = g.pE[i] * (f[c + 1] - x);
+  L = fma(g.pW[i], f[c - 1] - x, L);
+  L = fma(g.pN[j], f[c + P] - x, L);
+  L = fma(g.pS[j], f[c - P] - x, L);
+  return L;
+}
+
+// raw coarse features and their maxima (ws_max[0..3], bit patterns)
+__global__ void k_ws_features(Geo g, int Hc, int Wc, const double* __restrict__ b, const double* __restrict__ phi,
+                              const double* __restrict__ p, Band B, const uint8_t* __restrict__ fc,
+                              float* __restrict__ feat, unsigned long long* __restrict__ ws_max) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= Wc || J >= Hc) return;
+  double r0 = 0.0, bb = 0.0, body = 0.0, pp = 0.0;
+  for (int a = 0; a < 2; ++a)
+    for (int c2 = 0; c2 < 2; ++c2) {
+      int i = 2 * I + a, j = 2 * J + c2;
+      size_t c = at(i, j, g.pitch);
+      r0 += b[c] - lap_p(g, phi, i, j);
+      bb += b[c];
+      pp += p[c];
+      int bi = i - B.i0, bj = j - B.j0;
+      if (bi >= 0 && bj >= 0 && bi < B.w && bj < B.h && fc[bj * B.w + bi]) body += 1.0;
+    }
+  float* f = feat + ((size_t)J * Wc + I) * 4;
+  f[0] = (float)(0.25 * r0);
+  f[1] = (float)(0.25 * bb);
+  f[2] = (float)(0.25 * body);
+  f[3] = (float)(0.25 * pp);
+  atomic_max_abs(&ws_max[0], 0.25 * r0);
+  atomic_max_abs(&ws_max[1], 0.25 * bb);
+  atomic_max_abs(&ws_max[3], 0.25 * pp);
+}
+
+__device__ inline double bits2d(unsigned long long u) { return __longlong_as_double((long long)u); }
+
+__global__ void k_ws_normalize(long n, float* __restrict__ feat, const unsigned long long* __restrict__ ws_max) {
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    int ch = (int)(k & 3);
+    if (ch == 2) continue;
+    double s = bits2d(ws_max[ch]);
+    feat[k] = s > 0.0 ? (float)(feat[k] / s) : 0.f;
+  }
+}
+
+// phi (fine) += s0 * cT * out (coarse), piecewise constant over each coarse cell
+__global__ void k_ws_apply(Geo g, int Hc, int Wc, const float* __restrict__ out, double cT,
+                           const unsigned long long* __restrict__ ws_max, double* __restrict__ phi) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= 2 * Wc || j >= 2 * Hc) return;
+  const double s0 = bits2d(ws_max[0]);
+  phi[at(i, j, g.pitch)] += s0 * cT * (double)out[(size_t)(j >> 1) * Wc + (i >> 1)];
+}
+
+// training target: coarse average of (phi_new - phi_ref) - phi_old, over s0 cT
+__global__ void k_ws_target(Geo g, int Hc, int Wc, const double* __restrict__ phi_new,
+                            const double* __restrict__ phi_old, const DevScalars* __restrict__ sc, double cT,
+                            const unsigned long long* __restrict__ ws_max, float* __restrict__ target) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= Wc || J >= Hc) return;
+  const double ref = sc->phi_ref, s0 = bits2d(ws_max[0]);
+  double d = 0.0;
+  for (int a = 0; a < 2; ++a)
+    for (int c2 = 0; c2 < 2; ++c2) {
+      size_t c = at(2 * I + a, 2 * J + c2, g.pitch);
+      d += (phi_new[c] - ref) - phi_old[c];
+    }
+  target[(size_t)J * Wc + I] = s0 > 0.0 ? (float)(0.25 * d / (s0 * cT)) : 0.f;
+}
+
+}  // namespace
+
+void launch_ws_features(cudaStream_t s, const Geo& g, int Hc, int Wc, const double* b, const double* phi,
+                        const double* p, const Band& band, const uint8_t* fc, float* feat,
+                        unsigned long long* ws_max) {
+  cudaMemsetAsync(ws_max, 0, 4 * sizeof(unsigned long long), s);
+  dim3 blk(32, 8), grd((Wc + 31) / 32, (Hc + 7) / 8);
+  k_ws_features<<<grd, blk, 0, s>>>(g, Hc, Wc, b, phi, p, band, fc, feat, ws_max);
+  long n = (long)Hc * Wc * 4;
+  k_ws_normalize<<<(unsigned)((n + 255) / 256 > 4096 ? 4096 : (n + 255) / 256), 256, 0, s>>>(n, feat, ws_max);
+}
+
+void launch_ws_apply(cudaStream_t s, const Geo& g, int Hc, int Wc, const float* out, double cT,
+                     const unsigned long long* ws_max, double* phi) {
+  dim3 blk(32, 8), grd((2 * Wc + 31) / 32, (2 * Hc + 7) / 8);
+  k_ws_apply<<<grd, blk, 0, s>>>(g, Hc, Wc, out, cT, ws_max, phi);
+}
+
+void launch_ws_target(cudaStream_t s, const Geo& g, int Hc, int Wc, const double* phi_new, const double* phi_old,
+                      const DevScalars* sc, double cT, const unsigned long long* ws_max, float* target) {
+  dim3 blk(32, 8), grd((Wc + 31) / 32, (Hc + 7) / 8);
+  k_ws_target<<<grd, blk, 0, s>>>(g, Hc, Wc, phi_new, phi_old, sc, cT, ws_max, target);
+}
+
+}  // namespace ibm

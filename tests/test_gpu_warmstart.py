@@ -1,0 +1,66 @@
+"""Learned warm start: the recorded training samples against a recomputation
+from the solver's fields, and what a trained network gains over the plain
+warm start (previous increment) on held-out steps."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_17337_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def small_cfg():
+    return W.FlowConfig("plunge_256x128", -7.5, 24.0, -12.5, 12.5, 256, 128, 0.04, Re=500.0, dt=0.01, steps=60,
+                        h=0.25, k=2.0, div_tol=1e-8, init="uniform", check_p=8)
+
+
+def coarse(a):
+    return 0.25 * (a[0::2, 0::2] + a[0::2, 1::2] + a[1::2, 0::2] + a[1::2, 1::2])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_samples_match_recomputation_from_fields(precision):
+    import paper_2402_17337_gb300 as ibm
+    from paper_2402_17337_gb300 import build
+    build.build()
+    cfg = small_cfg()
+    s = ibm.Solver.from_config(cfg, precision=precision)
+    s.set("u", cfg.initial_u(s.shape("u")))
+    s.set_warmstart(2, None, 1.0)
+    s.step(4)
+    phi_n, p_n = s.get("phi"), s.get("p")
+    s.step(1)
+    b, phi_1 = s.get("b"), s.get("phi")
+    body = s.flags(2).astype(np.float64)
+    f, t = s.sample()
+    o = oracle.Sim(x0=cfg.x0, x1=cfg.x1, y0=cfg.y0, y1=cfg.y1, nx=cfg.nx, ny=cfg.ny, hmin=cfg.hmin,
+                   ubox=cfg.ubox, dt=cfg.dt)
+    r0 = b - o.lap_p(phi_n)
+    feats = [coarse(r0), coarse(b), coarse(body), coarse(p_n)]
+    for ch in (0, 1, 3):
+        feats[ch] = feats[ch] / np.abs(feats[ch]).max()
+    for ch in range(4):
+        np.testing.assert_allclose(f[..., ch], feats[ch], rtol=0, atol=1e-5 * max(1.0, np.abs(feats[ch]).max()))
+    s0 = np.abs(coarse(r0)).max()
+    ref = coarse(phi_1 - phi_n) / s0
+    np.testing.assert_allclose(t, ref, rtol=0, atol=1e-5 * np.abs(ref).max())
+
+
+def test_trained_network_gain_over_plain_warm_start():
+    """Trains a small U-Net on samples of steps 5..44 and compares pressure
+    sweeps with the plain warm start on steps 45..59 (held out)."""
+    import paper_2402_17337_gb300 as ibm
+    from paper_2402_17337_gb300 import build, warmstart
+    build.build()
+    cfg = small_cfg()
+    samples = warmstart.capture(cfg, steps=45, start=5, every=1)
+    net = ibm.UNet((16, 32, 32, 48), seed=1)
+    cT, hist = warmstart.train(net, samples, epochs=30, lr=2e-3)
+    assert hist[-1] < 0.5 * hist[0], hist
+    res = warmstart.evaluate(cfg, net, cT, steps=15, start=45)
+    plain, learned = sum(res["plain"]["sweeps"]), sum(res["learned"]["sweeps"])
+    print(f"held-out pressure sweeps: plain {plain}, learned {learned}, gain {1 - learned / plain:+.1%}; "
+          f"loss {hist[0]:.3e} -> {hist[-1]:.3e}")
+    # the learned start must not cost sweeps on the held-out steps
+    assert learned <= 1.02 * plain, res
