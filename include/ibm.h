@@ -265,6 +265,49 @@ int ibm_set_warmstart(ibm_ctx* ctx, int mode, ibm_unet* net, double target_scale
  * (host, FP32); either may be NULL; *Hc, *Wc receive the coarse sizes. */
 int ibm_get_sample(const ibm_ctx* ctx, float* feat, float* target, int* Hc, int* Wc);
 
+/* ---------------------------------------------------------------- batch
+ * Many independent cases (each a context of its own grid, body and
+ * parameters, precision 1) advancing together; the paper runs one case at
+ * a time, and this batching of cases has no counterpart in it.  Each step
+ * of the batch is one step (Sec. 2.2) of every case: the parts before and
+ * after the pressure solve run case by case, and the pressure solves of
+ * all cases run as one defect-correction loop whose FP32 sweep launches and
+ * FP64 residual launches each cover every case that has not converged yet
+ * (cases leave the launches as they reach their tolerance).  The tile
+ * shape is chosen for the whole batch by the autotuner on the first step;
+ * sweep launches are replayed from CUDA graphs (ibm_batch_set_graphs).
+ *
+ * The contexts are borrowed: they must outlive the batch and must not be
+ * used by other calls while ibm_batch_step runs.  The batch owns a stream
+ * of its own; a step waits for the work queued on the cases' streams and
+ * the cases' streams wait for the step.  Between batch steps a case may be
+ * read (ibm_get_field, ibm_forces) or stepped alone. */
+typedef struct ibm_batch ibm_batch;
+
+/* cases: n distinct contexts of precision 1.  IBM_E_INVAL otherwise. */
+int ibm_batch_create(ibm_ctx* const* cases, int n, ibm_batch** out);
+
+/* Advances every case by nsteps.  last (may be NULL): n entries receiving
+ * the statistics of each case's last step.  On an error the message names
+ * the case; the cases are then in an unspecified state. */
+int ibm_batch_step(ibm_batch* batch, int nsteps, ibm_step_stats* last);
+
+/* CUDA-graph replay of the sweep launches: on (1, the default) or off (0). */
+int ibm_batch_set_graphs(ibm_batch* batch, int on);
+
+/* Profiling of the batch (event timing of its sweep runs; counters of the
+ * batch and of its cases are reset). */
+int ibm_batch_set_profiling(ibm_batch* batch, int on);
+
+/* Counters: launches (the batch's and its cases'), sweep launches and time
+ * of the batched runs, steps, pressure sweeps summed over cases, velocity
+ * sweeps summed over cases, the batch's tile shape and time per sweep of
+ * the whole batch. */
+int ibm_batch_get_profile(const ibm_batch* batch, ibm_profile* out);
+
+/* Frees the batch (not its cases). */
+void ibm_batch_destroy(ibm_batch* batch);
+
 /* Frees the context and its device memory. */
 void ibm_destroy(ibm_ctx* ctx);
 

@@ -98,6 +98,13 @@ def lib():
             L.ibm_set_warmstart.argtypes = [_VP, C.c_int, _VP, C.c_double]
             L.ibm_get_sample.argtypes = [_VP, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_int),
                                          C.POINTER(C.c_int)]
+            L.ibm_batch_create.argtypes = [C.POINTER(_VP), C.c_int, C.POINTER(_VP)]
+            L.ibm_batch_step.argtypes = [_VP, C.c_int, C.POINTER(StepStats)]
+            L.ibm_batch_set_graphs.argtypes = [_VP, C.c_int]
+            L.ibm_batch_set_profiling.argtypes = [_VP, C.c_int]
+            L.ibm_batch_get_profile.argtypes = [_VP, C.POINTER(Profile)]
+            L.ibm_batch_destroy.argtypes = [_VP]
+            L.ibm_batch_destroy.restype = None
             L.ibm_destroy.argtypes = [_VP]
             L.ibm_destroy.restype = None
             L.ibm_last_error.restype = C.c_char_p
@@ -248,6 +255,48 @@ class Solver:
         rc = lib().ibm_poisson_solve(self._h, b_ptr, phi_ptr, tol, check_every, max_sweeps, C.byref(s),
                                      C.byref(r))
         return rc, s.value, r.value
+
+
+class Batch:
+    """Many Solver cases (precision 1) advanced together; the pressure solves
+    of all cases share every sweep launch.  The solvers are borrowed and
+    kept alive by the batch."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        arr = (_VP * len(self.solvers))(*[s._h for s in self.solvers])
+        h = _VP()
+        _check(lib().ibm_batch_create(arr, len(self.solvers), C.byref(h)))
+        self._h = h
+
+    def step(self, n=1):
+        """Advances every case by n steps; returns each case's last-step stats."""
+        st = (StepStats * len(self.solvers))()
+        _check(lib().ibm_batch_step(self._h, n, st))
+        return [x.as_dict() for x in st]
+
+    def set_graphs(self, on=True):
+        _check(lib().ibm_batch_set_graphs(self._h, 1 if on else 0))
+
+    def set_profiling(self, on=True):
+        _check(lib().ibm_batch_set_profiling(self._h, 1 if on else 0))
+
+    def profile(self):
+        p = Profile()
+        _check(lib().ibm_batch_get_profile(self._h, C.byref(p)))
+        return p.as_dict()
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().ibm_batch_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class UNet:

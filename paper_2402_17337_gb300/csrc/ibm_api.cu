@@ -4,8 +4,11 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/ibm.h"
@@ -553,13 +556,15 @@ int solve_helm(ibm_ctx* c, int grid, double beta, double Ub, int* sweeps, double
   }
 }
 
-int one_step(ibm_ctx* c) {
+// Part of a step before the pressure solve (a1-a7); *thr receives the
+// pressure tolerance of the step.
+int step_pre(ibm_ctx* c, ibm_step_stats* st, double* thr) {
   const Geo& g = c->geo;
   const ibm_grid_params& P = c->P;
   const double dt = P.dt, beta = dt / (2.0 * P.Re);
   const double t1 = (c->n + 1) * dt;
   double yb = c->yb0, vb = 0.0;
-  ibm_step_stats st{};
+  *st = ibm_step_stats{};
   int rc = ensure_history(c, c->n + 1);
   if (rc) return rc;
   // a1: kinematics at t^{n+1} (Eqs. 1-2)
@@ -569,8 +574,8 @@ int one_step(ibm_ctx* c) {
     // a2/a3: classification and forcing data
     launch_classify(c->stream, g, c->band, c->xb, yb, 0.5 * c->chord, 0.5 * c->tc * c->chord, c->fu, c->fv,
                     c->fc, c->au, c->av);
+    c->prof.launches += 3;
   }
-  if (c->has_body) c->prof.launches += 3;
   // boundary values of the intermediate velocity at t^{n+1}
   if (P.bc == 0) {
     launch_outflow_bc(c->stream, g, c->u, c->uh, c->vh, P.u_in, dt);
@@ -581,9 +586,9 @@ int one_step(ibm_ctx* c) {
                  c->band, c->fu, c->fv, dt, beta, vb, c->n == 0 ? 1 : 0);
   c->prof.launches += 2;
   // a5: implicit velocity solves
-  rc = solve_helm(c, 0, beta, 0.0, &st.sweeps_u, &st.res_u);
+  rc = solve_helm(c, 0, beta, 0.0, &st->sweeps_u, &st->res_u);
   if (rc) return rc;
-  rc = solve_helm(c, 1, beta, vb, &st.sweeps_v, &st.res_v);
+  rc = solve_helm(c, 1, beta, vb, &st->sweeps_v, &st->res_v);
   if (rc) return rc;
   // a6: right-hand side with the mass source on body cells
   launch_rhs(c->stream, g, c->uh, c->vh, c->b, dt);
@@ -592,7 +597,6 @@ int one_step(ibm_ctx* c) {
     launch_body_source(c->stream, g, c->band, c->fc, c->uh, c->vh, c->b, c->qband, dt, c->rowsum, c->sc);
     c->prof.launches += 3;
   }
-  // a7/a8: pressure solve warm-started from the previous increment
   // a7: warm start.  The solve starts from the previous increment; the
   // learned form adds the U-Net's prediction of the change.
   if (c->ws_mode) {
@@ -607,21 +611,24 @@ int one_step(ibm_ctx* c) {
       c->prof.launches += 16;
     }
   }
-  if (P.precision == 1) {
-    double thr = P.poisson_tol;
-    if (P.poisson_rtol > 0.0) {
-      CUDA_TRY(cudaMemsetAsync(&c->sc->bmax_bits, 0, 8, c->stream));
-      launch_bmax(c->stream, g, c->b, &c->sc->bmax_bits);
-      double bmax;
-      rc = read_norm(c, &c->sc->bmax_bits, &bmax);
-      if (rc) return rc;
-      thr = std::fmax(thr, P.poisson_rtol * bmax);
-    }
-    rc = solve_poisson_mixed(c, thr, P.max_sweeps, &st.sweeps_p, &st.res_p);
-  } else {
-    rc = solve_poisson(c, P.poisson_tol, P.poisson_rtol, P.check_every_p, P.max_sweeps, &st.sweeps_p, &st.res_p);
+  *thr = P.poisson_tol;
+  if (P.poisson_rtol > 0.0) {
+    CUDA_TRY(cudaMemsetAsync(&c->sc->bmax_bits, 0, 8, c->stream));
+    launch_bmax(c->stream, g, c->b, &c->sc->bmax_bits);
+    double bmax;
+    rc = read_norm(c, &c->sc->bmax_bits, &bmax);
+    if (rc) return rc;
+    *thr = std::fmax(*thr, P.poisson_rtol * bmax);
   }
-  if (rc) return rc;
+  return IBM_OK;
+}
+
+// Part of a step after the pressure solve (a9-a11): samples, forces,
+// projection, divergence, statistics.
+int step_post(ibm_ctx* c, ibm_step_stats* st) {
+  const Geo& g = c->geo;
+  const ibm_grid_params& P = c->P;
+  const double dt = P.dt, beta = dt / (2.0 * P.Re);
   if (c->ws_mode == 2) {
     launch_phi_ref(c->stream, g, c->phi, c->sc);
     launch_ws_target(c->stream, g, c->Hc, c->Wc, c->phi, c->phi_old, c->sc, c->ws_cT, c->ws_max, c->ws_target);
@@ -654,16 +661,319 @@ int one_step(ibm_ctx* c) {
   std::swap(c->Hv, c->Hvo);
   c->n += 1;
   c->prof.steps += 1;
-  c->prof.poisson_sweeps += st.sweeps_p;
-  c->prof.helm_sweeps += st.sweeps_u + st.sweeps_v;
-  st.n = c->n;
-  st.t = c->n * dt;
-  st.div_max = bits_to_double(c->sc_host->div_bits);
-  st.cl = clcd[0];
-  st.cd = clcd[1];
-  c->last = st;
+  c->prof.poisson_sweeps += st->sweeps_p;
+  c->prof.helm_sweeps += st->sweeps_u + st->sweeps_v;
+  st->n = c->n;
+  st->t = c->n * dt;
+  st->div_max = bits_to_double(c->sc_host->div_bits);
+  st->cl = clcd[0];
+  st->cd = clcd[1];
+  c->last = *st;
   return IBM_OK;
 }
+
+int one_step(ibm_ctx* c) {
+  ibm_step_stats st;
+  double thr;
+  int rc = step_pre(c, &st, &thr);
+  if (rc) return rc;
+  if (c->P.precision == 1)
+    rc = solve_poisson_mixed(c, thr, c->P.max_sweeps, &st.sweeps_p, &st.res_p);
+  else
+    rc = solve_poisson(c, c->P.poisson_tol, c->P.poisson_rtol, c->P.check_every_p, c->P.max_sweeps, &st.sweeps_p,
+                       &st.res_p);
+  if (rc) return rc;
+  return step_post(c, &st);
+}
+
+
+}  // namespace
+
+// ------------------------------------------------------------------ batch
+// Many cases advance together.  Per case, the parts of a step before and
+// after the pressure solve run as for a single context (on the batch's
+// stream); the pressure solves of all cases run as one defect-correction
+// loop in which every FP32 sweep launch and every FP64 residual launch
+// covers the tiles of all cases that have not converged yet.  Cases leave
+// the launches as they converge.  Inner sweeps run in pairs of launches
+// (e32 -> e32b -> e32), so each case's correction always ends in e32; the
+// pairs are replayed from CUDA graphs captured per active set.
+struct ibm_batch {
+  std::vector<ibm_ctx*> cs;
+  cudaStream_t stream = nullptr;
+  int cfg = -1;
+  double sor_us = 0.0;
+  bool use_graphs = true;
+  bool profiling = false;
+  Sor32Case *h_sor = nullptr, *d_sor = nullptr;  // tables A (e32 -> e32b) at [0, n), B (e32b -> e32) at [n, 2n)
+  DcCase *h_dc = nullptr, *d_dc = nullptr;
+  unsigned long long *h_bits = nullptr, *d_bits = nullptr;
+  std::vector<cudaEvent_t> ev;
+  cudaEvent_t ev_b = nullptr, t0 = nullptr, t1 = nullptr;
+  struct Graphs {
+    cudaGraphExec_t first = nullptr, pair = nullptr, many = nullptr;
+  };
+  std::map<std::pair<int, int>, Graphs> graphs;
+  ibm_profile prof{};
+
+  void drop_graphs() {
+    for (auto& kv : graphs) {
+      if (kv.second.first) cudaGraphExecDestroy(kv.second.first);
+      if (kv.second.pair) cudaGraphExecDestroy(kv.second.pair);
+      if (kv.second.many) cudaGraphExecDestroy(kv.second.many);
+    }
+    graphs.clear();
+  }
+  ~ibm_batch() {
+    drop_graphs();
+    if (h_sor) cudaFreeHost(h_sor);
+    if (h_dc) cudaFreeHost(h_dc);
+    if (h_bits) cudaFreeHost(h_bits);
+    if (d_sor) cudaFree(d_sor);
+    if (d_dc) cudaFree(d_dc);
+    if (d_bits) cudaFree(d_bits);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    if (ev_b) cudaEventDestroy(ev_b);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+constexpr int kPairsPerGraph = 8;
+
+// Sweep tables of the cases act[0..na) for tile shape cfg; *tiles receives
+// the CTAs of one launch.  Copied to the device on the batch's stream.
+int batch_sor_tables(ibm_batch* B, int cfg, const std::vector<int>& act, int* tiles) {
+  const int n = (int)B->cs.size(), na = (int)act.size();
+  int first = 0;
+  for (int k = 0; k < na; ++k) {
+    ibm_ctx* c = B->cs[act[k]];
+    int tx = 0, ty = 0;
+    sor32_tiles(cfg, c->geo32, &tx, &ty);
+    const float om = (float)c->P.omega_p;
+    B->h_sor[k] = Sor32Case{c->geo32, c->e32, c->e32b, c->r32, c->invd32, om, first, tx};
+    B->h_sor[n + k] = Sor32Case{c->geo32, c->e32b, c->e32, c->r32, c->invd32, om, first, tx};
+    first += tx * ty;
+  }
+  *tiles = first;
+  CUDA_TRY(cudaMemcpyAsync(B->d_sor, B->h_sor, 2 * n * sizeof(Sor32Case), cudaMemcpyHostToDevice, B->stream));
+  return IBM_OK;
+}
+
+void batch_launch_pair(ibm_batch* B, int na, int tiles, int zero_first) {
+  const int n = (int)B->cs.size();
+  launch_sor32_batch(B->stream, B->cfg, B->d_sor, na, tiles, zero_first);
+  launch_sor32_batch(B->stream, B->cfg, B->d_sor + n, na, tiles, 0);
+}
+
+int batch_capture(ibm_batch* B, int na, int tiles, int pairs, int zero_first, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+  for (int q = 0; q < pairs; ++q) batch_launch_pair(B, na, tiles, q == 0 ? zero_first : 0);
+  CUDA_TRY(cudaStreamEndCapture(B->stream, &g));
+  cudaError_t e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(IBM_E_CUDA, "graph instantiation: %s", cudaGetErrorString(e));
+  return IBM_OK;
+}
+
+// `pairs` launch pairs over the active set (tables already on the device),
+// the first one starting from e = 0.
+int batch_sweeps(ibm_batch* B, int na, int tiles, int pairs) {
+  B->prof.launches += 2 * pairs;
+  if (!B->use_graphs) {
+    for (int q = 0; q < pairs; ++q) batch_launch_pair(B, na, tiles, q == 0);
+    CUDA_TRY(cudaGetLastError());
+    return IBM_OK;
+  }
+  auto key = std::make_pair(na, tiles);
+  auto it = B->graphs.find(key);
+  if (it == B->graphs.end()) {
+    if (B->graphs.size() >= 512) B->drop_graphs();
+    ibm_batch::Graphs G;
+    int rc = batch_capture(B, na, tiles, 1, 1, &G.first);
+    if (!rc) rc = batch_capture(B, na, tiles, 1, 0, &G.pair);
+    if (!rc) rc = batch_capture(B, na, tiles, kPairsPerGraph, 0, &G.many);
+    if (rc) {
+      if (G.first) cudaGraphExecDestroy(G.first);
+      if (G.pair) cudaGraphExecDestroy(G.pair);
+      return rc;
+    }
+    it = B->graphs.emplace(key, G).first;
+  }
+  const ibm_batch::Graphs& G = it->second;
+  CUDA_TRY(cudaGraphLaunch(G.first, B->stream));
+  int rem = pairs - 1;
+  for (; rem >= kPairsPerGraph; rem -= kPairsPerGraph) CUDA_TRY(cudaGraphLaunch(G.many, B->stream));
+  for (; rem > 0; --rem) CUDA_TRY(cudaGraphLaunch(G.pair, B->stream));
+  return IBM_OK;
+}
+
+// Common tile shape of the batch: every shape timed over all cases.
+int batch_tune(ibm_batch* B) {
+  const int n = (int)B->cs.size();
+  std::vector<int> all(n);
+  for (int i = 0; i < n; ++i) all[i] = i;
+  double best = 1e300;
+  int best_cfg = 0;
+  const bool graphs = B->use_graphs;
+  B->use_graphs = false;
+  for (int cfg = 0; cfg < sor32_num_configs(); ++cfg) {
+    CUDA_TRY(sor32_batch_prepare(cfg));
+    B->cfg = cfg;
+    int tiles = 0;
+    int rc = batch_sor_tables(B, cfg, all, &tiles);
+    if (!rc) rc = batch_sweeps(B, n, tiles, 1);
+    CUDA_TRY(cudaEventRecord(B->t0, B->stream));
+    const int pairs = 3;
+    if (!rc) rc = batch_sweeps(B, n, tiles, pairs);
+    if (rc) {
+      B->use_graphs = graphs;
+      return rc;
+    }
+    CUDA_TRY(cudaEventRecord(B->t1, B->stream));
+    CUDA_TRY(cudaEventSynchronize(B->t1));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, B->t0, B->t1));
+    const double us = 1e3 * ms / (2 * pairs * (sor32_half_sweeps(cfg) / 2));
+    if (us < best) {
+      best = us;
+      best_cfg = cfg;
+    }
+  }
+  B->use_graphs = graphs;
+  B->cfg = best_cfg;
+  B->sor_us = best;
+  B->drop_graphs();
+  return IBM_OK;
+}
+
+// Pressure solves of all cases (defect correction, as solve_poisson_mixed,
+// with one check of every active case per round).  thr: tolerance per case.
+int batch_solve(ibm_batch* B, const std::vector<double>& thr, std::vector<ibm_step_stats>& st) {
+  const int n = (int)B->cs.size();
+  if (B->cfg < 0) {
+    int rc = batch_tune(B);
+    if (rc) return rc;
+  }
+  const int pair_sweeps = sor32_half_sweeps(B->cfg);  // full sweeps of one launch pair
+  struct State {
+    double *cur, *alt;
+    int s = 0, add = 0, inner = 0;
+    double prev = 0.0;
+  };
+  std::vector<State> S(n);
+  std::vector<int> act(n), next;
+  for (int i = 0; i < n; ++i) {
+    S[i].cur = B->cs[i]->phi;
+    S[i].alt = B->cs[i]->phi2;
+    act[i] = i;
+  }
+  std::vector<int> want(n, 0);
+  bool timing = false;
+  while (!act.empty()) {
+    // FP64 update + residual of every active case
+    const int na = (int)act.size();
+    int first = 0;
+    for (int k = 0; k < na; ++k) {
+      const int i = act[k];
+      ibm_ctx* c = B->cs[i];
+      B->h_dc[k] = DcCase{c->geo, c->geo32.pk, S[i].add, first, S[i].cur, S[i].alt, c->e32, c->b, c->r32,
+                          B->d_bits + k};
+      first += ((c->nx + 31) / 32) * ((c->ny + 7) / 8);
+    }
+    if (timing) CUDA_TRY(cudaEventRecord(B->t1, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(B->d_dc, B->h_dc, na * sizeof(DcCase), cudaMemcpyHostToDevice, B->stream));
+    CUDA_TRY(cudaMemsetAsync(B->d_bits, 0, na * sizeof(unsigned long long), B->stream));
+    launch_dc_residual_batch(B->stream, B->d_dc, na, first);
+    B->prof.launches += 1;
+    CUDA_TRY(cudaMemcpyAsync(B->h_bits, B->d_bits, na * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                             B->stream));
+    CUDA_TRY(cudaStreamSynchronize(B->stream));
+    CUDA_TRY(cudaGetLastError());
+    if (timing) {
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, B->t0, B->t1));
+      B->prof.sweep_ms += ms;
+      timing = false;
+    }
+    next.clear();
+    int round = 1 << 30;
+    for (int k = 0; k < na; ++k) {
+      const int i = act[k];
+      ibm_ctx* c = B->cs[i];
+      State& q = S[i];
+      if (q.add) std::swap(q.cur, q.alt);
+      const double r = bits_to_double(B->h_bits[k]);
+      st[i].sweeps_p = q.s;
+      st[i].res_p = r;
+      c->phi = q.cur;
+      c->phi2 = q.alt;
+      if (!std::isfinite(r))
+        return fail(IBM_E_DIVERGED, "batch case %d: pressure residual is not finite after %d sweeps", i, q.s);
+      if (r <= thr[i]) continue;
+      if (q.s >= c->P.max_sweeps)
+        return fail(IBM_E_NOCONV, "batch case %d: pressure solve: %d sweeps, residual %.3e > %.3e", i, q.s, r,
+                    thr[i]);
+      if (q.inner > 0 && q.prev > r && r > 0.0) {
+        const double rate = std::log(r / q.prev) / q.inner;
+        const int m = (int)(0.7 * std::log(thr[i] / r) / rate);
+        c->m_inner = m < 16 ? 16 : (m > 1024 ? 1024 : m);
+      }
+      int w = (c->m_inner + pair_sweeps - 1) / pair_sweeps * pair_sweeps;
+      const int left = (c->P.max_sweeps - q.s + pair_sweeps - 1) / pair_sweeps * pair_sweeps;
+      want[i] = w < left ? w : left;
+      round = std::min(round, want[i]);
+      q.prev = r;
+      next.push_back(i);
+    }
+    act.swap(next);
+    if (act.empty()) break;
+    // FP32 sweeps of every active case
+    int tiles = 0;
+    int rc = batch_sor_tables(B, B->cfg, act, &tiles);
+    if (rc) return rc;
+    if (B->profiling) {
+      CUDA_TRY(cudaEventRecord(B->t0, B->stream));
+      timing = true;
+      B->prof.sweep_launches += 2 * (round / pair_sweeps);
+    }
+    rc = batch_sweeps(B, (int)act.size(), tiles, round / pair_sweeps);
+    if (rc) return rc;
+    for (int i : act) {
+      S[i].s += round;
+      S[i].add = 1;
+      S[i].inner = round;
+    }
+  }
+  for (int i = 0; i < n; ++i) B->prof.poisson_sweeps += st[i].sweeps_p;
+  return IBM_OK;
+}
+
+int batch_one_step(ibm_batch* B) {
+  const int n = (int)B->cs.size();
+  std::vector<ibm_step_stats> st(n);
+  std::vector<double> thr(n);
+  for (int i = 0; i < n; ++i) {
+    int rc = step_pre(B->cs[i], &st[i], &thr[i]);
+    if (rc) return rc;
+  }
+  int rc = batch_solve(B, thr, st);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    rc = step_post(B->cs[i], &st[i]);
+    if (rc) return rc;
+  }
+  B->prof.steps += 1;
+  return IBM_OK;
+}
+
+}  // namespace
+
+namespace {
 
 struct FieldDesc {
   double* ptr;
@@ -1012,6 +1322,91 @@ void ibm_destroy(ibm_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   delete c;
+}
+
+int ibm_batch_create(ibm_ctx* const* cases, int n, ibm_batch** out) {
+  if (!cases || !out || n < 1) return fail(IBM_E_INVAL, "null argument or empty batch");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!cases[i]) return fail(IBM_E_INVAL, "batch case %d is null", i);
+    if (cases[i]->P.precision != 1) return fail(IBM_E_INVAL, "batch case %d: precision must be 1", i);
+    for (int k = 0; k < i; ++k)
+      if (cases[k] == cases[i]) return fail(IBM_E_INVAL, "batch cases %d and %d are the same context", k, i);
+  }
+  auto* B = new ibm_batch();
+  B->cs.assign(cases, cases + n);
+  bool ok = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaMallocHost((void**)&B->h_sor, 2 * n * sizeof(Sor32Case)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void**)&B->h_dc, n * sizeof(DcCase)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void**)&B->h_bits, n * sizeof(unsigned long long)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&B->d_sor, 2 * n * sizeof(Sor32Case)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&B->d_dc, n * sizeof(DcCase)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&B->d_bits, n * sizeof(unsigned long long)) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&B->ev_b, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreate(&B->t0) == cudaSuccess && cudaEventCreate(&B->t1) == cudaSuccess;
+  B->ev.resize(n, nullptr);
+  for (int i = 0; ok && i < n; ++i) ok = cudaEventCreateWithFlags(&B->ev[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    delete B;
+    return fail(IBM_E_CUDA, "batch allocation failed");
+  }
+  *out = B;
+  return IBM_OK;
+}
+
+int ibm_batch_step(ibm_batch* B, int nsteps, ibm_step_stats* last) {
+  if (!B || nsteps < 0) return fail(IBM_E_INVAL, "invalid argument");
+  const int n = (int)B->cs.size();
+  // all work of the batch runs on its stream, after what the cases' own
+  // streams hold, and the cases' streams wait for it afterwards
+  std::vector<cudaStream_t> own(n);
+  for (int i = 0; i < n; ++i) {
+    own[i] = B->cs[i]->stream;
+    CUDA_TRY(cudaEventRecord(B->ev[i], own[i]));
+    CUDA_TRY(cudaStreamWaitEvent(B->stream, B->ev[i], 0));
+    B->cs[i]->stream = B->stream;
+  }
+  int rc = IBM_OK;
+  for (int s = 0; s < nsteps && rc == IBM_OK; ++s) rc = batch_one_step(B);
+  for (int i = 0; i < n; ++i) B->cs[i]->stream = own[i];
+  cudaEventRecord(B->ev_b, B->stream);
+  for (int i = 0; i < n; ++i) cudaStreamWaitEvent(own[i], B->ev_b, 0);
+  if (rc) return rc;
+  if (last)
+    for (int i = 0; i < n; ++i) last[i] = B->cs[i]->last;
+  return IBM_OK;
+}
+
+int ibm_batch_set_graphs(ibm_batch* B, int on) {
+  if (!B) return fail(IBM_E_INVAL, "null batch");
+  B->use_graphs = on != 0;
+  return IBM_OK;
+}
+
+int ibm_batch_set_profiling(ibm_batch* B, int on) {
+  if (!B) return fail(IBM_E_INVAL, "null batch");
+  B->profiling = on != 0;
+  B->prof = ibm_profile{};
+  for (ibm_ctx* c : B->cs) c->prof = ibm_profile{};
+  return IBM_OK;
+}
+
+int ibm_batch_get_profile(const ibm_batch* B, ibm_profile* out) {
+  if (!B || !out) return fail(IBM_E_INVAL, "null argument");
+  *out = B->prof;
+  if (B->cfg >= 0) sor32_describe(B->cfg, &out->sor_shape[0], &out->sor_shape[1], &out->sor_shape[2]);
+  out->sor_us_per_sweep = B->sor_us;
+  for (ibm_ctx* c : B->cs) {
+    out->launches += c->prof.launches;
+    out->helm_sweeps += c->prof.helm_sweeps;
+  }
+  return IBM_OK;
+}
+
+void ibm_batch_destroy(ibm_batch* B) {
+  if (!B) return;
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  delete B;
 }
 
 }  // extern "C"

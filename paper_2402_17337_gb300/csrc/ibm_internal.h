@@ -111,6 +111,32 @@ void launch_helm_res(cudaStream_t s, const Geo& g, int grid, const double* x, co
                      const Band& band, const uint8_t* fl, const double* al, double beta, double Ub,
                      unsigned long long* res_bits);
 
+// batched mixed-precision solve: one launch over the tiles of many cases
+struct Sor32Case {
+  Geo32 g;
+  const float* e_in;
+  float* e_out;
+  const float* r;
+  const float* invd;
+  float omega;
+  int first, tiles_x;  // first CTA of this case, tiles per row
+};
+struct DcCase {
+  Geo g;
+  int pk, add_e, first;  // first block of this case (blocks of 32 x 8 cells)
+  const double* phi_in;
+  double* phi_out;
+  const float* e;
+  const double* b;
+  float* r32;
+  unsigned long long* res_bits;
+};
+void sor32_tiles(int cfg, const Geo32& g, int* tiles_x, int* tiles_y);
+cudaError_t sor32_batch_prepare(int cfg);
+void launch_sor32_batch(cudaStream_t s, int cfg, const Sor32Case* cases_dev, int ncases, int total_tiles,
+                        int zero_init);
+void launch_dc_residual_batch(cudaStream_t s, const DcCase* cases_dev, int ncases, int total_blocks);
+
 // learned warm start (k_ws.cu): coarse features, prediction, targets
 void launch_ws_features(cudaStream_t s, const Geo& g, int Hc, int Wc, const double* b, const double* phi,
                         const double* p, const Band& band, const uint8_t* fc, float* feat,

@@ -80,6 +80,46 @@ __global__ void k_dc_residual(Geo g, int pk, const double* __restrict__ phi_in, 
   block_max_bits(bits, res_bits);
 }
 
+// Batched FP64 update + residual: block b belongs to the case whose block
+// range holds it; each case has its own grid, buffers and norm slot.
+__global__ void k_dc_residual_batch(const DcCase* __restrict__ cases, int ncases) {
+  const int b = blockIdx.x;
+  int lo = 0, hi = ncases - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (cases[mid].first <= b) lo = mid; else hi = mid - 1;
+  }
+  const DcCase& c = cases[lo];
+  const Geo& g = c.g;
+  const int t = b - c.first, bxn = (g.nx + 31) / 32;
+  const int i = (t % bxn) * 32 + threadIdx.x, j = (t / bxn) * 8 + threadIdx.y;
+  const int nx = g.nx, ny = g.ny, pk = c.pk;
+  unsigned long long bits = 0ull;
+  if (i < nx && j < ny) {
+    const int P = g.pitch;
+    size_t cc = at(i, j, P);
+    const double* phi_in = c.phi_in;
+    double fP = phi_in[cc], fE = phi_in[cc + 1], fW = phi_in[cc - 1], fN = phi_in[cc + P], fS = phi_in[cc - P];
+    if (c.add_e) {
+      const float* e = c.e;
+      fP += (double)e[rb_at(i, j, ny, pk)];
+      if (i < nx - 1) fE += (double)e[rb_at(i + 1, j, ny, pk)];
+      if (i > 0) fW += (double)e[rb_at(i - 1, j, ny, pk)];
+      if (j < ny - 1) fN += (double)e[rb_at(i, j + 1, ny, pk)];
+      if (j > 0) fS += (double)e[rb_at(i, j - 1, ny, pk)];
+      c.phi_out[cc] = fP;
+    }
+    double L = g.pE[i] * (fE - fP);
+    L = fma(g.pW[i], fW - fP, L);
+    L = fma(g.pN[j], fN - fP, L);
+    L = fma(g.pS[j], fS - fP, L);
+    double r = c.b[cc] - L;
+    c.r32[rb_at(i, j, ny, pk)] = (float)r;
+    bits = abs_bits(r);
+  }
+  block_max_bits(bits, c.res_bits);
+}
+
 // K half-sweeps (red first) of FP32 red-black SOR on L_p e = r, from e_in
 // into e_out.  The two buffers must differ: a tile's halo is read from cells
 // that neighbouring tiles write, and tiles of later waves would otherwise
@@ -105,17 +145,16 @@ struct Sor32Shape {
 };
 
 template <int TY, int K, int NY>
-__global__ void __launch_bounds__(32 * NY, 2)
-    k_sor32_rb(const Geo32 g, const float* __restrict__ e_in, float* __restrict__ e_out, const float* __restrict__ r,
-               const float* __restrict__ invd, float omega, int zero_init) {
+__device__ __forceinline__ void sor32_tile(const Geo32& g, const float* __restrict__ e_in, float* __restrict__ e_out,
+                                           const float* __restrict__ r, const float* __restrict__ invd, float omega,
+                                           int zero_init, int bx, int by, float* smem) {
   using S = Sor32Shape<TY, K, NY>;
   constexpr int LK = S::LK, HK = S::HK, TK = S::TK, LY = S::LY, RPT = S::RPT;
-  extern __shared__ float smem[];
   float(*se)[LY][LK] = reinterpret_cast<float(*)[LY][LK]>(smem);                    // [2][LY][LK]
   float(*sr)[LY][LK] = reinterpret_cast<float(*)[LY][LK]>(smem + 2 * LY * LK);      // [2][LY][LK]
   float(*sd)[LY][LK] = reinterpret_cast<float(*)[LY][LK]>(smem + 4 * LY * LK);      // [2][LY][LK]
   const int nx = g.nx, ny = g.ny, pk = g.pk;
-  const int k0 = blockIdx.x * TK - HK, j0 = blockIdx.y * TY - K;
+  const int k0 = bx * TK - HK, j0 = by * TY - K;
   const int tx = threadIdx.x, ty = threadIdx.y;
   float ev[2][RPT][2];
   float cE[2][2], cW[2][2], cN[RPT], cS[RPT];
@@ -206,11 +245,43 @@ __global__ void __launch_bounds__(32 * NY, 2)
   }
 }
 
+template <int TY, int K, int NY>
+__global__ void __launch_bounds__(32 * NY, 2)
+    k_sor32_rb(const Geo32 g, const float* __restrict__ e_in, float* __restrict__ e_out, const float* __restrict__ r,
+               const float* __restrict__ invd, float omega, int zero_init) {
+  extern __shared__ float smem[];
+  sor32_tile<TY, K, NY>(g, e_in, e_out, r, invd, omega, zero_init, blockIdx.x, blockIdx.y, smem);
+}
+
+// Batched form: one launch sweeps the tiles of many cases (uneven grids).
+// CTA b belongs to the case whose tile range [first, first + count) holds b.
+template <int TY, int K, int NY>
+__global__ void __launch_bounds__(32 * NY, 2)
+    k_sor32_rb_batch(const Sor32Case* __restrict__ cases, int ncases, int zero_init) {
+  extern __shared__ float smem[];
+  __shared__ Sor32Case c;  // the case's descriptor, read from shared memory where needed
+  const int b = blockIdx.x;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    int lo = 0, hi = ncases - 1;
+    while (lo < hi) {  // last case with first <= b
+      int mid = (lo + hi + 1) >> 1;
+      if (cases[mid].first <= b) lo = mid; else hi = mid - 1;
+    }
+    c = cases[lo];
+  }
+  __syncthreads();
+  const int t = b - c.first;
+  sor32_tile<TY, K, NY>(c.g, c.e_in, c.e_out, c.r, c.invd, c.omega, zero_init, t % c.tiles_x, t / c.tiles_x, smem);
+}
+
 // Tile shapes the autotuner chooses from: (rows per tile, half-sweeps per
 // launch, thread rows).
 struct Sor32Config {
   int TY, K, NY;
   void (*launch)(cudaStream_t, const Geo32&, const float*, float*, const float*, const float*, float, int);
+  void (*launch_batch)(cudaStream_t, const Sor32Case*, int, int, int);
+  cudaError_t (*prepare_batch)();
+  void (*tiles)(const Geo32&, int*, int*);
 };
 
 template <int TY, int K, int NY>
@@ -227,11 +298,36 @@ void launch_shape(cudaStream_t s, const Geo32& g, const float* e_in, float* e_ou
   k_sor32_rb<TY, K, NY><<<grd, dim3(32, NY), S::smem, s>>>(g, e_in, e_out, r, invd, omega, zero_init);
 }
 
+template <int TY, int K, int NY>
+void launch_shape_batch(cudaStream_t s, const Sor32Case* cases, int ncases, int total_tiles, int zero_init) {
+  using S = Sor32Shape<TY, K, NY>;
+  if (total_tiles <= 0) return;
+  k_sor32_rb_batch<TY, K, NY><<<total_tiles, dim3(32, NY), S::smem, s>>>(cases, ncases, zero_init);
+}
+
+// dynamic shared memory limit of the batched kernel; set once, outside any
+// stream capture
+template <int TY, int K, int NY>
+cudaError_t prepare_shape_batch() {
+  using S = Sor32Shape<TY, K, NY>;
+  return cudaFuncSetAttribute(k_sor32_rb_batch<TY, K, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)S::smem);
+}
+
+template <int TY, int K, int NY>
+void shape_tiles(const Geo32& g, int* tx, int* ty) {
+  using S = Sor32Shape<TY, K, NY>;
+  *tx = ((g.nx + 1) / 2 + S::TK - 1) / S::TK;
+  *ty = (g.ny + TY - 1) / TY;
+}
+
+#define SOR32_SHAPE(a, b, c) \
+  { a, b, c, launch_shape<a, b, c>, launch_shape_batch<a, b, c>, prepare_shape_batch<a, b, c>, shape_tiles<a, b, c> }
 const Sor32Config kConfigs[] = {
-    {32, 8, 16, launch_shape<32, 8, 16>},  {48, 8, 16, launch_shape<48, 8, 16>},
-    {16, 8, 8, launch_shape<16, 8, 8>},    {32, 4, 8, launch_shape<32, 4, 8>},
-    {64, 16, 16, launch_shape<64, 16, 16>}, {32, 12, 16, launch_shape<32, 12, 16>},
+    SOR32_SHAPE(32, 8, 16), SOR32_SHAPE(48, 8, 16),  SOR32_SHAPE(16, 8, 8),
+    SOR32_SHAPE(32, 4, 8),  SOR32_SHAPE(64, 16, 16), SOR32_SHAPE(32, 12, 16),
 };
+#undef SOR32_SHAPE
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
 }  // namespace
@@ -253,6 +349,20 @@ void launch_dc_residual(cudaStream_t s, const Geo& g, int pk, const double* phi_
 void launch_sor32(cudaStream_t s, int cfg, const Geo32& g, const float* e_in, float* e_out, const float* r,
                   const float* invd, float omega, int zero_init) {
   kConfigs[cfg].launch(s, g, e_in, e_out, r, invd, omega, zero_init);
+}
+
+void sor32_tiles(int cfg, const Geo32& g, int* tiles_x, int* tiles_y) { kConfigs[cfg].tiles(g, tiles_x, tiles_y); }
+
+cudaError_t sor32_batch_prepare(int cfg) { return kConfigs[cfg].prepare_batch(); }
+
+void launch_sor32_batch(cudaStream_t s, int cfg, const Sor32Case* cases_dev, int ncases, int total_tiles,
+                        int zero_init) {
+  kConfigs[cfg].launch_batch(s, cases_dev, ncases, total_tiles, zero_init);
+}
+
+void launch_dc_residual_batch(cudaStream_t s, const DcCase* cases_dev, int ncases, int total_blocks) {
+  if (total_blocks <= 0) return;
+  k_dc_residual_batch<<<total_blocks, dim3(32, 8), 0, s>>>(cases_dev, ncases);
 }
 
 }  // namespace ibm

@@ -119,6 +119,24 @@ def batch64(n: int = 64, seed: int = 17337) -> list[FlowConfig]:
     return out
 
 
+def batch_small(n: int = 4, seed: int = 17337, sizes=(96, 112, 128, 144, 160, 176, 192)) -> list[FlowConfig]:
+    """The 64-case batch's recipe at grids the oracle steps in seconds:
+    same parameter distributions, nx from `sizes`, ny = nx/2, min spacing
+    10/nx, divergence tolerance 1e-10, 5 steps."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in range(n):
+        h = float(rng.uniform(0.1, 0.5))
+        k = float(rng.uniform(1.0, 4.0))
+        Re = float(rng.uniform(100.0, 1000.0))
+        nx = int(rng.choice(np.asarray(sizes)))
+        hmin = 10.0 / nx
+        dt = 0.25 * hmin / (1.0 + k * h)
+        out.append(FlowConfig(f"batch_small[{c}]", *PAPER_DOMAIN, nx, nx // 2, hmin, Re=Re, dt=dt, steps=5,
+                              h=h, k=k, div_tol=1e-10, init="uniform"))
+    return out
+
+
 def unet_1024x512() -> FlowConfig:
     dt = 2e-3
     return FlowConfig("unet_1024x512", *PAPER_DOMAIN, 1024, 512, 0.01, Re=300.0, dt=dt, steps=1000,
