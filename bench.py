@@ -10,9 +10,17 @@ dt 1e-3, divergence 1e-8).  Synthetic: the flow starts as the uniform free
 stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--warmstart learned|plain] [--workload plunge_2048x1024|batch64]
 
-The value is the mixed path (FP32 sweeps inside FP64 defect correction);
-the plain FP64 path is timed on the same steps and reported beside it.
+The value is the learned warm start with the mixed path (the U-Net's
+prediction added to the previous increment, then FP32 sweeps inside FP64
+defect correction to the same tolerance); the mixed path with the plain warm
+start and the plain FP64 path are timed on the same steps and reported
+beside it.  The U-Net weights come from train_warmstart (trained on
+snapshots of seeded runs on the same grid).
+
+--workload batch64 times the batch of 64 cases with uneven grids (512x256 ..
+1536x768) advancing together (--cases N: the first N of them).
 
 --impl reference times the FP64 CPU oracle (the slow, plain restatement of
 the method) on the host cores with the same metric; under torchrun only rank
@@ -21,6 +29,7 @@ the method) on the host cores with the same metric; under torchrun only rank
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -37,6 +46,8 @@ FP32_FLOPS_PER_CLK_SM = 256.0  # 128 FP32 FMA per clock per SM
 SOR32_BYTES_PER_CELL_LAUNCH = 12  # read e, r; write e (FP32) once per launch
 SOR_FLOPS_PER_UPDATE = 12     # 4 products + 3 adds, minus b, times 1/d, relaxation (2)
 SOR_BYTES_PER_CELL_HALF = 16  # read phi (8, all cells), read b (4), write phi (4) per half-sweep
+WORKLOADS = ("plunge_2048x1024", "batch64")
+METRIC = "cell-steps/s at div<1e-8: learned warm-start+mixed vs plain FP64, one GB300"
 
 
 def env_int(k, d):
@@ -113,14 +124,21 @@ def solver_kwargs(cfg, precision):
                 omega_h=cfg.omega_h, precision=precision)
 
 
+def oracle_sim(cfg, threads):
+    """An oracle context for the workload, its pressure relaxation factor
+    set by the oracle's own probe of the grid (untimed)."""
+    import oracle
+    kw = solver_kwargs(cfg, 0)
+    kw.pop("precision")
+    kw["omega_p"] = oracle.tune_omega(oracle.Sim(**kw, threads=threads))
+    return oracle.Sim(**kw, threads=threads), kw["omega_p"]
+
+
 def cpu_oracle_sample(cfg, state=None, max_seconds=60.0):
     """Times the FP64 oracle on one full step of the workload (all host
     cores), optionally started from a given (u, v, p, phi) state."""
-    import oracle
     threads = os.cpu_count() or 1
-    kw = solver_kwargs(cfg, 0)
-    kw.pop("precision")
-    o = oracle.Sim(**kw, threads=threads)
+    o, w = oracle_sim(cfg, threads)
     o.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
     if state is not None:
         for name, arr in state.items():
@@ -129,7 +147,7 @@ def cpu_oracle_sample(cfg, state=None, max_seconds=60.0):
     rc, st = o.step(1)
     t = time.perf_counter() - t0
     return {"seconds": t, "rc": rc, "sweeps_p": st["sweeps_p"], "threads": threads,
-            "div_max": st["div_max"]}
+            "div_max": st["div_max"], "omega": w}
 
 
 def run_reference(args, cfg):
@@ -140,9 +158,7 @@ def run_reference(args, cfg):
     import oracle
     oracle.build()
     threads = os.cpu_count() or 1
-    kw = solver_kwargs(cfg, 0)
-    kw.pop("precision")
-    o = oracle.Sim(**kw, threads=threads)
+    o, w = oracle_sim(cfg, threads)
     o.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
     o.set("u", cfg.initial_u(o.shape("u")))
     for _ in range(args.warmup):
@@ -161,17 +177,183 @@ def run_reference(args, cfg):
     T = sum(times)
     value = cfg.cells * ok / T
     line = {
-        "impl": "reference", "metric": "cell-steps/s", "value": value, "unit": "cell-steps/s",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": cfg.name, "nx": cfg.nx, "ny": cfg.ny, "global_batch": 1, "path": "cpu-oracle",
-                   "poisson_sweeps_per_step": statistics.mean(sweeps)},
+                   "poisson_sweeps_per_step": statistics.mean(sweeps), "omega_p": w},
         "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": threads, "kind": "oracle",
                          "sample": f"{args.warmup} untimed + {args.steps} timed full steps of {cfg.name} "
                                    f"from the uniform free stream, FP64 oracle, {threads} OpenMP threads in the pressure solve"},
         "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batch(args):
+    """--workload batch64: the first --cases cases of the 64-case batch
+    advancing together; value = sum over cases and timed steps of the cells
+    of steps that met the divergence tolerance, over the device time."""
+    import numpy as np
+    import torch
+
+    import paper_2402_17337_gb300 as ibm
+    from paper_2402_17337_gb300 import build as B
+    from paper_2402_17337_gb300 import workloads as W
+
+    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    B.build()
+    cfgs = W.batch64()[:args.cases]
+    cells = [c.cells for c in cfgs]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def reduce(x, op):
+        if not dist:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    omegas = []
+    for c in cfgs:  # each case's relaxation factor from the device probe (untimed)
+        s = ibm.Solver.from_config(c, precision=1)
+        omegas.append(s.tune_omega())
+        s.close()
+    cfgs = [dataclasses.replace(c, omega_p=w) for c, w in zip(cfgs, omegas)]
+
+    def make():
+        ss = []
+        for c in cfgs:
+            s = ibm.Solver.from_config(c, precision=1)
+            s.set("u", c.initial_u(s.shape("u")))
+            ss.append(s)
+        return ss, ibm.Batch(ss)
+
+    ss, batch = make()
+    for _ in range(args.warmup):
+        batch.step(1)
+    state0 = {n: ss[0].get(n) for n in ("u", "v", "p", "phi")} if rank == 0 else None
+    batch.set_profiling(True)
+    bstream = torch.cuda.ExternalStream(batch.stream)
+    clocks = ClockSampler(local)
+    barrier()
+    if not args.no_clocks:
+        clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()  # marks the timed region for a profiler (no-op otherwise)
+    e0.record(bstream)
+    stats = [batch.step(1) for _ in range(args.steps)]
+    e1.record(bstream)
+    barrier()
+    torch.cuda.profiler.stop()
+    clk = clocks.stop() if not args.no_clocks else None
+    ms = reduce(e0.elapsed_time(e1), dist.ReduceOp.MAX if dist else None)
+    prof = batch.profile()
+    ok_cells = sum(n for st in stats for n, c, x in zip(cells, cfgs, st) if x["div_max"] < c.div_tol)
+    ok_cells = reduce(ok_cells, dist.ReduceOp.SUM if dist else None)
+    value = ok_cells / (ms / 1e3)
+    batch.close()
+    for s in ss:
+        s.close()
+
+    peaks, peak_src = load_peaks()
+    roof = None
+    if prof["sweep_ms"] > 0:
+        nbytes = SOR32_BYTES_PER_CELL_LAUNCH * prof["sweep_cells"]
+        achieved = nbytes / (prof["sweep_ms"] / 1e3) / 1e9
+        rows, half, _ = prof["sor_shape"]
+        roof = {"bound": "hbm", "kernel": f"k_sor32_rb_batch (FP32 red-black SOR over the tiles of every active "
+                                          f"case, tile {rows} rows x 128 cells, {half} half-sweeps per launch)",
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": None, "launch_us": 1e3 * prof["sweep_ms"] / prof["sweep_launches"],
+                "peak_note": f"HBM {peaks['hbm_gbs']} GB/s ({peak_src}); algorithmic bytes {SOR32_BYTES_PER_CELL_LAUNCH}"
+                             f" B per covered cell per launch, summed over the timed sweep launches (cases leave "
+                             f"the launches as they converge)"}
+
+    e2e = None
+    if not args.no_e2e:
+        ss2, batch2 = make()
+        for _ in range(args.warmup):
+            batch2.step(1)
+        names = ("u", "v", "p", "phi")
+        pinned = [{n: torch.empty(s.shape(n), dtype=torch.float64, pin_memory=True).numpy() for n in names}
+                  for s in ss2]
+        for s, pn in zip(ss2, pinned):
+            for n in names:
+                pn[n][...] = s.get(n)
+        h2d = sum(a.nbytes for pn in pinned for a in pn.values())
+        barrier()
+        t0 = time.perf_counter()
+        ok2 = 0
+        for _ in range(args.steps):
+            for s, pn in zip(ss2, pinned):
+                for n in names:
+                    s.set(n, pn[n])
+            st = batch2.step(1)
+            for s, pn in zip(ss2, pinned):
+                for n in names:
+                    pn[n][...] = s.get(n)
+            ok2 += sum(n for n, c, x in zip(cells, cfgs, st) if x["div_max"] < c.div_tol)
+        barrier()
+        te = reduce(time.perf_counter() - t0, dist.ReduceOp.MAX if dist else None)
+        ok2 = reduce(ok2, dist.ReduceOp.SUM if dist else None)
+        batch2.close()
+        for s in ss2:
+            s.close()
+        e2e = {"value": ok2 / te, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+               "note": "a second batch over the same steps; per step every case's u, v, p, phi copied in from "
+                       "pinned host memory, batch step, copied back; host wall clock"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        r = cpu_oracle_sample(cfgs[0], state0)
+        cpu = {"value": cfgs[0].cells / r["seconds"] if r["rc"] == 0 else None, "unit": "cell-steps/s",
+               "cores": r["threads"], "kind": "oracle",
+               "sample": f"one full step of {cfgs[0].name} ({cfgs[0].nx}x{cfgs[0].ny}) from the GPU run's state at "
+                         f"the start of the timed window, {r['sweeps_p']} pressure sweeps at the oracle's own "
+                         f"relaxation factor {r['omega']:.6f}, {r['seconds']:.1f} s, FP64 oracle, "
+                         f"{r['threads']} OpenMP threads in the pressure solve"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 sweeps, f64 residual/update/norms", "data": "synthetic",
+            "config": {"workload": "batch64" if args.cases == 64 else f"batch64[:{args.cases}]",
+                       "cases": args.cases, "cells_per_step": sum(cells),
+                       "grids": sorted({f"{c.nx}x{c.ny}" for c in cfgs}), "global_batch": args.cases * world,
+                       "parallelism": f"replicas x{world}", "path": "mixed, batched, graph replay",
+                       "warm_start": "previous increment", "sor_us_per_sweep_whole_batch": prof["sor_us_per_sweep"],
+                       "poisson_sweeps_per_step_sum": statistics.mean(sum(x["sweeps_p"] for x in st) for st in stats),
+                       "l2": f"{sum(cells) * 16 / 1e6:.0f} MB of FP32 sweep arrays per launch set; no flush",
+                       "div_max": max(x["div_max"] for st in stats for x in st)},
+            "gpu_launches": prof["launches"],
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
     return 0
 
 
@@ -187,11 +369,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="no nvidia-smi sampling (for profiler runs)")
+    ap.add_argument("--warmstart", choices=["learned", "plain"], default="learned",
+                    help="learned: U-Net warm start (the value); plain: previous increment")
+    ap.add_argument("--weights", default=None, help="U-Net weights (default: the package's trained weights)")
+    ap.add_argument("--workload", choices=WORKLOADS, default=WORKLOADS[0])
+    ap.add_argument("--cases", type=int, default=64, help="batch64: number of cases")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
 
     from paper_2402_17337_gb300 import workloads as W
+    if args.workload == "batch64":
+        if args.impl == "reference":
+            return run_reference(args, W.batch64()[0])
+        return run_batch(args)
     cfg = W.plunge_2048x1024()
     if args.impl == "reference":
         return run_reference(args, cfg)
@@ -236,11 +427,30 @@ def main():
         dist.all_reduce(t)
         return float(t.item())
 
-    def timed_run(precision, sample_clocks):
+    # pressure relaxation factor of this grid from the device probe (untimed),
+    # used by every timed run below
+    probe = ibm.Solver(**solver_kwargs(cfg, 1), stream=stream.cuda_stream)
+    omega_default = cfg.omega()
+    cfg = dataclasses.replace(cfg, omega_p=probe.tune_omega())
+    probe.close()
+
+    learned = None
+    if args.warmstart == "learned" and args.precision == "mixed":
+        from paper_2402_17337_gb300 import warmstart
+        path = args.weights or warmstart.DEFAULT_WEIGHTS
+        if not os.path.exists(path):
+            raise SystemExit(f"no U-Net weights at {path}: run paper_2402_17337_gb300.train_warmstart "
+                             f"or pass --warmstart plain")
+        net, cT, meta = warmstart.load(path)
+        learned = {"net": net, "cT": cT, "meta": meta}
+
+    def timed_run(precision, sample_clocks, ws=None):
         """W untimed steps, then K steps timed with CUDA events on the solver's stream."""
         s = ibm.Solver(**solver_kwargs(cfg, precision), stream=stream.cuda_stream)
         s.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
         s.set("u", cfg.initial_u(s.shape("u")))
+        if ws is not None:
+            s.set_warmstart(1, ws["net"], ws["cT"])
         for _ in range(args.warmup):
             s.step(1)
         state = {n: s.get(n) for n in ("u", "v", "p", "phi")} if rank == 0 else None
@@ -251,10 +461,12 @@ def main():
         if sample_clocks:
             clocks.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.profiler.start()  # marks the timed region for a profiler (no-op otherwise)
         e0.record(stream)
         stats = [s.step(1) for _ in range(args.steps)]
         e1.record(stream)
         barrier()
+        torch.cuda.profiler.stop()
         clk = clocks.stop() if sample_clocks else None
         ms = max_over_ranks(e0.elapsed_time(e1))
         prof = s.profile()
@@ -264,10 +476,11 @@ def main():
                 "launches": prof["launches"] - prof0["launches"], "prof": prof, "state": state}
 
     precision = 1 if args.precision == "mixed" else 0
-    main_run = timed_run(precision, not args.no_clocks)
+    main_run = timed_run(precision, not args.no_clocks, learned)
     value, t_max, stats, total_ok = main_run["value"], main_run["ms"], main_run["stats"], main_run["ok"]
     prof, clk, launches, start_state = main_run["prof"], main_run["clocks"], main_run["launches"], main_run["state"]
     fp64_run = timed_run(0, False) if (precision == 1 and not args.no_fp64_compare) else None
+    plain_ws_run = timed_run(1, False) if (learned is not None and not args.no_fp64_compare) else None
 
     # roofline of the dominant kernel
     peaks, peak_src = load_peaks()
@@ -310,6 +523,8 @@ def main():
         s2 = ibm.Solver(**solver_kwargs(cfg, precision), stream=stream.cuda_stream)
         s2.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
         s2.set("u", cfg.initial_u(s2.shape("u")))
+        if learned is not None:
+            s2.set_warmstart(1, learned["net"], learned["cT"])
         for _ in range(args.warmup):
             s2.step(1)
         names = ("u", "v", "p", "phi")
@@ -348,8 +563,9 @@ def main():
         cpu = {"value": cfg.cells / r["seconds"] if r["rc"] == 0 else None, "unit": "cell-steps/s",
                "cores": r["threads"], "kind": "oracle",
                "sample": f"one full step of {cfg.name} started from the GPU run's state at the start of the "
-                         f"timed window (AB2 history restarted), {r['sweeps_p']} pressure sweeps, "
-                         f"{r['seconds']:.1f} s, FP64 oracle, {r['threads']} OpenMP threads in the pressure solve"}
+                         f"timed window (AB2 history restarted), {r['sweeps_p']} pressure sweeps at the oracle's "
+                         f"own relaxation factor {r['omega']:.6f}, {r['seconds']:.1f} s, FP64 oracle, "
+                         f"{r['threads']} OpenMP threads in the pressure solve"}
 
     if rank == 0:
         sweeps = [st["sweeps_p"] for st in stats]
@@ -358,14 +574,28 @@ def main():
             fp64 = {"value": fp64_run["value"], "ms_per_step": fp64_run["ms"] / args.steps,
                     "poisson_sweeps_per_step": statistics.mean(st["sweeps_p"] for st in fp64_run["stats"]),
                     "speedup_of_value": value / fp64_run["value"]}
+        plain_ws = None
+        if plain_ws_run:
+            plain_ws = {"value": plain_ws_run["value"], "ms_per_step": plain_ws_run["ms"] / args.steps,
+                        "poisson_sweeps_per_step": statistics.mean(st["sweeps_p"] for st in plain_ws_run["stats"]),
+                        "speedup_of_value": value / plain_ws_run["value"]}
+        ws_desc = "previous increment"
+        if learned is not None:
+            m = learned["meta"]
+            ws_desc = (f"learned: U-Net widths {tuple(m.get('widths', ()))} on the 2x coarsened grid, trained on "
+                       f"{m.get('samples')} snapshots of {m.get('runs')} seeded runs (h, k, Re drawn), BF16 "
+                       f"tensor-core kernels")
         line = {
-            "metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": world,
+            "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 sweeps, f64 residual/update/norms" if precision == 1 else "f64",
+            "dtype": ("f32 sweeps, f64 residual/update/norms" + (", bf16 U-Net" if learned else ""))
+                     if precision == 1 else "f64",
             "data": "synthetic",
             "config": {"workload": cfg.name, "nx": cfg.nx, "ny": cfg.ny, "global_batch": world,
-                       "parallelism": f"replicas x{world}", "path": args.precision, "plain_fp64": fp64,
+                       "parallelism": f"replicas x{world}", "path": args.precision, "warm_start": ws_desc,
+                       "omega_p": cfg.omega_p, "omega_p_grid_formula": omega_default,
+                       "mixed_plain_warmstart": plain_ws, "plain_fp64": fp64,
                        "steps_counted": total_ok, "poisson_sweeps_per_step": statistics.mean(sweeps),
                        "helm_sweeps_per_step": statistics.mean(st["sweeps_u"] + st["sweeps_v"] for st in stats),
                        "l2": "state 14 FP64 fields x 17 MB > L2; no flush",

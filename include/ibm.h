@@ -212,6 +212,7 @@ typedef struct {
   int sor_shape[3];          /* FP32 sweep tile chosen by the autotuner: rows per tile,
                                 half-sweeps per launch, thread rows (0 if not tuned) */
   double sor_us_per_sweep;   /* its measured time per full sweep, microseconds */
+  long long sweep_cells;     /* cells covered by the timed sweep launches, summed over launches */
 } ibm_profile;
 
 /* Autotuner of the FP32 sweep kernel (precision 1): times each tile shape on
@@ -219,6 +220,24 @@ typedef struct {
  * before the first mixed-precision solve; calling it re-tunes.  A no-op for
  * precision 0.  Uses the context's work arrays: not during a step. */
 int ibm_tune(ibm_ctx* ctx);
+
+/* Relaxation factor of the pressure SOR (Sec. 2.2 leaves it free) from the
+ * observed convergence: red-black SOR runs on the homogeneous pressure
+ * system from a pseudo-random start until the residual has fallen by 1e-10
+ * or `sweeps` sweeps have run (<= 0: 8 max(nx, ny), clamped to 2048..32768),
+ * the asymptotic rate rho over the second half at the context's omega gives
+ * the Jacobi spectral radius through Young's relation for consistently
+ * ordered matrices, and the optimum 2 / (1 + sqrt(1 - mu^2)) replaces omega
+ * if a second run confirms a faster rate.  The optimum depends on the grid
+ * only (stretching included), not on the flow.  *omega receives the factor in
+ * use.  Uses temporary device memory and the context's stream; not during a
+ * step.  FP64 sweeps whatever the precision. */
+int ibm_tune_omega(ibm_ctx* ctx, int sweeps, double* omega);
+
+/* Young's relation as used by ibm_tune_omega: the optimal relaxation factor
+ * given the convergence factor per sweep rho observed at omega (omega itself
+ * when rho <= omega - 1, i.e. omega at or above the optimum).  Host only. */
+double ibm_omega_from_rate(double omega, double rho);
 
 /* Turns the event timing of pressure sweeps on (1) or off (0); counters are
  * reset.  Timing adds one event pair per run of sweeps. */
@@ -291,6 +310,10 @@ int ibm_batch_create(ibm_ctx* const* cases, int n, ibm_batch** out);
  * the statistics of each case's last step.  On an error the message names
  * the case; the cases are then in an unspecified state. */
 int ibm_batch_step(ibm_batch* batch, int nsteps, ibm_step_stats* last);
+
+/* The batch's own stream (a cudaStream_t), for timing with events; NULL for
+ * a NULL batch. */
+void* ibm_batch_stream(const ibm_batch* batch);
 
 /* CUDA-graph replay of the sweep launches: on (1, the default) or off (0). */
 int ibm_batch_set_graphs(ibm_batch* batch, int on);

@@ -6,7 +6,7 @@ CUDA library and its binding) never imports this package.
 
 The oracle is the plain restatement of the immersed-boundary fractional step
 of arXiv 2402.17337 (Sec. 2.1 Eqs. 1-2, Sec. 2.2 Eqs. 3-4, Sec. 2.3, Sec. 3.1):
-classification, AB2/CN predictor with red-black SOR, mass source on cut cells,
+classification, AB2/CN predictor with red-black SOR, mass source on body cells,
 red-black SOR pressure Poisson, projection and force histories.
 """
 from __future__ import annotations
@@ -259,3 +259,55 @@ class Sim:
 
     def clear_flags(self):
         lib().or_clear_flags(self._h)
+
+
+def omega_from_rate(omega, rho):
+    """Optimal SOR relaxation factor from the convergence factor per sweep rho
+    observed at omega (Young's relation for consistently ordered matrices,
+    omega below the optimum: (rho + omega - 1)^2 = rho omega^2 mu^2 with mu the
+    Jacobi spectral radius; optimum 2 / (1 + sqrt(1 - mu^2))).  Returns omega
+    when rho <= omega - 1 (at or above the optimum)."""
+    if not (0.0 < rho < 1.0) or rho <= omega - 1.0:
+        return omega
+    mu = (rho + omega - 1.0) / (np.sqrt(rho) * omega)
+    if not mu < 1.0:
+        return omega
+    return float(2.0 / (1.0 + np.sqrt((1.0 - mu) * (1.0 + mu))))
+
+
+def sor_rate(sim, omega, sweeps, seed=5, chunk=64):
+    """Asymptotic convergence factor per sweep of the pressure SOR on the
+    homogeneous system from a seeded random start: the residual is taken
+    every `chunk` sweeps until it has fallen by 1e-10 or `sweeps` sweeps have
+    run, and the factor over the second half of the sweeps run."""
+    ny, nx = sim.shape("p")
+    phi = np.random.default_rng(seed).standard_normal((ny, nx))
+    zero = np.zeros((ny, nx))
+    _, _, _, r0 = sim.poisson(zero, phi0=phi, omega=omega, tol=0.0, check=1, maxs=0)
+    r = [r0]
+    s = 0
+    while r[-1] > 1e-10 * r[0] and s + chunk <= sweeps:
+        _, phi, _, res = sim.poisson(zero, phi0=phi, omega=omega, tol=0.0, check=chunk, maxs=chunk)
+        r.append(res)
+        s += chunk
+    b = len(r) - 1
+    a = b // 2
+    if b == a or r[a] <= 0.0 or r[b] <= 0.0:
+        return 0.0
+    return (r[b] / r[a]) ** (1.0 / (chunk * (b - a)))
+
+
+def tune_omega(sim, sweeps=0):
+    """Relaxation factor of the pressure SOR for the oracle's grid: the rate at
+    the current factor through Young's relation, kept if a second probe
+    confirms a faster rate (the same procedure as the library's, written
+    independently)."""
+    ny, nx = sim.shape("p")
+    if sweeps <= 0:
+        sweeps = min(max(8 * max(nx, ny), 2048), 32768)
+    w0 = sim.P.omega_p
+    rho0 = sor_rate(sim, w0, sweeps)
+    w1 = omega_from_rate(w0, rho0)
+    if w1 != w0 and sor_rate(sim, w1, sweeps) < rho0:
+        return w1
+    return w0

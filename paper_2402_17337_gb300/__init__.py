@@ -51,7 +51,7 @@ class StepStats(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("launches", C.c_longlong), ("sweep_launches", C.c_longlong), ("sweep_ms", C.c_double),
                 ("steps", C.c_longlong), ("poisson_sweeps", C.c_longlong), ("helm_sweeps", C.c_longlong),
-                ("sor_shape", C.c_int * 3), ("sor_us_per_sweep", C.c_double)]
+                ("sor_shape", C.c_int * 3), ("sor_us_per_sweep", C.c_double), ("sweep_cells", C.c_longlong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -98,9 +98,14 @@ def lib():
             L.ibm_set_warmstart.argtypes = [_VP, C.c_int, _VP, C.c_double]
             L.ibm_get_sample.argtypes = [_VP, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_int),
                                          C.POINTER(C.c_int)]
+            L.ibm_tune_omega.argtypes = [_VP, C.c_int, _D]
+            L.ibm_omega_from_rate.argtypes = [C.c_double, C.c_double]
+            L.ibm_omega_from_rate.restype = C.c_double
             L.ibm_batch_create.argtypes = [C.POINTER(_VP), C.c_int, C.POINTER(_VP)]
             L.ibm_batch_step.argtypes = [_VP, C.c_int, C.POINTER(StepStats)]
             L.ibm_batch_set_graphs.argtypes = [_VP, C.c_int]
+            L.ibm_batch_stream.argtypes = [_VP]
+            L.ibm_batch_stream.restype = _VP
             L.ibm_batch_set_profiling.argtypes = [_VP, C.c_int]
             L.ibm_batch_get_profile.argtypes = [_VP, C.POINTER(Profile)]
             L.ibm_batch_destroy.argtypes = [_VP]
@@ -120,6 +125,11 @@ def _check(rc):
 
 def _dp(a):
     return a.ctypes.data_as(_D)
+
+
+def omega_from_rate(omega, rho):
+    """Young's relation: optimal relaxation factor from the rate observed at omega."""
+    return lib().ibm_omega_from_rate(omega, rho)
 
 
 def default_omega(nx, ny):
@@ -233,6 +243,13 @@ class Solver:
         _check(lib().ibm_get_profile(self._h, C.byref(p)))
         return p.as_dict()
 
+    def tune_omega(self, sweeps=0):
+        """Sets the pressure SOR relaxation factor from the observed convergence; returns it."""
+        w = C.c_double(0)
+        _check(lib().ibm_tune_omega(self._h, sweeps, C.byref(w)))
+        self.P.omega_p = w.value
+        return w.value
+
     def set_warmstart(self, mode, net=None, target_scale=1.0):
         """0: previous increment; 1: learned (U-Net net); 2: previous increment + samples."""
         self._ws_net = net  # keep the network alive while the context uses it
@@ -277,6 +294,11 @@ class Batch:
 
     def set_graphs(self, on=True):
         _check(lib().ibm_batch_set_graphs(self._h, 1 if on else 0))
+
+    @property
+    def stream(self):
+        """The batch's cudaStream_t (an integer handle)."""
+        return lib().ibm_batch_stream(self._h)
 
     def set_profiling(self, on=True):
         _check(lib().ibm_batch_set_profiling(self._h, 1 if on else 0))

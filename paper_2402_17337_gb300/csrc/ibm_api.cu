@@ -403,6 +403,7 @@ int solve_poisson(ibm_ctx* c, double tol, double rtol, int m, int maxs, int* swe
         CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
         c->prof.sweep_ms += ms;
         c->prof.sweep_launches += pending;
+        c->prof.sweep_cells += (long long)pending * c->nx * c->ny;
         pending = 0;
       }
       *sweeps = s;
@@ -464,6 +465,79 @@ int tune_sor32(ibm_ctx* c) {
   return IBM_OK;
 }
 
+// Relaxation factor of the pressure SOR from its observed convergence
+// (adaptive SOR): for a consistently ordered matrix (red-black ordering of
+// the five-point operator is one) and omega below the optimum, the SOR
+// spectral radius rho and the Jacobi spectral radius mu satisfy Young's
+// relation (rho + omega - 1)^2 = rho omega^2 mu^2, and the optimum is
+// omega_opt = 2 / (1 + sqrt(1 - mu^2)).  At or above the optimum rho equals
+// omega - 1 and says nothing about mu: omega is returned unchanged.
+double omega_from_rate(double omega, double rho) {
+  if (!(rho > 0.0) || !(rho < 1.0) || !(omega > 0.0) || !(omega < 2.0)) return omega;
+  if (rho <= omega - 1.0) return omega;
+  double mu = (rho + omega - 1.0) / (std::sqrt(rho) * omega);
+  if (!(mu < 1.0)) return omega;
+  return 2.0 / (1.0 + std::sqrt((1.0 - mu) * (1.0 + mu)));
+}
+
+// Asymptotic convergence factor per sweep of FP64 red-black SOR on the
+// homogeneous pressure system (b = 0) from a pseudo-random start.  The
+// residual's infinity norm is read every 64 sweeps until it has fallen by
+// 1e-10 (well above the rounding floor) or S sweeps have run; the factor is
+// taken over the second half of the sweeps run.
+int sor_rate(ibm_ctx* c, double* x, const double* zero, double omega, int S, double* rho) {
+  const Geo& g = c->geo;
+  const int C = 64;
+  CUDA_TRY(cudaMemsetAsync(x, 0, c->nelem * sizeof(double), c->stream));
+  launch_fill_hash(c->stream, g, x);
+  std::vector<double> r;
+  for (int s = 0;; s += C) {
+    double v = 0.0;
+    CUDA_TRY(cudaMemsetAsync(&c->sc->res_bits, 0, 8, c->stream));
+    launch_poisson_res(c->stream, g, x, zero, &c->sc->res_bits);
+    int rc = read_norm(c, &c->sc->res_bits, &v);
+    if (rc) return rc;
+    r.push_back(v);
+    c->prof.launches += 1;
+    if (!(v > 1e-10 * r[0]) || s + C > S) break;
+    for (int k = 0; k < C; ++k) {
+      launch_poisson_half(c->stream, g, x, zero, c->invd_p, 0, omega);
+      launch_poisson_half(c->stream, g, x, zero, c->invd_p, 1, omega);
+    }
+    c->prof.launches += 2 * C;
+  }
+  CUDA_TRY(cudaGetLastError());
+  const int b = (int)r.size() - 1, a = b / 2;
+  *rho = (b > a && r[a] > 0.0 && r[b] > 0.0) ? std::pow(r[b] / r[a], 1.0 / (C * (b - a))) : 0.0;
+  return IBM_OK;
+}
+
+int tune_omega(ibm_ctx* c, int S, double* out) {
+  if (S <= 0) {
+    S = 8 * (c->nx > c->ny ? c->nx : c->ny);
+    S = S < 2048 ? 2048 : (S > 32768 ? 32768 : S);
+  }
+  double *x = nullptr, *zero = nullptr;
+  CUDA_TRY(cudaMalloc((void**)&x, c->nelem * sizeof(double)));
+  if (cudaMalloc((void**)&zero, c->nelem * sizeof(double)) != cudaSuccess) {
+    cudaFree(x);
+    return fail(IBM_E_CUDA, "tune_omega: allocation failed");
+  }
+  int rc = cudaMemsetAsync(zero, 0, c->nelem * sizeof(double), c->stream) == cudaSuccess ? IBM_OK : IBM_E_CUDA;
+  const double w0 = c->P.omega_p;
+  double rho0 = 0.0, rho1 = 0.0, w1 = w0;
+  if (!rc) rc = sor_rate(c, x, zero, w0, S, &rho0);
+  if (!rc) w1 = omega_from_rate(w0, rho0);
+  if (!rc && w1 != w0) rc = sor_rate(c, x, zero, w1, S, &rho1);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(x);
+  cudaFree(zero);
+  if (rc) return rc;
+  if (w1 != w0 && rho1 > 0.0 && rho1 < rho0) c->P.omega_p = w1;
+  *out = c->P.omega_p;
+  return IBM_OK;
+}
+
 // Defect correction: FP64 residual and update around FP32 red-black SOR
 // sweeps on the correction equation.  The number of inner sweeps between two
 // FP64 checks adapts to the observed convergence rate.
@@ -495,6 +569,7 @@ int solve_poisson_mixed(ibm_ctx* c, double tol, int maxs, int* sweeps, double* r
       CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
       c->prof.sweep_ms += ms;
       c->prof.sweep_launches += pending;
+      c->prof.sweep_cells += (long long)pending * c->nx * c->ny;
       pending = 0;
     }
     *sweeps = s;
@@ -939,7 +1014,10 @@ int batch_solve(ibm_batch* B, const std::vector<double>& thr, std::vector<ibm_st
     if (B->profiling) {
       CUDA_TRY(cudaEventRecord(B->t0, B->stream));
       timing = true;
+      long long cells = 0;
+      for (int i : act) cells += (long long)B->cs[i]->nx * B->cs[i]->ny;
       B->prof.sweep_launches += 2 * (round / pair_sweeps);
+      B->prof.sweep_cells += cells * 2 * (round / pair_sweeps);
     }
     rc = batch_sweeps(B, (int)act.size(), tiles, round / pair_sweeps);
     if (rc) return rc;
@@ -1376,6 +1454,15 @@ int ibm_batch_step(ibm_batch* B, int nsteps, ibm_step_stats* last) {
     for (int i = 0; i < n; ++i) last[i] = B->cs[i]->last;
   return IBM_OK;
 }
+
+double ibm_omega_from_rate(double omega, double rho) { return omega_from_rate(omega, rho); }
+
+int ibm_tune_omega(ibm_ctx* c, int sweeps, double* omega) {
+  if (!c || !omega) return fail(IBM_E_INVAL, "null argument");
+  return tune_omega(c, sweeps, omega);
+}
+
+void* ibm_batch_stream(const ibm_batch* B) { return B ? (void*)B->stream : nullptr; }
 
 int ibm_batch_set_graphs(ibm_batch* B, int on) {
   if (!B) return fail(IBM_E_INVAL, "null batch");

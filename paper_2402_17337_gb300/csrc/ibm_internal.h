@@ -104,6 +104,7 @@ void launch_poisson_res(cudaStream_t s, const Geo& g, const double* phi, const d
                         unsigned long long* res_bits);
 void launch_shift(cudaStream_t s, const Geo& g, double* phi, const DevScalars* sc);
 void launch_bmax(cudaStream_t s, const Geo& g, const double* b, unsigned long long* bits);
+void launch_fill_hash(cudaStream_t s, const Geo& g, double* x);
 void launch_helm_half(cudaStream_t s, const Geo& g, int grid, double* x, const double* R, const double* invd,
                       const Band& band, const uint8_t* fl, const double* al, int colour, double omega,
                       double beta, double Ub);

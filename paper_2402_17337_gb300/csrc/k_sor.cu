@@ -190,9 +190,27 @@ __global__ void k_shift(Geo g, double* __restrict__ phi, const DevScalars* __res
   if (i < g.nx && j < g.ny) phi[at(i, j, g.pitch)] -= sc->phi_ref;
 }
 
+// x = pseudo-random values in [-1, 1) on the interior cells (an integer
+// hash of the cell index; any field with all modes present serves)
+__global__ void k_fill_hash(Geo g, double* __restrict__ x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  unsigned h = (unsigned)i * 0x9E3779B1u ^ ((unsigned)j + 0x7F4A7C15u) * 0x85EBCA77u;
+  h ^= h >> 16;
+  h *= 0x7FEB352Du;
+  h ^= h >> 15;
+  h *= 0x846CA68Bu;
+  h ^= h >> 16;
+  x[at(i, j, g.pitch)] = (double)(h >> 8) * (1.0 / 8388608.0) - 1.0;
+}
+
 inline dim3 grid2(int nx, int ny) { return dim3((nx + TBX - 1) / TBX, (ny + TBY - 1) / TBY); }
 
 }  // namespace
+
+void launch_fill_hash(cudaStream_t s, const Geo& g, double* x) {
+  k_fill_hash<<<grid2(g.nx, g.ny), dim3(TBX, TBY), 0, s>>>(g, x);
+}
 
 void launch_shift(cudaStream_t s, const Geo& g, double* phi, const DevScalars* sc) {
   k_shift<<<grid2(g.nx, g.ny), dim3(TBX, TBY), 0, s>>>(g, phi, sc);

@@ -101,7 +101,9 @@ def evaluate(cfg, net, cT, steps, start, precision=1, stream=None):
 
 
 def save(path, net, cT, meta):
-    os.makedirs(os.path.dirname(path), exist_ok=True)
+    d = os.path.dirname(path)
+    if d:
+        os.makedirs(d, exist_ok=True)
     np.savez_compressed(path, params=net.params(), widths=np.array(net.widths), cT=cT, meta=json.dumps(meta))
 
 

@@ -7,18 +7,23 @@ tests take their inputs from it.
 Configurations (non-dimensional, chord = U_inf = 1).  The 192x128 case starts
 from rest; the stretched cases start from the uniform free stream (at
 divergence 1e-8 the first pressure increment of a start from rest lies below
-the FP64 resolution of the pressure residual on those grids).
+the FP64 resolution of the pressure residual on those grids).  The stretched
+cases take the paper's ratio of time step to minimum spacing (Sec. 4:
+spacing 0.004, time step 1e-4, i.e. dt = 0.025 hmin): the flow round the
+thin ellipse's leading edge at the plunge's effective incidence is several
+times the free stream, and the explicit convection goes unstable at ratios
+near 0.2.
   plunge_192x128   uniform 192x128 on [-4,8]x[-4,4], ellipse t/c 0.12, Re 300,
                    h 0.25, k 2, dt 2e-3, 100 steps, divergence 1e-10 (Poisson residual 1e-10/dt).
   plunge_2048x1024 stretched 2048x1024 on the paper's domain [-7.5,24]x[-12.5,12.5]
-                   (Sec. 2.3), min spacing 0.005, Re 1000, h 0.25, k 2, dt 1e-3,
+                   (Sec. 2.3), min spacing 0.005, Re 1000, h 0.25, k 2, dt 1.25e-4,
                    divergence 1e-8 (Poisson residual 1e-8/dt).
   plunge_4096x2048 stretched 4096x2048, min spacing 0.0025, Re 1000, h 0.4, k 3,
-                   dt 5e-4, divergence 1e-8.
+                   dt 6.25e-5, divergence 1e-8.
   batch64          64 cases, numpy default_rng(17337): h~U[0.1,0.5], k~U[1,4],
                    Re~U[100,1000], nx uniform on {512,576,...,1536}, ny = nx/2;
-                   min spacing 10/nx (uniform block ~30 % of nx), dt = 0.25 hmin/(1+k h).
-  unet_1024x512    1024x512, min spacing 0.01, dt 2e-3.
+                   min spacing 10/nx (uniform block ~30 % of nx), dt = 0.025 hmin.
+  unet_1024x512    1024x512, min spacing 0.01, dt 2.5e-4.
 """
 from __future__ import annotations
 
@@ -28,6 +33,7 @@ import math
 import numpy as np
 
 PAPER_DOMAIN = (-7.5, 24.0, -12.5, 12.5)
+DT_PER_HMIN = 0.025  # the paper's time step over its grid spacing (Sec. 4)
 UBOX = (-1.0, 2.0, -0.75, 0.75)
 
 
@@ -91,13 +97,13 @@ def plunge_192x128() -> FlowConfig:
 
 
 def plunge_2048x1024() -> FlowConfig:
-    dt = 1e-3
+    dt = DT_PER_HMIN * 0.005
     return FlowConfig("plunge_2048x1024", *PAPER_DOMAIN, 2048, 1024, 0.005, Re=1000.0, dt=dt,
                       steps=2000, h=0.25, k=2.0, div_tol=1e-8, init="uniform")
 
 
 def plunge_4096x2048() -> FlowConfig:
-    dt = 5e-4
+    dt = DT_PER_HMIN * 0.0025
     return FlowConfig("plunge_4096x2048", *PAPER_DOMAIN, 4096, 2048, 0.0025, Re=1000.0, dt=dt,
                       steps=500, h=0.4, k=3.0, div_tol=1e-8, init="uniform")
 
@@ -113,7 +119,7 @@ def batch64(n: int = 64, seed: int = 17337) -> list[FlowConfig]:
         nx = int(rng.choice(sizes))
         ny = nx // 2
         hmin = 10.0 / nx
-        dt = 0.25 * hmin / (1.0 + k * h)
+        dt = DT_PER_HMIN * hmin
         out.append(FlowConfig(f"batch64[{c}]", *PAPER_DOMAIN, nx, ny, hmin, Re=Re, dt=dt, steps=1000,
                               h=h, k=k, div_tol=1e-8, init="uniform"))
     return out
@@ -131,14 +137,14 @@ def batch_small(n: int = 4, seed: int = 17337, sizes=(96, 112, 128, 144, 160, 17
         Re = float(rng.uniform(100.0, 1000.0))
         nx = int(rng.choice(np.asarray(sizes)))
         hmin = 10.0 / nx
-        dt = 0.25 * hmin / (1.0 + k * h)
+        dt = DT_PER_HMIN * hmin
         out.append(FlowConfig(f"batch_small[{c}]", *PAPER_DOMAIN, nx, nx // 2, hmin, Re=Re, dt=dt, steps=5,
                               h=h, k=k, div_tol=1e-10, init="uniform"))
     return out
 
 
 def unet_1024x512() -> FlowConfig:
-    dt = 2e-3
+    dt = DT_PER_HMIN * 0.01
     return FlowConfig("unet_1024x512", *PAPER_DOMAIN, 1024, 512, 0.01, Re=300.0, dt=dt, steps=1000,
                       div_tol=1e-10, init="uniform")
 
