@@ -152,7 +152,9 @@ int ibm_get_grid(const ibm_ctx* ctx, double* xf, double* yf);
  * ||b - L_p phi||_inf <= tol checked every check_every sweeps (precision 1:
  * FP32 sweeps inside FP64 defect correction, checked in FP64 after whole
  * launches of the tuned tile, so sweep counts and the max_sweeps cap are
- * rounded up to a multiple of the sweeps per launch), then shifts
+ * rounded up to a multiple of the sweeps per launch; check_every is the
+ * length of the first run of FP32 sweeps, later runs adapt to the observed
+ * convergence rate), then shifts
  * phi so that the cell (nx-1, 0) is zero.  b_dev, phi_dev: device pointers
  * to nx*ny doubles in the compact layout; phi_dev holds the initial guess
  * and receives the result (on IBM_E_NOCONV: the last iterate, unshifted).
@@ -213,6 +215,7 @@ typedef struct {
                                 half-sweeps per launch, thread rows (0 if not tuned) */
   double sor_us_per_sweep;   /* its measured time per full sweep, microseconds */
   long long sweep_cells;     /* cells covered by the timed sweep launches, summed over launches */
+  int sor_form;              /* form of that sweep kernel (3, 4 or 5; 0 if not tuned) */
 } ibm_profile;
 
 /* Autotuner of the FP32 sweep kernel (precision 1): times each tile shape on
@@ -220,6 +223,13 @@ typedef struct {
  * before the first mixed-precision solve; calling it re-tunes.  A no-op for
  * precision 0.  Uses the context's work arrays: not during a step. */
 int ibm_tune(ibm_ctx* ctx);
+
+/* Tile shapes of the FP32 sweep kernel: their number, and a fixed choice
+ * for the context (index 0 .. n-1; -1 returns to the autotuner on the next
+ * mixed-precision solve).  Every shape performs the same red-black SOR
+ * iterates; they differ in speed only. */
+int ibm_sor_num_shapes(void);
+int ibm_set_sor_shape(ibm_ctx* ctx, int index);
 
 /* Relaxation factor of the pressure SOR (Sec. 2.2 leaves it free) from the
  * observed convergence: red-black SOR runs on the homogeneous pressure

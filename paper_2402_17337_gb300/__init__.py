@@ -51,7 +51,8 @@ class StepStats(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("launches", C.c_longlong), ("sweep_launches", C.c_longlong), ("sweep_ms", C.c_double),
                 ("steps", C.c_longlong), ("poisson_sweeps", C.c_longlong), ("helm_sweeps", C.c_longlong),
-                ("sor_shape", C.c_int * 3), ("sor_us_per_sweep", C.c_double), ("sweep_cells", C.c_longlong)]
+                ("sor_shape", C.c_int * 3), ("sor_us_per_sweep", C.c_double), ("sweep_cells", C.c_longlong),
+                ("sor_form", C.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -99,6 +100,8 @@ def lib():
             L.ibm_get_sample.argtypes = [_VP, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_int),
                                          C.POINTER(C.c_int)]
             L.ibm_tune_omega.argtypes = [_VP, C.c_int, _D]
+            L.ibm_set_sor_shape.argtypes = [_VP, C.c_int]
+            L.ibm_sor_num_shapes.argtypes = []
             L.ibm_omega_from_rate.argtypes = [C.c_double, C.c_double]
             L.ibm_omega_from_rate.restype = C.c_double
             L.ibm_batch_create.argtypes = [C.POINTER(_VP), C.c_int, C.POINTER(_VP)]
@@ -125,6 +128,10 @@ def _check(rc):
 
 def _dp(a):
     return a.ctypes.data_as(_D)
+
+
+def num_sor_shapes():
+    return lib().ibm_sor_num_shapes()
 
 
 def omega_from_rate(omega, rho):
@@ -242,6 +249,10 @@ class Solver:
         p = Profile()
         _check(lib().ibm_get_profile(self._h, C.byref(p)))
         return p.as_dict()
+
+    def set_sor_shape(self, index):
+        """Fixes the FP32 sweep tile shape (index into the library's table; -1: autotune)."""
+        _check(lib().ibm_set_sor_shape(self._h, index))
 
     def tune_omega(self, sweeps=0):
         """Sets the pressure SOR relaxation factor from the observed convergence; returns it."""

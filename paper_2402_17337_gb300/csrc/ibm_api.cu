@@ -1313,6 +1313,7 @@ int ibm_poisson_solve(ibm_ctx* c, const double* b_dev, double* phi_dev, double t
   int s = 0;
   double r = 0.0;
   const int maxs = max_sweeps > 0 ? max_sweeps : c->P.max_sweeps;
+  if (c->P.precision == 1 && check_every > 0) c->m_inner = check_every;  // first run of FP32 sweeps
   int rc = c->P.precision == 1 ? solve_poisson_mixed(c, tol, maxs, &s, &r)
                                : solve_poisson(c, tol, 0.0, check_every, maxs, &s, &r);
   if (sweeps) *sweeps = s;
@@ -1345,7 +1346,8 @@ int ibm_get_profile(const ibm_ctx* c, ibm_profile* out) {
   *out = c->prof;
   out->sor_shape[0] = out->sor_shape[1] = out->sor_shape[2] = 0;
   out->sor_us_per_sweep = c->sor_us;
-  if (c->sor_cfg >= 0) sor32_describe(c->sor_cfg, &out->sor_shape[0], &out->sor_shape[1], &out->sor_shape[2]);
+  if (c->sor_cfg >= 0)
+    sor32_describe(c->sor_cfg, &out->sor_shape[0], &out->sor_shape[1], &out->sor_shape[2], &out->sor_form);
   return IBM_OK;
 }
 
@@ -1385,6 +1387,21 @@ int ibm_get_sample(const ibm_ctx* c, float* feat, float* target, int* Hc, int* W
   if (feat) CUDA_TRY(cudaMemcpyAsync(feat, c->ws_feat, 4 * nc * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   if (target) CUDA_TRY(cudaMemcpyAsync(target, c->ws_target, nc * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return IBM_OK;
+}
+
+int ibm_sor_num_shapes(void) { return sor32_num_configs(); }
+
+int ibm_set_sor_shape(ibm_ctx* c, int index) {
+  if (!c) return fail(IBM_E_INVAL, "null context");
+  if (index < -1 || index >= sor32_num_configs())
+    return fail(IBM_E_INVAL, "sweep shape %d out of range (-1 .. %d)", index, sor32_num_configs() - 1);
+  if (index >= 0) {
+    cudaError_t e = sor32_batch_prepare(index);
+    if (e != cudaSuccess) return fail(IBM_E_CUDA, "sweep shape %d: %s", index, cudaGetErrorString(e));
+  }
+  c->sor_cfg = index;
+  c->sor_us = 0.0;
   return IBM_OK;
 }
 
@@ -1481,7 +1498,7 @@ int ibm_batch_set_profiling(ibm_batch* B, int on) {
 int ibm_batch_get_profile(const ibm_batch* B, ibm_profile* out) {
   if (!B || !out) return fail(IBM_E_INVAL, "null argument");
   *out = B->prof;
-  if (B->cfg >= 0) sor32_describe(B->cfg, &out->sor_shape[0], &out->sor_shape[1], &out->sor_shape[2]);
+  if (B->cfg >= 0) sor32_describe(B->cfg, &out->sor_shape[0], &out->sor_shape[1], &out->sor_shape[2], &out->sor_form);
   out->sor_us_per_sweep = B->sor_us;
   for (ibm_ctx* c : B->cs) {
     out->launches += c->prof.launches;

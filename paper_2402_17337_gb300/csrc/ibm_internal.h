@@ -153,7 +153,7 @@ void set_last_error(const char* msg);
 // mixed precision: FP64 update + residual, FP32 temporally blocked sweeps
 int sor32_num_configs();
 int sor32_half_sweeps(int cfg);  // half-sweeps per launch of tile shape cfg (even)
-void sor32_describe(int cfg, int* rows_per_tile, int* half_sweeps, int* thread_rows);
+void sor32_describe(int cfg, int* rows_per_tile, int* half_sweeps, int* thread_rows, int* form);
 void launch_dc_residual(cudaStream_t s, const Geo& g, int pk, const double* phi_in, double* phi_out,
                         const float* e, const double* b, float* r32, int add_e, unsigned long long* res_bits);
 void launch_sor32(cudaStream_t s, int cfg, const Geo32& g, const float* e_in, float* e_out, const float* r,

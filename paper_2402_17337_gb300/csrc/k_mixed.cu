@@ -245,18 +245,181 @@ __device__ __forceinline__ void sor32_tile(const Geo32& g, const float* __restri
   }
 }
 
-template <int TY, int K, int NY>
-__global__ void __launch_bounds__(32 * NY, 2)
+// Second form of the tile sweep (same iterates, fewer instructions per
+// update).  The region is stored with one zero row and column on each side
+// and cells outside the domain carry r = 0 and a zero reciprocal diagonal,
+// so every cell of the region is updated without a test: a cell outside the
+// domain stays exactly zero, and a cell on the region's edge takes wrong
+// values that, like any value spoiled by the region's finite size, move
+// inwards by one cell per half-sweep (the written tile is K cells inside).
+// Because NY is even, the colour parity s of a thread's cells is the same in
+// all its rows, so coefficient selection and neighbour offsets are fixed per
+// thread and colour; of the W and E neighbours one is the thread's own cell
+// of the other colour (register) and the other is read from shared memory.
+// The arithmetic of an update is the same as in sor32_tile, in the same
+// order, so both forms give identical iterates.  With RDREG the right-hand
+// side and reciprocal diagonal of a thread's cells stay in registers.
+template <int TY, int K, int NY, bool RDREG>
+struct Sor32ShapeV4 {
+  static constexpr int LK = 64, HK = (K + 1) / 2, TK = LK - 2 * HK, LY = TY + 2 * K;
+  static constexpr int RPT = LY / NY, PY = LY + 2, PK = LK + 2;
+  static constexpr size_t smem = sizeof(float) * (RDREG ? 2 : 6) * PY * PK;
+  static_assert(LY % NY == 0, "rows per thread must be whole");
+  static_assert(NY % 2 == 0, "an even number of thread rows keeps a thread's colour parity fixed");
+};
+
+template <int TY, int K, int NY, bool RDREG>
+__device__ __forceinline__ void sor32_tile_v4(const Geo32& g, const float* __restrict__ e_in, float* __restrict__ e_out,
+                                              const float* __restrict__ r, const float* __restrict__ invd,
+                                              float omega, int zero_init, int bx, int by, float* smem) {
+  using S = Sor32ShapeV4<TY, K, NY, RDREG>;
+  constexpr int HK = S::HK, TK = S::TK, LY = S::LY, RPT = S::RPT, PY = S::PY, PK = S::PK;
+  float(*se)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem);  // [2][PY][PK], cell (ly, kk) at [ly+1][kk+1]
+  float(*sr)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem + 2 * PY * PK);
+  float(*sd)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem + 4 * PY * PK);
+  const int nx = g.nx, ny = g.ny, pk = g.pk;
+  const int k0 = bx * TK - HK, j0 = by * TY - K;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int sc[2] = {(j0 + ty) & 1, (1 + j0 + ty) & 1};  // colour c sits at i = 2k + sc[c] in all rows of this thread
+  // zero padding of the correction (rows -1 and LY, columns -1 and LK)
+  for (int t = ty * 32 + tx; t < 2 * (2 * PK + 2 * LY); t += 32 * NY) {
+    const int c = t / (2 * PK + 2 * LY), u = t % (2 * PK + 2 * LY);
+    if (u < 2 * PK)
+      se[c][u < PK ? 0 : PY - 1][u % PK] = 0.f;
+    else
+      se[c][1 + (u - 2 * PK) / 2][(u & 1) ? PK - 1 : 0] = 0.f;
+  }
+  float ev[2][RPT][2];
+  float rv[RDREG ? 2 : 1][RDREG ? RPT : 1][2], dv[RDREG ? 2 : 1][RDREG ? RPT : 1][2];
+  float ce[2][2], cw[2][2], cN[RPT], cS[RPT];
+  unsigned live = 0u;  // bit (c, q, m): inside the domain (written back)
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const int k = k0 + tx + 32 * m;
+    const bool ok = k >= 0 && k < pk;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      ce[c][m] = ok ? (sc[c] ? g.cE1[k] : g.cE0[k]) : 0.f;
+      cw[c][m] = ok ? (sc[c] ? g.cW1[k] : g.cW0[k]) : 0.f;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int ly = ty + NY * q, j = j0 + ly;
+    const bool rowok = j >= 0 && j < ny;
+    cN[q] = rowok ? g.pN[j] : 0.f;
+    cS[q] = rowok ? g.pS[j] : 0.f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int kk = tx + 32 * m, k = k0 + kk, i = 2 * k + sc[c];
+        const bool in = rowok && k >= 0 && i < nx;
+        const size_t o = (size_t)(c * ny + j) * pk + k;
+        const float x = (in && !zero_init) ? e_in[o] : 0.f;
+        const float rr = in ? r[o] : 0.f, dd = in ? invd[o] : 0.f;
+        ev[c][q][m] = x;
+        se[c][ly + 1][kk + 1] = x;
+        if constexpr (RDREG) {
+          rv[c][q][m] = rr;
+          dv[c][q][m] = dd;
+        } else {
+          sr[c][ly + 1][kk + 1] = rr;
+          sd[c][ly + 1][kk + 1] = dd;
+        }
+        if (in) live |= 1u << ((c * RPT + q) * 2 + m);
+      }
+  }
+  __syncthreads();
+  auto half = [&](auto colour) {
+    constexpr int c = decltype(colour)::value, oc = c ^ 1;
+    const int s = sc[c];
+    const int off = s ? 2 : 0;  // padded column of the neighbour of the other colour in shared memory: kk+1 -/+ 1
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int ly = ty + NY * q;
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int kk = tx + 32 * m;
+        const float xSelf = ev[oc][q][m];                 // the other colour in this packed column
+        const float xOther = se[oc][ly + 1][kk + off];    // the other colour one packed column away
+        const float xN = se[oc][ly + 2][kk + 1], xS = se[oc][ly][kk + 1];
+        const float xE = s ? xOther : xSelf, xW = s ? xSelf : xOther;
+        float sum = ce[c][m] * xE;
+        sum = fmaf(cw[c][m], xW, sum);
+        sum = fmaf(cN[q], xN, sum);
+        sum = fmaf(cS[q], xS, sum);
+        float rr, dd;
+        if constexpr (RDREG) {
+          rr = rv[c][q][m];
+          dd = dv[c][q][m];
+        } else {
+          rr = sr[c][ly + 1][kk + 1];
+          dd = sd[c][ly + 1][kk + 1];
+        }
+        const float gs = (sum - rr) * dd;
+        const float x = ev[c][q][m];
+        const float nxv = fmaf(omega, gs - x, x);
+        ev[c][q][m] = nxv;
+        se[c][ly + 1][kk + 1] = nxv;
+      }
+    }
+    __syncthreads();
+  };
+#pragma unroll 1
+  for (int h = 0; h < K; h += 2) {
+    half(std::integral_constant<int, 0>{});
+    half(std::integral_constant<int, 1>{});
+  }
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int ly = ty + NY * q;
+    if (ly < K || ly >= K + TY) continue;
+    const int j = j0 + ly;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int kk = tx + 32 * m;
+        if (kk < HK || kk >= HK + TK) continue;
+        if (!(live >> ((c * RPT + q) * 2 + m) & 1u)) continue;
+        e_out[(size_t)(c * ny + j) * pk + (k0 + kk)] = ev[c][q][m];
+      }
+  }
+}
+
+// A tile shape: rows per tile, half-sweeps per launch, thread rows, form
+// (3: sor32_tile; 4: sor32_tile_v4 with r and 1/d in shared memory; 5: with
+// r and 1/d in registers) and minimum resident CTAs per SM.
+template <int TY_, int K_, int NY_, int V_, int MINB_>
+struct Cfg {
+  static constexpr int TY = TY_, K = K_, NY = NY_, V = V_, MINB = MINB_;
+  static constexpr int HK = (K + 1) / 2, TK = 64 - 2 * HK;
+  static constexpr size_t smem =
+      std::conditional_t<V == 3, Sor32Shape<TY, K, NY>, Sor32ShapeV4<TY, K, NY, V == 5>>::smem;
+};
+
+template <class C>
+__device__ __forceinline__ void tile(const Geo32& g, const float* e_in, float* e_out, const float* r,
+                                     const float* invd, float omega, int zero_init, int bx, int by, float* smem) {
+  if constexpr (C::V == 3)
+    sor32_tile<C::TY, C::K, C::NY>(g, e_in, e_out, r, invd, omega, zero_init, bx, by, smem);
+  else
+    sor32_tile_v4<C::TY, C::K, C::NY, C::V == 5>(g, e_in, e_out, r, invd, omega, zero_init, bx, by, smem);
+}
+
+template <class C>
+__global__ void __launch_bounds__(32 * C::NY, C::MINB)
     k_sor32_rb(const Geo32 g, const float* __restrict__ e_in, float* __restrict__ e_out, const float* __restrict__ r,
                const float* __restrict__ invd, float omega, int zero_init) {
   extern __shared__ float smem[];
-  sor32_tile<TY, K, NY>(g, e_in, e_out, r, invd, omega, zero_init, blockIdx.x, blockIdx.y, smem);
+  tile<C>(g, e_in, e_out, r, invd, omega, zero_init, blockIdx.x, blockIdx.y, smem);
 }
 
 // Batched form: one launch sweeps the tiles of many cases (uneven grids).
 // CTA b belongs to the case whose tile range [first, first + count) holds b.
-template <int TY, int K, int NY>
-__global__ void __launch_bounds__(32 * NY, 2)
+template <class C>
+__global__ void __launch_bounds__(32 * C::NY, C::MINB)
     k_sor32_rb_batch(const Sor32Case* __restrict__ cases, int ncases, int zero_init) {
   extern __shared__ float smem[];
   __shared__ Sor32Case c;  // the case's descriptor, read from shared memory where needed
@@ -271,73 +434,75 @@ __global__ void __launch_bounds__(32 * NY, 2)
   }
   __syncthreads();
   const int t = b - c.first;
-  sor32_tile<TY, K, NY>(c.g, c.e_in, c.e_out, c.r, c.invd, c.omega, zero_init, t % c.tiles_x, t / c.tiles_x, smem);
+  tile<C>(c.g, c.e_in, c.e_out, c.r, c.invd, c.omega, zero_init, t % c.tiles_x, t / c.tiles_x, smem);
 }
 
-// Tile shapes the autotuner chooses from: (rows per tile, half-sweeps per
-// launch, thread rows).
+// Tile shapes the autotuner chooses from.
 struct Sor32Config {
-  int TY, K, NY;
+  int TY, K, NY, V;
   void (*launch)(cudaStream_t, const Geo32&, const float*, float*, const float*, const float*, float, int);
   void (*launch_batch)(cudaStream_t, const Sor32Case*, int, int, int);
-  cudaError_t (*prepare_batch)();
+  cudaError_t (*prepare)();
   void (*tiles)(const Geo32&, int*, int*);
 };
 
-template <int TY, int K, int NY>
+// dynamic shared memory limits of both kernels of a shape; set once, outside
+// any stream capture
+template <class C>
+cudaError_t prepare_shape() {
+  cudaError_t e = cudaFuncSetAttribute(k_sor32_rb<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_sor32_rb_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+}
+
+template <class C>
 void launch_shape(cudaStream_t s, const Geo32& g, const float* e_in, float* e_out, const float* r, const float* invd,
                   float omega, int zero_init) {
-  using S = Sor32Shape<TY, K, NY>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_sor32_rb<TY, K, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
+    prepare_shape<C>();
     attr = true;
   }
   const int ncol = (g.nx + 1) / 2;
-  dim3 grd((ncol + S::TK - 1) / S::TK, (g.ny + TY - 1) / TY);
-  k_sor32_rb<TY, K, NY><<<grd, dim3(32, NY), S::smem, s>>>(g, e_in, e_out, r, invd, omega, zero_init);
+  dim3 grd((ncol + C::TK - 1) / C::TK, (g.ny + C::TY - 1) / C::TY);
+  k_sor32_rb<C><<<grd, dim3(32, C::NY), C::smem, s>>>(g, e_in, e_out, r, invd, omega, zero_init);
 }
 
-template <int TY, int K, int NY>
+template <class C>
 void launch_shape_batch(cudaStream_t s, const Sor32Case* cases, int ncases, int total_tiles, int zero_init) {
-  using S = Sor32Shape<TY, K, NY>;
   if (total_tiles <= 0) return;
-  k_sor32_rb_batch<TY, K, NY><<<total_tiles, dim3(32, NY), S::smem, s>>>(cases, ncases, zero_init);
+  k_sor32_rb_batch<C><<<total_tiles, dim3(32, C::NY), C::smem, s>>>(cases, ncases, zero_init);
 }
 
-// dynamic shared memory limit of the batched kernel; set once, outside any
-// stream capture
-template <int TY, int K, int NY>
-cudaError_t prepare_shape_batch() {
-  using S = Sor32Shape<TY, K, NY>;
-  return cudaFuncSetAttribute(k_sor32_rb_batch<TY, K, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)S::smem);
-}
-
-template <int TY, int K, int NY>
+template <class C>
 void shape_tiles(const Geo32& g, int* tx, int* ty) {
-  using S = Sor32Shape<TY, K, NY>;
-  *tx = ((g.nx + 1) / 2 + S::TK - 1) / S::TK;
-  *ty = (g.ny + TY - 1) / TY;
+  *tx = ((g.nx + 1) / 2 + C::TK - 1) / C::TK;
+  *ty = (g.ny + C::TY - 1) / C::TY;
 }
 
-#define SOR32_SHAPE(a, b, c) \
-  { a, b, c, launch_shape<a, b, c>, launch_shape_batch<a, b, c>, prepare_shape_batch<a, b, c>, shape_tiles<a, b, c> }
+template <class C>
+constexpr Sor32Config shape() {
+  return {C::TY, C::K, C::NY, C::V, launch_shape<C>, launch_shape_batch<C>, prepare_shape<C>, shape_tiles<C>};
+}
+
 const Sor32Config kConfigs[] = {
-    SOR32_SHAPE(32, 8, 16), SOR32_SHAPE(48, 8, 16),  SOR32_SHAPE(16, 8, 8),
-    SOR32_SHAPE(32, 4, 8),  SOR32_SHAPE(64, 16, 16), SOR32_SHAPE(32, 12, 16),
+    shape<Cfg<32, 8, 16, 3, 2>>(),  shape<Cfg<48, 8, 16, 3, 2>>(),  shape<Cfg<16, 8, 8, 3, 2>>(),
+    shape<Cfg<32, 4, 8, 3, 2>>(),   shape<Cfg<64, 16, 16, 3, 2>>(), shape<Cfg<32, 12, 16, 3, 2>>(),
+    shape<Cfg<32, 8, 16, 4, 2>>(),  shape<Cfg<48, 8, 16, 4, 2>>(),  shape<Cfg<40, 12, 16, 4, 2>>(),
+    shape<Cfg<16, 8, 8, 4, 3>>(),   shape<Cfg<24, 4, 8, 4, 3>>(),   shape<Cfg<64, 16, 16, 4, 1>>(),
+    shape<Cfg<16, 8, 8, 5, 2>>(),   shape<Cfg<32, 8, 16, 5, 1>>(),  shape<Cfg<24, 4, 8, 5, 2>>(),
 };
-#undef SOR32_SHAPE
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
 }  // namespace
 
 int sor32_num_configs() { return kNumConfigs; }
 int sor32_half_sweeps(int cfg) { return kConfigs[cfg].K; }
-void sor32_describe(int cfg, int* ty, int* k, int* ny) {
+void sor32_describe(int cfg, int* ty, int* k, int* ny, int* form) {
   *ty = kConfigs[cfg].TY;
   *k = kConfigs[cfg].K;
   *ny = kConfigs[cfg].NY;
+  *form = kConfigs[cfg].V;
 }
 
 void launch_dc_residual(cudaStream_t s, const Geo& g, int pk, const double* phi_in, double* phi_out, const float* e,
@@ -353,7 +518,7 @@ void launch_sor32(cudaStream_t s, int cfg, const Geo32& g, const float* e_in, fl
 
 void sor32_tiles(int cfg, const Geo32& g, int* tiles_x, int* tiles_y) { kConfigs[cfg].tiles(g, tiles_x, tiles_y); }
 
-cudaError_t sor32_batch_prepare(int cfg) { return kConfigs[cfg].prepare_batch(); }
+cudaError_t sor32_batch_prepare(int cfg) { return kConfigs[cfg].prepare(); }
 
 void launch_sor32_batch(cudaStream_t s, int cfg, const Sor32Case* cases_dev, int ncases, int total_tiles,
                         int zero_init) {
