@@ -290,6 +290,12 @@ int ibm_unet_train_step(ibm_unet* net, const float* feat_dev, const float* targe
  * s0 the norm of the residual feature and c_T = target_scale. */
 int ibm_set_warmstart(ibm_ctx* ctx, int mode, ibm_unet* net, double target_scale);
 
+/* Base guess of the warm start (any mode): 0, the previous increment
+ * phi^n (default); 1, its linear extrapolation in time 2 phi^n - phi^{n-1}
+ * (the history starts when the base is set: the first step after it uses
+ * phi^n).  The learned form predicts the change from the base guess. */
+int ibm_set_warmstart_base(ibm_ctx* ctx, int base);
+
 /* Last recorded sample (mode 2): feat [Hc][Wc][4] and target [Hc][Wc]
  * (host, FP32); either may be NULL; *Hc, *Wc receive the coarse sizes. */
 int ibm_get_sample(const ibm_ctx* ctx, float* feat, float* target, int* Hc, int* Wc);

@@ -97,6 +97,7 @@ def lib():
             L.ibm_unet_train_step.argtypes = [_VP, _VP, _VP, C.c_int, C.c_int, C.c_float, C.c_int,
                                               C.POINTER(C.c_double), _VP]
             L.ibm_set_warmstart.argtypes = [_VP, C.c_int, _VP, C.c_double]
+            L.ibm_set_warmstart_base.argtypes = [_VP, C.c_int]
             L.ibm_get_sample.argtypes = [_VP, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_int),
                                          C.POINTER(C.c_int)]
             L.ibm_tune_omega.argtypes = [_VP, C.c_int, _D]
@@ -265,6 +266,10 @@ class Solver:
         """0: previous increment; 1: learned (U-Net net); 2: previous increment + samples."""
         self._ws_net = net  # keep the network alive while the context uses it
         _check(lib().ibm_set_warmstart(self._h, mode, net._h if net is not None else None, target_scale))
+
+    def set_warmstart_base(self, base):
+        """0: previous increment; 1: linear extrapolation 2 phi^n - phi^(n-1)."""
+        _check(lib().ibm_set_warmstart_base(self._h, base))
 
     def sample(self):
         """(features [Hc][Wc][4], target [Hc][Wc]) recorded by the last step (mode 2)."""

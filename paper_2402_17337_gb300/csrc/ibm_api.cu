@@ -141,6 +141,8 @@ struct ibm_ctx {
   ibm_step_stats last{};
   // warm start: 0 previous increment, 1 learned (U-Net), 2 previous increment + sample capture
   int ws_mode = 0;
+  int ws_base = 0;             // base guess: 0 previous increment, 1 linear extrapolation in time
+  double* phi_prev = nullptr;  // increment of the previous step (ws_base 1)
   ibm_unet* ws_net = nullptr;
   double ws_cT = 1.0;
   int Hc = 0, Wc = 0;
@@ -672,8 +674,13 @@ int step_pre(ibm_ctx* c, ibm_step_stats* st, double* thr) {
     launch_body_source(c->stream, g, c->band, c->fc, c->uh, c->vh, c->b, c->qband, dt, c->rowsum, c->sc);
     c->prof.launches += 3;
   }
-  // a7: warm start.  The solve starts from the previous increment; the
-  // learned form adds the U-Net's prediction of the change.
+  // a7: warm start.  The solve starts from the previous increment, or from
+  // its linear extrapolation in time; the learned form adds the U-Net's
+  // prediction of the remaining change.
+  if (c->ws_base == 1) {
+    launch_extrapolate(c->stream, g, c->phi, c->phi_prev);
+    c->prof.launches += 1;
+  }
   if (c->ws_mode) {
     launch_ws_features(c->stream, g, c->Hc, c->Wc, c->b, c->phi, c->p, c->band, c->fc, c->ws_feat, c->ws_max);
     c->prof.launches += 2;
@@ -1374,6 +1381,19 @@ int ibm_set_warmstart(ibm_ctx* c, int mode, ibm_unet* net, double target_scale) 
   c->ws_net = net;
   c->ws_cT = mode ? target_scale : 1.0;
   c->has_sample = false;
+  return IBM_OK;
+}
+
+int ibm_set_warmstart_base(ibm_ctx* c, int base) {
+  if (!c) return fail(IBM_E_INVAL, "null context");
+  if (base != 0 && base != 1) return fail(IBM_E_INVAL, "warm-start base must be 0 or 1");
+  if (base == 1 && !c->phi_prev) {
+    int rc = c->alloc(&c->phi_prev, c->nelem);
+    if (rc) return rc;
+  }
+  if (base == 1 && c->ws_base == 0)  // no history yet: the first extrapolation is the previous increment
+    CUDA_TRY(cudaMemcpyAsync(c->phi_prev, c->phi, c->nelem * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  c->ws_base = base;
   return IBM_OK;
 }
 

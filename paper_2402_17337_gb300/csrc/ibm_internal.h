@@ -138,7 +138,8 @@ void launch_sor32_batch(cudaStream_t s, int cfg, const Sor32Case* cases_dev, int
                         int zero_init);
 void launch_dc_residual_batch(cudaStream_t s, const DcCase* cases_dev, int ncases, int total_blocks);
 
-// learned warm start (k_ws.cu): coarse features, prediction, targets
+// learned warm start (k_ws.cu): coarse features, prediction, targets; base guess
+void launch_extrapolate(cudaStream_t s, const Geo& g, double* phi, double* phi_prev);
 void launch_ws_features(cudaStream_t s, const Geo& g, int Hc, int Wc, const double* b, const double* phi,
                         const double* p, const Band& band, const uint8_t* fc, float* feat,
                         unsigned long long* ws_max);

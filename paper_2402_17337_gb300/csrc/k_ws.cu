@@ -98,7 +98,23 @@ __global__ void k_ws_target(Geo g, int Hc, int Wc, const double* __restrict__ ph
   target[(size_t)J * Wc + I] = s0 > 0.0 ? (float)(0.25 * d / (s0 * cT)) : 0.f;
 }
 
+// Linear extrapolation of the pressure increment in time: phi <- 2 phi^n -
+// phi^{n-1}, and phi_prev <- phi^n for the next step.
+__global__ void k_extrapolate(Geo g, double* __restrict__ phi, double* __restrict__ phi_prev) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  const size_t c = at(i, j, g.pitch);
+  const double a = phi[c];
+  phi[c] = 2.0 * a - phi_prev[c];
+  phi_prev[c] = a;
+}
+
 }  // namespace
+
+void launch_extrapolate(cudaStream_t s, const Geo& g, double* phi, double* phi_prev) {
+  dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
+  k_extrapolate<<<grd, blk, 0, s>>>(g, phi, phi_prev);
+}
 
 void launch_ws_features(cudaStream_t s, const Geo& g, int Hc, int Wc, const double* b, const double* phi,
                         const double* p, const Band& band, const uint8_t* fc, float* feat,
