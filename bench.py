@@ -481,6 +481,7 @@ def main():
     prof, clk, launches, start_state = main_run["prof"], main_run["clocks"], main_run["launches"], main_run["state"]
     fp64_run = timed_run(0, False) if (precision == 1 and not args.no_fp64_compare) else None
     plain_ws_run = timed_run(1, False) if (learned is not None and not args.no_fp64_compare) else None
+    mg_run = timed_run(2, False) if (precision == 1 and not args.no_fp64_compare) else None
 
     # roofline of the dominant kernel
     peaks, peak_src = load_peaks()
@@ -579,6 +580,14 @@ def main():
             plain_ws = {"value": plain_ws_run["value"], "ms_per_step": plain_ws_run["ms"] / args.steps,
                         "poisson_sweeps_per_step": statistics.mean(st["sweeps_p"] for st in plain_ws_run["stats"]),
                         "speedup_of_value": value / plain_ws_run["value"]}
+        mg = None
+        if mg_run:
+            mg = {"value": mg_run["value"], "ms_per_step": mg_run["ms"] / args.steps,
+                  "vcycles_per_step": statistics.mean(st["sweeps_p"] for st in mg_run["stats"]),
+                  "speedup_of_value": mg_run["value"] / value,
+                  "note": "variant, not the paper's solver: FP32 geometric-multigrid V(2,2)-cycles (red-black "
+                          "Gauss-Seidel smoothing, bilinear prolongation) inside the same FP64 defect correction "
+                          "and stopping rule; previous-increment warm start"}
         ws_desc = "previous increment"
         if learned is not None:
             m = learned["meta"]
@@ -595,7 +604,7 @@ def main():
             "config": {"workload": cfg.name, "nx": cfg.nx, "ny": cfg.ny, "global_batch": world,
                        "parallelism": f"replicas x{world}", "path": args.precision, "warm_start": ws_desc,
                        "omega_p": cfg.omega_p, "omega_p_grid_formula": omega_default,
-                       "mixed_plain_warmstart": plain_ws, "plain_fp64": fp64,
+                       "mixed_plain_warmstart": plain_ws, "plain_fp64": fp64, "multigrid_variant": mg,
                        "steps_counted": total_ok, "poisson_sweeps_per_step": statistics.mean(sweeps),
                        "helm_sweeps_per_step": statistics.mean(st["sweeps_u"] + st["sweeps_v"] for st in stats),
                        "l2": "state 14 FP64 fields x 17 MB > L2; no flush",

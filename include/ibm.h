@@ -57,7 +57,16 @@ typedef struct ibm_ctx ibm_ctx;
  *                   free-slip walls at y0,y1;  1: free-slip walls all round
  *   Re, dt       Reynolds number and time step
  *   precision    0: FP64 throughout;  1: FP32 SOR sweeps inside FP64 defect
- *                correction (residuals, updates, norms and forces in FP64)
+ *                correction (residuals, updates, norms and forces in FP64);
+ *                2: as 1 with FP32 geometric-multigrid V-cycles as the inner
+ *                solver (a variant; the paper's solver is SOR, Sec. 2.2): the
+ *                stretched grid is coarsened by merging cell pairs, every level
+ *                carries the five-point operator rediscretised from its faces,
+ *                residuals are restricted as volume-weighted averages,
+ *                corrections prolonged piecewise constant, smoothing is two
+ *                red-black Gauss-Seidel sweeps before and after, the coarsest
+ *                level (<= 64 cells) is solved by SOR; the same FP64 stopping
+ *                rule; sweeps_p then counts V-cycles
  *   poisson_tol  the pressure solve stops when
  *   poisson_rtol ||b - L_p phi||_inf <= max(poisson_tol, poisson_rtol*||b||_inf);
  *                the divergence left in fluid cells is dt times that residual
@@ -87,7 +96,7 @@ typedef struct {
 typedef struct {
   int n;                 /* steps completed */
   double t;              /* time after the step */
-  int sweeps_u, sweeps_v, sweeps_p;
+  int sweeps_u, sweeps_v, sweeps_p;  /* sweeps per solve (precision 2: sweeps_p counts V-cycles) */
   double res_u, res_v, res_p;
   double div_max;        /* max |div u| over cells whose centre is in the fluid */
   double cl, cd;         /* lift and drag coefficients of the step */

@@ -125,6 +125,14 @@ struct ibm_ctx {
   int m_inner = 32;  // inner sweeps between FP64 checks (adapted)
   int sor_cfg = -1;          // tile shape of the FP32 sweeps, -1: not tuned yet
   double sor_us = 0.0;       // its measured time per full sweep
+  // geometric multigrid on the correction equation (precision 2)
+  std::vector<MgLevel> mg;
+  int mg_shape = -1;                                 // tile shape of the smoother
+  int mg_cycles = 2;                                 // V-cycles between FP64 checks (adapted)
+  int mg_coarse_sweeps = 0;
+  float mg_coarse_omega = 1.f;
+  cudaGraphExec_t mg_graph[2] = {nullptr, nullptr};  // one V-cycle: from e = 0 / continuing
+  bool mg_graph_failed = false;
   // body and band
   bool has_body = false;
   double chord = 1, tc = 0.12, h = 0, k = 0, xb = 0, yb0 = 0;
@@ -156,6 +164,8 @@ struct ibm_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
   ~ibm_ctx() {
+    for (cudaGraphExec_t g : mg_graph)
+      if (g) cudaGraphExecDestroy(g);
     for (void* a : allocs) cudaFree(a);
     if (sc_host) cudaFreeHost(sc_host);
     if (cl_d) cudaFree(cl_d);
@@ -186,6 +196,33 @@ struct ibm_ctx {
 };
 
 namespace {
+
+// Five-point coefficients per unit volume on the cells between the faces xf,
+// yf (homogeneous Neumann: no coupling across the domain boundary); the same
+// formulas as the fine grid's.
+void laplace_coefs(const std::vector<double>& xf, std::vector<double>& pE, std::vector<double>& pW) {
+  const int n = (int)xf.size() - 1;
+  std::vector<double> dx(n), xc(n);
+  for (int i = 0; i < n; ++i) {
+    dx[i] = xf[i + 1] - xf[i];
+    xc[i] = 0.5 * (xf[i] + xf[i + 1]);
+  }
+  pE.assign(n, 0.0);
+  pW.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    if (i < n - 1) pE[i] = 1.0 / (dx[i] * (xc[i + 1] - xc[i]));
+    if (i > 0) pW[i] = 1.0 / (dx[i] * (xc[i] - xc[i - 1]));
+  }
+}
+
+std::vector<double> coarse_faces(const std::vector<double>& xf) {
+  const int n = (int)xf.size() - 1, nc = (n + 1) / 2;
+  std::vector<double> out(nc + 1);
+  for (int I = 0; I <= nc; ++I) out[I] = xf[2 * I < n ? 2 * I : n];
+  return out;
+}
+
+int build_mg(ibm_ctx* c);
 
 int setup_geometry(ibm_ctx* c) {
   const int nx = c->nx, ny = c->ny;
@@ -303,7 +340,7 @@ int setup_geometry(ibm_ctx* c) {
   c->invd_p = const_cast<double*>(a);
   c->invd_u = const_cast<double*>(bb);
   c->invd_v = const_cast<double*>(cc);
-  if (c->P.precision == 1) {
+  if (c->P.precision >= 1) {
     // colour-split FP32 data of the inner sweeps (Geo32)
     Geo32& g32 = c->geo32;
     const int pk = ((nx + 1) / 2 + 31) / 32 * 32;
@@ -337,6 +374,7 @@ int setup_geometry(ibm_ctx* c) {
     if (rc) return IBM_E_CUDA;
     c->invd32 = const_cast<float*>(d32);
   }
+  if (c->P.precision == 2) return build_mg(c);
   return IBM_OK;
 }
 
@@ -364,6 +402,236 @@ double bits_to_double(unsigned long long b) {
   double d;
   std::memcpy(&d, &b, 8);
   return d;
+}
+
+int read_norm(ibm_ctx* c, const unsigned long long* dev_bits, double* out);
+
+// Level hierarchy of the multigrid: level 0 is the fine grid (its FP32
+// arrays are those of the inner sweeps); each coarser level merges pairs of
+// cells in both directions until at most 64 cells remain.
+int build_mg(ibm_ctx* c) {
+  c->mg_shape = sor32_find_shape(24, 4, 4);
+  if (c->mg_shape < 0) return fail(IBM_E_CUDA, "multigrid smoother shape missing");
+  CUDA_TRY(sor32_batch_prepare(c->mg_shape));
+  std::vector<double> xf = c->xf, yf = c->yf;
+  int rc = 0;
+  for (int l = 0;; ++l) {
+    const int nx = (int)xf.size() - 1, ny = (int)yf.size() - 1;
+    std::vector<double> pE, pW, pN, pS;
+    laplace_coefs(xf, pE, pW);
+    laplace_coefs(yf, pN, pS);
+    MgLevel L{};
+    L.cur = 0;
+    std::vector<float> pe(nx), pw(nx);
+    for (int i = 0; i < nx; ++i) pe[i] = (float)pE[i], pw[i] = (float)pW[i];
+    rc |= c->upload(&L.pE, pe);
+    rc |= c->upload(&L.pW, pw);
+    if (l == 0) {
+      L.g = c->geo32;
+      L.e[0] = c->e32;
+      L.e[1] = c->e32b;
+      L.r = c->r32;
+      L.invd = c->invd32;
+    } else {
+      Geo32& g = L.g;
+      const int pk = ((nx + 1) / 2 + 31) / 32 * 32;
+      g.nx = nx;
+      g.ny = ny;
+      g.pk = pk;
+      std::vector<float> ce0(pk, 0.f), ce1(pk, 0.f), cw0(pk, 0.f), cw1(pk, 0.f), pn(ny), ps(ny);
+      for (int k = 0; k < pk; ++k) {
+        if (2 * k < nx) ce0[k] = (float)pE[2 * k], cw0[k] = (float)pW[2 * k];
+        if (2 * k + 1 < nx) ce1[k] = (float)pE[2 * k + 1], cw1[k] = (float)pW[2 * k + 1];
+      }
+      for (int j = 0; j < ny; ++j) pn[j] = (float)pN[j], ps[j] = (float)pS[j];
+      rc |= c->upload(&g.cE0, ce0);
+      rc |= c->upload(&g.cE1, ce1);
+      rc |= c->upload(&g.cW0, cw0);
+      rc |= c->upload(&g.cW1, cw1);
+      rc |= c->upload(&g.pN, pn);
+      rc |= c->upload(&g.pS, ps);
+      const size_t n32 = (size_t)2 * ny * pk;
+      std::vector<float> ip(n32, 0.f);
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          const float d = (float)pE[i] + (float)pW[i] + (float)pN[j] + (float)pS[j];
+          ip[rb_at(i, j, ny, pk)] = d > 0.f ? 1.0f / d : 0.f;
+        }
+      rc |= c->upload(&L.invd, ip);
+      rc |= c->alloc(&L.e[0], n32);
+      rc |= c->alloc(&L.e[1], n32);
+      rc |= c->alloc(&L.r, n32);
+    }
+    const bool last = (long)nx * ny <= 64 || (nx <= 2 && ny <= 2) || l == 15;
+    if (!last) {
+      // restriction weights: a cell's share of its parent's width
+      std::vector<double> xfc = coarse_faces(xf), yfc = coarse_faces(yf);
+      std::vector<float> wx(nx), wy(ny);
+      for (int i = 0; i < nx; ++i) wx[i] = (float)((xf[i + 1] - xf[i]) / (xfc[i / 2 + 1] - xfc[i / 2]));
+      for (int j = 0; j < ny; ++j) wy[j] = (float)((yf[j + 1] - yf[j]) / (yfc[j / 2 + 1] - yfc[j / 2]));
+      rc |= c->upload(&L.wx, wx);
+      rc |= c->upload(&L.wy, wy);
+      // bilinear prolongation: each fine centre between its parent's centre
+      // and the centre of the parent's neighbour on its side
+      auto interp = [](const std::vector<double>& f, const std::vector<double>& fc, std::vector<int>& o,
+                       std::vector<float>& a) {
+        const int n = (int)f.size() - 1, ncoarse = (int)fc.size() - 1;
+        o.assign(n, 0);
+        a.assign(n, 0.f);
+        for (int i = 0; i < n; ++i) {
+          const int I = i / 2;
+          const double x = 0.5 * (f[i] + f[i + 1]), X = 0.5 * (fc[I] + fc[I + 1]);
+          const int side = x < X ? -1 : (x > X ? 1 : 0);
+          const int I2 = I + side;
+          if (side == 0 || I2 < 0 || I2 >= ncoarse) continue;  // at the boundary: zero slope
+          const double X2 = 0.5 * (fc[I2] + fc[I2 + 1]);
+          o[i] = side;
+          a[i] = (float)((x - X) / (X2 - X));
+        }
+      };
+      std::vector<int> ox, oy;
+      std::vector<float> ax, ay;
+      interp(xf, xfc, ox, ax);
+      interp(yf, yfc, oy, ay);
+      rc |= c->upload(&L.ox, ox);
+      rc |= c->upload(&L.oy, oy);
+      rc |= c->upload(&L.ax, ax);
+      rc |= c->upload(&L.ay, ay);
+      xf.swap(xfc);
+      yf.swap(yfc);
+    }
+    if (rc) return IBM_E_CUDA;
+    c->mg.push_back(L);
+    if (last) {
+      if ((long)nx * ny > mg_coarse_max()) return fail(IBM_E_INVAL, "multigrid: coarsest level too large");
+      const int m = nx > ny ? nx : ny;
+      c->mg_coarse_omega = (float)(2.0 / (1.0 + std::sin(M_PI / (m + 1))));
+      c->mg_coarse_sweeps = 4 * (nx + ny) + 16;
+      break;
+    }
+  }
+  return IBM_OK;
+}
+
+// One V(2,2)-cycle on the correction equation of level 0: smoothing by two
+// red-black Gauss-Seidel sweeps (one tile launch of four half-sweeps) before
+// and after the coarse-grid correction.  Each level's correction ends in the
+// buffer it started in, so the launch sequence is the same every cycle.
+void mg_vcycle(ibm_ctx* c, int zero_first) {
+  const int n = (int)c->mg.size();
+  for (int l = 0; l < n - 1; ++l) {
+    MgLevel& A = c->mg[l];
+    launch_sor32(c->stream, c->mg_shape, A.g, A.e[A.cur], A.e[A.cur ^ 1], A.r, A.invd, 1.0f, l > 0 || zero_first);
+    A.cur ^= 1;
+    launch_mg_restrict(c->stream, A, A.e[A.cur], c->mg[l + 1]);
+  }
+  MgLevel& Z = c->mg[n - 1];
+  launch_mg_coarse(c->stream, Z, Z.e[Z.cur], c->mg_coarse_omega, c->mg_coarse_sweeps);
+  for (int l = n - 2; l >= 0; --l) {
+    MgLevel& A = c->mg[l];
+    const MgLevel& B = c->mg[l + 1];
+    launch_mg_prolong(c->stream, B, B.e[B.cur], A, A.e[A.cur]);
+    launch_sor32(c->stream, c->mg_shape, A.g, A.e[A.cur], A.e[A.cur ^ 1], A.r, A.invd, 1.0f, 0);
+    A.cur ^= 1;
+  }
+  c->prof.launches += 4 * (n - 1) + 1;
+}
+
+// CUDA graphs of one V-cycle (from e = 0 and continuing); direct launches if
+// the stream cannot be captured.
+void mg_capture(ibm_ctx* c) {
+  if (c->mg_graph[0] || c->mg_graph_failed) return;
+  for (int z = 0; z < 2; ++z) {
+    cudaGraph_t g = nullptr;
+    const long long launches = c->prof.launches;
+    bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      mg_vcycle(c, z == 0);
+      ok = cudaStreamEndCapture(c->stream, &g) == cudaSuccess;
+    }
+    c->prof.launches = launches;
+    if (ok) ok = cudaGraphInstantiate(&c->mg_graph[z], g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+      cudaGetLastError();
+      for (cudaGraphExec_t& e : c->mg_graph)
+        if (e) cudaGraphExecDestroy(e), e = nullptr;
+      c->mg_graph_failed = true;
+      return;
+    }
+  }
+}
+
+int mg_cycles(ibm_ctx* c, int m) {
+  const int per = 4 * ((int)c->mg.size() - 1) + 1;
+  for (int k = 0; k < m; ++k) {
+    if (c->mg_graph[0]) {
+      CUDA_TRY(cudaGraphLaunch(c->mg_graph[k == 0 ? 0 : 1], c->stream));
+      c->prof.launches += per;
+    } else {
+      mg_vcycle(c, k == 0);
+    }
+  }
+  return IBM_OK;
+}
+
+// Defect correction with FP32 V-cycles as the inner solver: FP64 update,
+// residual and norm as in solve_poisson_mixed; the number of V-cycles per
+// check adapts to the observed reduction per cycle, aiming at the tolerance
+// or at a reduction of 1e-4 (about the resolution of an FP32 correction).
+// *cycles receives the V-cycles performed.
+int solve_poisson_mg(ibm_ctx* c, double tol, int maxc, int* cycles, double* res) {
+  const Geo& g = c->geo;
+  mg_capture(c);
+  MgLevel& L0 = c->mg[0];
+  double* cur = c->phi;
+  double* alt = c->phi2;
+  int s = 0, add = 0, m = 0;
+  double prev = 0.0;
+  bool timing = false;
+  for (;;) {
+    if (timing) CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+    CUDA_TRY(cudaMemsetAsync(&c->sc->res_bits, 0, 8, c->stream));
+    launch_dc_residual(c->stream, g, c->geo32.pk, cur, alt, L0.e[L0.cur], c->b, L0.r, add, &c->sc->res_bits);
+    c->prof.launches += 1;
+    if (add) std::swap(cur, alt);
+    double r;
+    int rc = read_norm(c, &c->sc->res_bits, &r);
+    if (rc) return rc;
+    if (timing) {
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+      c->prof.sweep_ms += ms;
+      timing = false;
+    }
+    *cycles = s;
+    *res = r;
+    c->phi = cur;
+    c->phi2 = alt;
+    if (!std::isfinite(r)) return fail(IBM_E_DIVERGED, "pressure residual is not finite after %d V-cycles", s);
+    if (r <= tol) return IBM_OK;
+    if (s >= maxc) return fail(IBM_E_NOCONV, "pressure solve: %d V-cycles, residual %.3e > %.3e", s, r, tol);
+    if (m > 0 && prev > r && r > 0.0) {
+      const double rate = std::log(r / prev) / m;  // per cycle, < 0
+      double target = std::log(tol / r);
+      if (target < std::log(1e-4)) target = std::log(1e-4);
+      const int want = (int)std::ceil(target / rate);
+      c->mg_cycles = want < 1 ? 1 : (want > 64 ? 64 : want);
+    }
+    m = c->mg_cycles;
+    if (s + m > maxc) m = maxc - s;
+    if (c->profiling) {
+      CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+      timing = true;
+      c->prof.sweep_launches += (long long)m * (4 * ((int)c->mg.size() - 1) + 1);
+      c->prof.sweep_cells += (long long)m * c->nx * c->ny;
+    }
+    rc = mg_cycles(c, m);
+    if (rc) return rc;
+    prev = r;
+    s += m;
+    add = 1;
+  }
 }
 
 // Reads one norm accumulator back (waits for the stream).
@@ -759,7 +1027,9 @@ int one_step(ibm_ctx* c) {
   double thr;
   int rc = step_pre(c, &st, &thr);
   if (rc) return rc;
-  if (c->P.precision == 1)
+  if (c->P.precision == 2)
+    rc = solve_poisson_mg(c, thr, c->P.max_sweeps, &st.sweeps_p, &st.res_p);
+  else if (c->P.precision == 1)
     rc = solve_poisson_mixed(c, thr, c->P.max_sweeps, &st.sweeps_p, &st.res_p);
   else
     rc = solve_poisson(c, c->P.poisson_tol, c->P.poisson_rtol, c->P.check_every_p, c->P.max_sweeps, &st.sweeps_p,
@@ -1102,7 +1372,7 @@ int ibm_create_grid(const ibm_grid_params* params, ibm_ctx** out) {
   if (P.ny > 8192) return fail(IBM_E_INVAL, "ny must be <= 8192 (outflow flux reduction)");
   if (!(P.Re > 0.0) || !(P.dt > 0.0)) return fail(IBM_E_INVAL, "Re and dt must be positive");
   if (P.bc != 0 && P.bc != 1) return fail(IBM_E_INVAL, "bc must be 0 or 1");
-  if (P.precision != 0 && P.precision != 1) return fail(IBM_E_INVAL, "precision must be 0 or 1");
+  if (P.precision < 0 || P.precision > 2) return fail(IBM_E_INVAL, "precision must be 0, 1 or 2");
   if (P.omega_p <= 0.0) P.omega_p = 2.0 / (1.0 + std::sin(M_PI / (P.nx > P.ny ? P.nx : P.ny)));
   if (P.omega_h <= 0.0) P.omega_h = 1.0;
   if (!(P.omega_p < 2.0) || !(P.omega_h < 2.0)) return fail(IBM_E_INVAL, "omega must lie in (0, 2)");
@@ -1321,8 +1591,9 @@ int ibm_poisson_solve(ibm_ctx* c, const double* b_dev, double* phi_dev, double t
   double r = 0.0;
   const int maxs = max_sweeps > 0 ? max_sweeps : c->P.max_sweeps;
   if (c->P.precision == 1 && check_every > 0) c->m_inner = check_every;  // first run of FP32 sweeps
-  int rc = c->P.precision == 1 ? solve_poisson_mixed(c, tol, maxs, &s, &r)
-                               : solve_poisson(c, tol, 0.0, check_every, maxs, &s, &r);
+  int rc = c->P.precision == 2   ? solve_poisson_mg(c, tol, maxs, &s, &r)
+           : c->P.precision == 1 ? solve_poisson_mixed(c, tol, maxs, &s, &r)
+                                 : solve_poisson(c, tol, 0.0, check_every, maxs, &s, &r);
   if (sweeps) *sweeps = s;
   if (res) *res = r;
   if (rc && rc != IBM_E_NOCONV) return rc;

@@ -138,6 +138,24 @@ void launch_sor32_batch(cudaStream_t s, int cfg, const Sor32Case* cases_dev, int
                         int zero_init);
 void launch_dc_residual_batch(cudaStream_t s, const DcCase* cases_dev, int ncases, int total_blocks);
 
+// geometric multigrid on the FP32 correction equation (k_mg.cu)
+struct MgLevel {
+  Geo32 g;              // split-colour coefficients of this level (smoothing by the tile kernel)
+  const float *pE, *pW;  // the same coefficients by column (nx entries), rows in g.pN, g.pS
+  const float *wx, *wy;  // restriction weights of this level's cells into the next coarser level
+  const int *ox, *oy;    // prolongation from the next coarser level: neighbour of the parent (-1, 0, +1)
+  const float *ax, *ay;  //   and the neighbour's interpolation weight, per column / row
+  float* e[2];           // correction (ping-pong of the tile kernel)
+  float* r;              // right-hand side
+  const float* invd;     // reciprocal diagonal
+  int cur;               // buffer holding the current correction
+};
+int mg_coarse_max();
+void launch_mg_restrict(cudaStream_t s, const MgLevel& F, const float* ef, const MgLevel& C);
+void launch_mg_prolong(cudaStream_t s, const MgLevel& C, const float* ec, const MgLevel& F, float* ef);
+void launch_mg_coarse(cudaStream_t s, const MgLevel& L, float* e_out, float omega, int sweeps);
+int sor32_find_shape(int rows_per_tile, int half_sweeps, int form);
+
 // learned warm start (k_ws.cu): coarse features, prediction, targets; base guess
 void launch_extrapolate(cudaStream_t s, const Geo& g, double* phi, double* phi_prev);
 void launch_ws_features(cudaStream_t s, const Geo& g, int Hc, int Wc, const double* b, const double* phi,

@@ -497,6 +497,11 @@ constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 }  // namespace
 
 int sor32_num_configs() { return kNumConfigs; }
+int sor32_find_shape(int ty, int k, int form) {
+  for (int i = 0; i < kNumConfigs; ++i)
+    if (kConfigs[i].TY == ty && kConfigs[i].K == k && kConfigs[i].V == form) return i;
+  return -1;
+}
 int sor32_half_sweeps(int cfg) { return kConfigs[cfg].K; }
 void sor32_describe(int cfg, int* ty, int* k, int* ny, int* form) {
   *ty = kConfigs[cfg].TY;

@@ -1,0 +1,96 @@
+"""Multigrid variant of the pressure solve (precision 2: FP32 V-cycles inside
+the FP64 defect correction) against the FP64 oracle.
+
+The variant stops at the same FP64 residual tolerance as the oracle's SOR
+(the paper's solver), so the solutions agree to the algebraic error of the
+two solves, ||L^-1|| times the two residuals, and the fields of whole steps
+to the same bound as the SOR mixed path."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_17337_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 1e-6
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def kwargs(cfg):
+    return dict(x0=cfg.x0, x1=cfg.x1, y0=cfg.y0, y1=cfg.y1, nx=cfg.nx, ny=cfg.ny, hmin=cfg.hmin,
+                ubox=cfg.ubox, bc=cfg.bc, u_in=cfg.u_in, Re=cfg.Re, dt=cfg.dt, ptol=cfg.ptol,
+                htol=cfg.htol, check_p=cfg.check_p, check_h=cfg.check_h, omega_p=cfg.omega(),
+                omega_h=cfg.omega_h)
+
+
+@pytest.mark.parametrize("nx,ny,hmin", [(70, 45, 0.0), (261, 133, 0.06), (517, 263, 0.05), (1024, 512, 0.01)])
+def test_mg_poisson_solve_matches_oracle(nx, ny, hmin):
+    import torch
+    from paper_2402_17337_gb300 import Solver, build
+    build.build()
+    kw = dict(x0=-7.5, x1=24.0, y0=-12.5, y1=12.5, nx=nx, ny=ny, hmin=hmin, ubox=(-1.0, 2.0, -0.8, 0.8), dt=1.0)
+    o = oracle.Sim(**kw, threads=8)
+    g = Solver(**kw, precision=2)
+    xf, yf = o.grid()
+    V = np.outer(np.diff(yf), np.diff(xf))
+    b = W.random_field((ny, nx), seed=3 * nx + ny)
+    b -= np.sum(b * V) / np.sum(V)
+    tol = 1e-9 * np.abs(b).max()
+    rc, phio, so, ro = o.poisson(b, tol=tol, check=8, maxs=2000000)
+    assert rc == 0
+    bd = torch.tensor(b, device="cuda")
+    pd = torch.zeros_like(bd)
+    torch.cuda.synchronize()
+    rc, cycles, rg = g.poisson_solve(bd.data_ptr(), pd.data_ptr(), tol, 0, 2000)
+    assert rc == 0 and rg <= tol
+    print(f"{nx}x{ny}: oracle SOR {so} sweeps, multigrid {cycles} V-cycles")
+    # both residuals <= tol: the solutions differ by at most ||L^-1|| * 2 tol
+    xc = 0.5 * (xf[1:] + xf[:-1])
+    inv_bound = 2.0 * (xf[-1] - xf[0]) ** 2  # ||L^-1||_inf on mean-free data, generous
+    d = pd.cpu().numpy() - phio
+    d -= d[0, -1]  # both gauges pin cell (nx-1, 0)
+    assert np.abs(d).max() <= inv_bound * 2 * tol
+    # a V-cycle costs a few fine sweeps; it must replace many more SOR sweeps
+    assert cycles <= so / 8, (cycles, so)
+
+
+@pytest.mark.parametrize("idx", [0, 1])
+def test_mg_steps_match_fp64_oracle(idx):
+    from paper_2402_17337_gb300 import Solver, build
+    build.build()
+    cfg = W.small_cases()[idx]
+    o = oracle.Sim(**kwargs(cfg))
+    g = Solver(**kwargs(cfg), precision=2)
+    for s in (o, g):
+        s.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
+    for n in range(cfg.steps):
+        rc, so = o.step(1)
+        assert rc == 0
+        sg = g.step(1)
+        assert sg["res_p"] <= cfg.ptol and sg["div_max"] <= cfg.div_tol * 1.001
+    errs = {n: rel(g.get(n), o.get(n)) for n in ("u", "v", "p")}
+    print("multigrid vs fp64 oracle, per-field relative error:", errs)
+    assert max(errs.values()) <= MIXED_TOL, errs
+
+
+def test_mg_full_size_steps_agree_with_sor_mixed_path():
+    """Two steps of the 2048x1024 workload: divergence below 1e-8 and the same
+    fields, to the solve tolerance, as the SOR mixed path."""
+    from paper_2402_17337_gb300 import Solver, build
+    build.build()
+    cfg = W.plunge_2048x1024()
+    runs = {}
+    for prec in (1, 2):
+        s = Solver.from_config(cfg, precision=prec)
+        s.set("u", cfg.initial_u(s.shape("u")))
+        st = s.step(2)
+        assert st["div_max"] <= cfg.div_tol * 1.001, (prec, st)
+        runs[prec] = ({f: s.get(f) for f in ("u", "v")}, st)
+        s.close()
+    errs = {f: rel(runs[2][0][f], runs[1][0][f]) for f in ("u", "v")}
+    print("multigrid vs SOR (mixed):", errs, "V-cycles", runs[2][1]["sweeps_p"], "SOR sweeps", runs[1][1]["sweeps_p"])
+    assert max(errs.values()) <= MIXED_TOL
