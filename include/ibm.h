@@ -58,15 +58,16 @@ typedef struct ibm_ctx ibm_ctx;
  *   Re, dt       Reynolds number and time step
  *   precision    0: FP64 throughout;  1: FP32 SOR sweeps inside FP64 defect
  *                correction (residuals, updates, norms and forces in FP64);
- *                2: as 1 with FP32 geometric-multigrid V-cycles as the inner
- *                solver (a variant; the paper's solver is SOR, Sec. 2.2): the
- *                stretched grid is coarsened by merging cell pairs, every level
- *                carries the five-point operator rediscretised from its faces,
- *                residuals are restricted as volume-weighted averages,
- *                corrections prolonged piecewise constant, smoothing is two
- *                red-black Gauss-Seidel sweeps before and after, the coarsest
- *                level (<= 64 cells) is solved by SOR; the same FP64 stopping
- *                rule; sweeps_p then counts V-cycles
+ *                2: as 1 with an FP32 inner solver of geometric multigrid
+ *                (a variant; the paper's solver is SOR, Sec. 2.2): flexible
+ *                conjugate gradients preconditioned by one V(2,2)-cycle per
+ *                iteration; the stretched grid is coarsened by merging cell
+ *                pairs, every level carries the five-point operator
+ *                rediscretised from its faces, residuals are restricted as
+ *                volume-weighted averages, corrections prolonged bilinearly,
+ *                smoothing is red-black Gauss-Seidel, the coarsest level
+ *                (<= 64 cells) is solved by SOR; the same FP64 stopping rule;
+ *                sweeps_p then counts V-cycles
  *   poisson_tol  the pressure solve stops when
  *   poisson_rtol ||b - L_p phi||_inf <= max(poisson_tol, poisson_rtol*||b||_inf);
  *                the divergence left in fluid cells is dt times that residual

@@ -131,8 +131,11 @@ struct ibm_ctx {
   int mg_cycles = 2;                                 // V-cycles between FP64 checks (adapted)
   int mg_coarse_sweeps = 0;
   float mg_coarse_omega = 1.f;
-  cudaGraphExec_t mg_graph[2] = {nullptr, nullptr};  // one V-cycle: from e = 0 / continuing
+  cudaGraphExec_t mg_graph[2] = {nullptr, nullptr};  // one FCG iteration: first / later
   bool mg_graph_failed = false;
+  float *fcg_x = nullptr, *fcg_p = nullptr, *fcg_q = nullptr;  // level-0 FCG vectors
+  double* fcg_sc = nullptr;                                   // <p,Lp>, <p,r>, <z,q>
+  const float *mg_dxv = nullptr, *mg_dyv = nullptr;           // level-0 cell widths (inner products)
   // body and band
   bool has_body = false;
   double chord = 1, tc = 0.12, h = 0, k = 0, xb = 0, yb0 = 0;
@@ -510,7 +513,17 @@ int build_mg(ibm_ctx* c) {
       break;
     }
   }
-  return IBM_OK;
+  const size_t n32 = (size_t)2 * c->ny * c->geo32.pk;
+  std::vector<float> dxv(c->nx), dyv(c->ny);
+  for (int i = 0; i < c->nx; ++i) dxv[i] = (float)(c->xf[i + 1] - c->xf[i]);
+  for (int j = 0; j < c->ny; ++j) dyv[j] = (float)(c->yf[j + 1] - c->yf[j]);
+  rc |= c->upload(&c->mg_dxv, dxv);
+  rc |= c->upload(&c->mg_dyv, dyv);
+  rc |= c->alloc(&c->fcg_x, n32);
+  rc |= c->alloc(&c->fcg_p, n32);
+  rc |= c->alloc(&c->fcg_q, n32);
+  rc |= c->alloc(&c->fcg_sc, 4);
+  return rc ? IBM_E_CUDA : IBM_OK;
 }
 
 // One V(2,2)-cycle on the correction equation of level 0: smoothing by two
@@ -537,8 +550,32 @@ void mg_vcycle(ibm_ctx* c, int zero_first) {
   c->prof.launches += 4 * (n - 1) + 1;
 }
 
-// CUDA graphs of one V-cycle (from e = 0 and continuing); direct launches if
-// the stream cannot be captured.
+// One iteration of flexible conjugate gradients, FCG(1), on level 0's
+// correction equation L x = r (r is level 0's right-hand side, updated in
+// place), preconditioned by one V-cycle: z = V(r); p = z + beta p with
+// beta = -<z, q>/<p, Lp> (p = z first); q = L p; alpha = <p, r>/<p, Lp>;
+// x += alpha p; r -= alpha q.  The Krylov recurrence removes the few error
+// components the V-cycle reduces slowly (cells of large aspect ratio where
+// the stretched directions cross).
+void fcg_iter(ibm_ctx* c, int first) {
+  MgLevel& L0 = c->mg[0];
+  mg_vcycle(c, 1);
+  const float* z = L0.e[L0.cur];
+  if (!first) {
+    cudaMemsetAsync(c->fcg_sc + 2, 0, sizeof(double), c->stream);
+    launch_fcg_dot(c->stream, L0, c->mg_dxv, c->mg_dyv, z, c->fcg_q, c->fcg_sc);
+  }
+  launch_fcg_dir(c->stream, L0, z, c->fcg_p, c->fcg_sc, first);
+  cudaMemsetAsync(c->fcg_sc, 0, 2 * sizeof(double), c->stream);
+  launch_fcg_apply(c->stream, L0, c->mg_dxv, c->mg_dyv, c->fcg_p, L0.r, c->fcg_q, c->fcg_sc);
+  launch_fcg_update(c->stream, L0, c->fcg_p, c->fcg_q, c->fcg_x, L0.r, c->fcg_sc);
+  c->prof.launches += first ? 3 : 4;
+}
+
+int fcg_launches(const ibm_ctx* c) { return 4 * ((int)c->mg.size() - 1) + 1 + 4; }
+
+// CUDA graphs of one FCG iteration (first and later); direct launches if the
+// stream cannot be captured.
 void mg_capture(ibm_ctx* c) {
   if (c->mg_graph[0] || c->mg_graph_failed) return;
   for (int z = 0; z < 2; ++z) {
@@ -546,7 +583,7 @@ void mg_capture(ibm_ctx* c) {
     const long long launches = c->prof.launches;
     bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
-      mg_vcycle(c, z == 0);
+      fcg_iter(c, z == 0);
       ok = cudaStreamEndCapture(c->stream, &g) == cudaSuccess;
     }
     c->prof.launches = launches;
@@ -562,24 +599,26 @@ void mg_capture(ibm_ctx* c) {
   }
 }
 
-int mg_cycles(ibm_ctx* c, int m) {
-  const int per = 4 * ((int)c->mg.size() - 1) + 1;
+int fcg_iters(ibm_ctx* c, int m) {
+  CUDA_TRY(cudaMemsetAsync(c->fcg_x, 0, (size_t)2 * c->ny * c->geo32.pk * sizeof(float), c->stream));
   for (int k = 0; k < m; ++k) {
     if (c->mg_graph[0]) {
       CUDA_TRY(cudaGraphLaunch(c->mg_graph[k == 0 ? 0 : 1], c->stream));
-      c->prof.launches += per;
+      c->prof.launches += fcg_launches(c) - (k == 0 ? 1 : 0);
     } else {
-      mg_vcycle(c, k == 0);
+      fcg_iter(c, k == 0);
     }
   }
+  CUDA_TRY(cudaGetLastError());
   return IBM_OK;
 }
 
-// Defect correction with FP32 V-cycles as the inner solver: FP64 update,
-// residual and norm as in solve_poisson_mixed; the number of V-cycles per
-// check adapts to the observed reduction per cycle, aiming at the tolerance
-// or at a reduction of 1e-4 (about the resolution of an FP32 correction).
-// *cycles receives the V-cycles performed.
+// Defect correction with FP32 multigrid-preconditioned FCG as the inner
+// solver: FP64 update, residual and norm as in solve_poisson_mixed; the
+// number of FCG iterations (one V-cycle each) per check adapts to the
+// observed reduction per iteration, aiming at the tolerance or at a
+// reduction of 1e-4 (about the resolution of an FP32 correction).  *cycles
+// receives the V-cycles performed.
 int solve_poisson_mg(ibm_ctx* c, double tol, int maxc, int* cycles, double* res) {
   const Geo& g = c->geo;
   mg_capture(c);
@@ -592,7 +631,7 @@ int solve_poisson_mg(ibm_ctx* c, double tol, int maxc, int* cycles, double* res)
   for (;;) {
     if (timing) CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
     CUDA_TRY(cudaMemsetAsync(&c->sc->res_bits, 0, 8, c->stream));
-    launch_dc_residual(c->stream, g, c->geo32.pk, cur, alt, L0.e[L0.cur], c->b, L0.r, add, &c->sc->res_bits);
+    launch_dc_residual(c->stream, g, c->geo32.pk, cur, alt, c->fcg_x, c->b, L0.r, add, &c->sc->res_bits);
     c->prof.launches += 1;
     if (add) std::swap(cur, alt);
     double r;
@@ -623,10 +662,10 @@ int solve_poisson_mg(ibm_ctx* c, double tol, int maxc, int* cycles, double* res)
     if (c->profiling) {
       CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
       timing = true;
-      c->prof.sweep_launches += (long long)m * (4 * ((int)c->mg.size() - 1) + 1);
+      c->prof.sweep_launches += (long long)m * fcg_launches(c);
       c->prof.sweep_cells += (long long)m * c->nx * c->ny;
     }
-    rc = mg_cycles(c, m);
+    rc = fcg_iters(c, m);
     if (rc) return rc;
     prev = r;
     s += m;

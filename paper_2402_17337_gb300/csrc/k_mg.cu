@@ -114,7 +114,106 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(MgLevel L, float* __restrict
 
 inline dim3 grid_for(int nx, int ny) { return dim3((nx + 31) / 32, (ny + 7) / 8); }
 
+// ---- flexible conjugate gradients, FCG(1), preconditioned by the V-cycle,
+// on level 0 in the volume-weighted inner product <a, b> = sum V_ij a_ij b_ij
+// (L is self-adjoint in it).  Scalars stay on the device: sc[0] = <p, Lp>,
+// sc[1] = <p, r>, sc[2] = <z, q>.
+
+__device__ inline void block_sum_add(double v, double* dst) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __shared__ double ws[32];
+  const int t = threadIdx.x + threadIdx.y * blockDim.x, lane = t & 31, warp = t >> 5;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+  if (lane == 0) ws[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < nw ? ws[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) atomicAdd(dst, v);
+  }
+}
+
+// sc[2] = <z, q>
+__global__ void k_fcg_dot(const MgLevel L, const float* __restrict__ dxv, const float* __restrict__ dyv,
+                          const float* __restrict__ z, const float* __restrict__ q, double* __restrict__ sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  double v = 0.0;
+  if (i < L.g.nx && j < L.g.ny) {
+    const size_t o = rb_at(i, j, L.g.ny, L.g.pk);
+    v = (double)(dxv[i] * dyv[j]) * (double)z[o] * (double)q[o];
+  }
+  block_sum_add(v, &sc[2]);
+}
+
+// p = z (first) or p = z + beta p, beta = -<z, q> / <p, Lp> of the previous direction
+__global__ void k_fcg_dir(const MgLevel L, const float* __restrict__ z, float* __restrict__ p,
+                          const double* __restrict__ sc, int first) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= L.g.nx || j >= L.g.ny) return;
+  const size_t o = rb_at(i, j, L.g.ny, L.g.pk);
+  if (first) {
+    p[o] = z[o];
+  } else {
+    const float beta = sc[0] != 0.0 ? (float)(-sc[2] / sc[0]) : 0.f;
+    p[o] = fmaf(beta, p[o], z[o]);
+  }
+}
+
+// q = L p, sc[0] += <p, q>, sc[1] += <p, r>
+__global__ void k_fcg_apply(const MgLevel L, const float* __restrict__ dxv, const float* __restrict__ dyv,
+                            const float* __restrict__ p, const float* __restrict__ r, float* __restrict__ q,
+                            double* __restrict__ sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  double vpq = 0.0, vpr = 0.0;
+  const int nx = L.g.nx, ny = L.g.ny, pk = L.g.pk;
+  if (i < nx && j < ny) {
+    const size_t o = rb_at(i, j, ny, pk);
+    const float x = p[o];
+    const float xE = i < nx - 1 ? p[rb_at(i + 1, j, ny, pk)] : x;
+    const float xW = i > 0 ? p[rb_at(i - 1, j, ny, pk)] : x;
+    const float xN = j < ny - 1 ? p[rb_at(i, j + 1, ny, pk)] : x;
+    const float xS = j > 0 ? p[rb_at(i, j - 1, ny, pk)] : x;
+    float Lp = L.pE[i] * (xE - x);
+    Lp = fmaf(L.pW[i], xW - x, Lp);
+    Lp = fmaf(L.g.pN[j], xN - x, Lp);
+    Lp = fmaf(L.g.pS[j], xS - x, Lp);
+    q[o] = Lp;
+    const double V = (double)(dxv[i] * dyv[j]);
+    vpq = V * (double)x * (double)Lp;
+    vpr = V * (double)x * (double)r[o];
+  }
+  block_sum_add(vpq, &sc[0]);
+  block_sum_add(vpr, &sc[1]);
+}
+
+// alpha = <p, r> / <p, Lp>; x += alpha p; r -= alpha q
+__global__ void k_fcg_update(const MgLevel L, const float* __restrict__ p, const float* __restrict__ q,
+                             float* __restrict__ x, float* __restrict__ r, const double* __restrict__ sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= L.g.nx || j >= L.g.ny) return;
+  const size_t o = rb_at(i, j, L.g.ny, L.g.pk);
+  const float alpha = sc[0] != 0.0 ? (float)(sc[1] / sc[0]) : 0.f;
+  x[o] = fmaf(alpha, p[o], x[o]);
+  r[o] = fmaf(-alpha, q[o], r[o]);
+}
+
 }  // namespace
+
+void launch_fcg_dot(cudaStream_t s, const MgLevel& L, const float* dxv, const float* dyv, const float* z,
+                    const float* q, double* sc) {
+  k_fcg_dot<<<grid_for(L.g.nx, L.g.ny), dim3(32, 8), 0, s>>>(L, dxv, dyv, z, q, sc);
+}
+void launch_fcg_dir(cudaStream_t s, const MgLevel& L, const float* z, float* p, const double* sc, int first) {
+  k_fcg_dir<<<grid_for(L.g.nx, L.g.ny), dim3(32, 8), 0, s>>>(L, z, p, sc, first);
+}
+void launch_fcg_apply(cudaStream_t s, const MgLevel& L, const float* dxv, const float* dyv, const float* p,
+                      const float* r, float* q, double* sc) {
+  k_fcg_apply<<<grid_for(L.g.nx, L.g.ny), dim3(32, 8), 0, s>>>(L, dxv, dyv, p, r, q, sc);
+}
+void launch_fcg_update(cudaStream_t s, const MgLevel& L, const float* p, const float* q, float* x, float* r,
+                       const double* sc) {
+  k_fcg_update<<<grid_for(L.g.nx, L.g.ny), dim3(32, 8), 0, s>>>(L, p, q, x, r, sc);
+}
 
 int mg_coarse_max() { return kCoarseMax; }
 
