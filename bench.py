@@ -46,6 +46,9 @@ FP32_FLOPS_PER_CLK_SM = 256.0  # 128 FP32 FMA per clock per SM
 SOR32_BYTES_PER_CELL_LAUNCH = 12  # read e, r; write e (FP32) once per launch
 SOR_FLOPS_PER_UPDATE = 12     # 4 products + 3 adds, minus b, times 1/d, relaxation (2)
 SOR_BYTES_PER_CELL_HALF = 16  # read phi (8, all cells), read b (4), write phi (4) per half-sweep
+# multigrid variant, one FCG iteration per fine cell: smoothing 2 x 12, restriction 9, prolongation 9,
+# FCG dot 8 + direction 12 + operator 12 + update 16, coarser levels a third of smoothing + transfers (14)
+MG_BYTES_PER_CELL_ITER = 104
 WORKLOADS = ("plunge_2048x1024", "batch64")
 METRIC = "cell-steps/s at div<1e-8: learned warm-start+mixed vs plain FP64, one GB300"
 
@@ -363,8 +366,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed",
-                    help="mixed: FP32 sweeps inside FP64 defect correction (the value); fp64: plain FP64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "mg"], default="mixed",
+                    help="mixed: FP32 SOR sweeps inside FP64 defect correction (the value); fp64: plain FP64; "
+                         "mg: the multigrid variant as the timed path")
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -435,7 +439,7 @@ def main():
     probe.close()
 
     learned = None
-    if args.warmstart == "learned" and args.precision == "mixed":
+    if args.warmstart == "learned" and args.precision in ("mixed", "mg"):
         from paper_2402_17337_gb300 import warmstart
         path = args.weights or warmstart.DEFAULT_WEIGHTS
         if not os.path.exists(path):
@@ -473,15 +477,15 @@ def main():
         ok = sum_over_ranks(sum(1 for st in stats if st["div_max"] < cfg.div_tol))
         s.close()
         return {"value": cfg.cells * ok / (ms / 1e3), "ms": ms, "stats": stats, "ok": int(ok), "clocks": clk,
-                "launches": prof["launches"] - prof0["launches"], "prof": prof, "state": state}
+                "launches": prof["launches"] - prof0["launches"], "prof": prof, "prof0": prof0, "state": state}
 
-    precision = 1 if args.precision == "mixed" else 0
+    precision = {"fp64": 0, "mixed": 1, "mg": 2}[args.precision]
     main_run = timed_run(precision, not args.no_clocks, learned)
     value, t_max, stats, total_ok = main_run["value"], main_run["ms"], main_run["stats"], main_run["ok"]
     prof, clk, launches, start_state = main_run["prof"], main_run["clocks"], main_run["launches"], main_run["state"]
-    fp64_run = timed_run(0, False) if (precision == 1 and not args.no_fp64_compare) else None
+    fp64_run = timed_run(0, False) if (precision != 0 and not args.no_fp64_compare) else None
     plain_ws_run = timed_run(1, False) if (learned is not None and not args.no_fp64_compare) else None
-    mg_run = timed_run(2, False) if (precision == 1 and not args.no_fp64_compare) else None
+    mg_run = timed_run(2, False) if (precision != 2 and not args.no_fp64_compare) else None
 
     # roofline of the dominant kernel
     peaks, peak_src = load_peaks()
@@ -492,7 +496,17 @@ def main():
     roof = None
     if prof["sweep_launches"] > 0:
         t_launch = prof["sweep_ms"] / prof["sweep_launches"] / 1e3
-        if precision == 0:
+        if precision == 2:
+            iters = prof["poisson_sweeps"] - main_run["prof0"]["poisson_sweeps"]
+            t_iter = prof["sweep_ms"] / max(iters, 1) / 1e3
+            achieved = MG_BYTES_PER_CELL_ITER * cfg.cells / t_iter / 1e9
+            roof = {"bound": "hbm", "kernel": "multigrid-preconditioned FCG iteration (one V(2,2)-cycle, "
+                                              "FP32, graph-replayed)",
+                    "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": None, "iter_us": t_iter * 1e6,
+                    "peak_note": f"HBM {peaks['hbm_gbs']} GB/s ({peak_src}); algorithmic "
+                                 f"{MG_BYTES_PER_CELL_ITER} B per fine cell per iteration; working set fits in L2"}
+        elif precision == 0:
             flops = SOR_FLOPS_PER_UPDATE * cfg.cells / 2
             achieved = flops / t_launch / 1e12
             roof = {"bound": "alu", "kernel": "k_poisson_half (FP64 red-black SOR half-sweep)",
@@ -591,15 +605,18 @@ def main():
         ws_desc = "previous increment"
         if learned is not None:
             m = learned["meta"]
+            kept = prof["ws_kept"] - main_run["prof0"]["ws_kept"]
+            applied = prof["ws_applied"] - main_run["prof0"]["ws_applied"]
             ws_desc = (f"learned: U-Net widths {tuple(m.get('widths', ()))} on the 2x coarsened grid, trained on "
                        f"{m.get('samples')} snapshots of {m.get('runs')} seeded runs (h, k, Re drawn), BF16 "
-                       f"tensor-core kernels")
+                       f"tensor-core kernels; the learned guess is kept only when its residual is below the "
+                       f"previous increment's: kept in {kept} of {applied} timed steps")
         line = {
             "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": ("f32 sweeps, f64 residual/update/norms" + (", bf16 U-Net" if learned else ""))
-                     if precision == 1 else "f64",
+                     if precision >= 1 else "f64",
             "data": "synthetic",
             "config": {"workload": cfg.name, "nx": cfg.nx, "ny": cfg.ny, "global_batch": world,
                        "parallelism": f"replicas x{world}", "path": args.precision, "warm_start": ws_desc,

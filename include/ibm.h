@@ -226,6 +226,8 @@ typedef struct {
   double sor_us_per_sweep;   /* its measured time per full sweep, microseconds */
   long long sweep_cells;     /* cells covered by the timed sweep launches, summed over launches */
   int sor_form;              /* form of that sweep kernel (3, 4 or 5; 0 if not tuned) */
+  long long ws_applied;      /* steps that evaluated the learned warm start */
+  long long ws_kept;         /* of those, steps whose learned guess had the smaller residual and was kept */
 } ibm_profile;
 
 /* Autotuner of the FP32 sweep kernel (precision 1): times each tile shape on
@@ -292,7 +294,8 @@ int ibm_unet_train_step(ibm_unet* net, const float* feat_dev, const float* targe
 /* Warm start of the pressure solve of each step (Sec. 2.2 solves it by SOR
  * from a starting guess): mode 0, the previous increment; mode 1, the
  * previous increment plus the U-Net's prediction of its change (the net is
- * borrowed, not owned); mode 2, the previous increment and, every step, a
+ * borrowed, not owned), kept only if its residual ||b - L_p phi||_inf is
+ * below that of the previous increment (counted in ibm_profile); mode 2, the previous increment and, every step, a
  * training sample recorded for ibm_get_sample.  The network works on the
  * grid coarsened 2x (nx, ny must be divisible by 16) with four features per
  * coarse cell (initial residual b - L_p phi^n, b, body-cell fraction, p^n,
@@ -340,6 +343,10 @@ int ibm_batch_step(ibm_batch* batch, int nsteps, ibm_step_stats* last);
 /* The batch's own stream (a cudaStream_t), for timing with events; NULL for
  * a NULL batch. */
 void* ibm_batch_stream(const ibm_batch* batch);
+
+/* A fixed FP32 sweep tile shape for the batch (index as for
+ * ibm_set_sor_shape; -1: tuned over the batch on the next step). */
+int ibm_batch_set_sor_shape(ibm_batch* batch, int index);
 
 /* CUDA-graph replay of the sweep launches: on (1, the default) or off (0). */
 int ibm_batch_set_graphs(ibm_batch* batch, int on);

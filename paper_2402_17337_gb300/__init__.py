@@ -52,7 +52,7 @@ class Profile(C.Structure):
     _fields_ = [("launches", C.c_longlong), ("sweep_launches", C.c_longlong), ("sweep_ms", C.c_double),
                 ("steps", C.c_longlong), ("poisson_sweeps", C.c_longlong), ("helm_sweeps", C.c_longlong),
                 ("sor_shape", C.c_int * 3), ("sor_us_per_sweep", C.c_double), ("sweep_cells", C.c_longlong),
-                ("sor_form", C.c_int)]
+                ("sor_form", C.c_int), ("ws_applied", C.c_longlong), ("ws_kept", C.c_longlong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -108,6 +108,7 @@ def lib():
             L.ibm_batch_create.argtypes = [C.POINTER(_VP), C.c_int, C.POINTER(_VP)]
             L.ibm_batch_step.argtypes = [_VP, C.c_int, C.POINTER(StepStats)]
             L.ibm_batch_set_graphs.argtypes = [_VP, C.c_int]
+            L.ibm_batch_set_sor_shape.argtypes = [_VP, C.c_int]
             L.ibm_batch_stream.argtypes = [_VP]
             L.ibm_batch_stream.restype = _VP
             L.ibm_batch_set_profiling.argtypes = [_VP, C.c_int]
@@ -310,6 +311,10 @@ class Batch:
 
     def set_graphs(self, on=True):
         _check(lib().ibm_batch_set_graphs(self._h, 1 if on else 0))
+
+    def set_sor_shape(self, index):
+        """Fixes the FP32 sweep tile shape of the batch (-1: tune over the batch)."""
+        _check(lib().ibm_batch_set_sor_shape(self._h, index))
 
     @property
     def stream(self):

@@ -134,7 +134,7 @@ struct ibm_ctx {
   cudaGraphExec_t mg_graph[2] = {nullptr, nullptr};  // one FCG iteration: first / later
   bool mg_graph_failed = false;
   float *fcg_x = nullptr, *fcg_p = nullptr, *fcg_q = nullptr;  // level-0 FCG vectors
-  double* fcg_sc = nullptr;                                   // <p,Lp>, <p,r>, <z,q>
+  void* fcg_sc = nullptr;                                     // device scalars of the FCG iteration
   const float *mg_dxv = nullptr, *mg_dyv = nullptr;           // level-0 cell widths (inner products)
   // body and band
   bool has_body = false;
@@ -509,7 +509,7 @@ int build_mg(ibm_ctx* c) {
       if ((long)nx * ny > mg_coarse_max()) return fail(IBM_E_INVAL, "multigrid: coarsest level too large");
       const int m = nx > ny ? nx : ny;
       c->mg_coarse_omega = (float)(2.0 / (1.0 + std::sin(M_PI / (m + 1))));
-      c->mg_coarse_sweeps = 4 * (nx + ny) + 16;
+      c->mg_coarse_sweeps = 2 * (nx + ny) + 8;
       break;
     }
   }
@@ -522,7 +522,11 @@ int build_mg(ibm_ctx* c) {
   rc |= c->alloc(&c->fcg_x, n32);
   rc |= c->alloc(&c->fcg_p, n32);
   rc |= c->alloc(&c->fcg_q, n32);
-  rc |= c->alloc(&c->fcg_sc, 4);
+  {
+    unsigned char* scb = nullptr;
+    rc |= c->alloc(&scb, fcg_scalars_bytes());  // zeroed: empty slots, counter 0
+    c->fcg_sc = scb;
+  }
   return rc ? IBM_E_CUDA : IBM_OK;
 }
 
@@ -561,12 +565,8 @@ void fcg_iter(ibm_ctx* c, int first) {
   MgLevel& L0 = c->mg[0];
   mg_vcycle(c, 1);
   const float* z = L0.e[L0.cur];
-  if (!first) {
-    cudaMemsetAsync(c->fcg_sc + 2, 0, sizeof(double), c->stream);
-    launch_fcg_dot(c->stream, L0, c->mg_dxv, c->mg_dyv, z, c->fcg_q, c->fcg_sc);
-  }
+  if (!first) launch_fcg_dot(c->stream, L0, c->mg_dxv, c->mg_dyv, z, c->fcg_q, c->fcg_sc);
   launch_fcg_dir(c->stream, L0, z, c->fcg_p, c->fcg_sc, first);
-  cudaMemsetAsync(c->fcg_sc, 0, 2 * sizeof(double), c->stream);
   launch_fcg_apply(c->stream, L0, c->mg_dxv, c->mg_dyv, c->fcg_p, L0.r, c->fcg_q, c->fcg_sc);
   launch_fcg_update(c->stream, L0, c->fcg_p, c->fcg_q, c->fcg_x, L0.r, c->fcg_sc);
   c->prof.launches += first ? 3 : 4;
@@ -994,10 +994,28 @@ int step_pre(ibm_ctx* c, ibm_step_stats* st, double* thr) {
     if (c->ws_mode == 2)
       CUDA_TRY(cudaMemcpyAsync(c->phi_old, c->phi, c->nelem * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     if (c->ws_mode == 1) {
+      // the plain guess is kept; the learned one replaces it only if it
+      // starts the solve with a smaller residual (the plain iteration is the
+      // fallback and the judge)
       rc = ibm_unet_forward(c->ws_net, c->ws_feat, c->Hc, c->Wc, c->ws_out, c->stream);
       if (rc) return rc;
+      CUDA_TRY(cudaMemcpyAsync(c->phi_old, c->phi, c->nelem * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
       launch_ws_apply(c->stream, g, c->Hc, c->Wc, c->ws_out, c->ws_cT, c->ws_max, c->phi);
-      c->prof.launches += 16;
+      CUDA_TRY(cudaMemsetAsync(&c->sc->res_bits, 0, 8, c->stream));
+      launch_poisson_res(c->stream, g, c->phi, c->b, &c->sc->res_bits);
+      double r_learned = 0.0, r_plain = 0.0;
+      rc = read_norm(c, &c->sc->res_bits, &r_learned);
+      if (rc) return rc;
+      CUDA_TRY(cudaMemsetAsync(&c->sc->res_bits, 0, 8, c->stream));
+      launch_poisson_res(c->stream, g, c->phi_old, c->b, &c->sc->res_bits);
+      rc = read_norm(c, &c->sc->res_bits, &r_plain);
+      if (rc) return rc;
+      c->prof.launches += 18;
+      c->prof.ws_applied += 1;
+      if (r_learned < r_plain)
+        c->prof.ws_kept += 1;
+      else
+        std::swap(c->phi, c->phi_old);
     }
   }
   *thr = P.poisson_tol;
@@ -1807,6 +1825,17 @@ double ibm_omega_from_rate(double omega, double rho) { return omega_from_rate(om
 int ibm_tune_omega(ibm_ctx* c, int sweeps, double* omega) {
   if (!c || !omega) return fail(IBM_E_INVAL, "null argument");
   return tune_omega(c, sweeps, omega);
+}
+
+int ibm_batch_set_sor_shape(ibm_batch* B, int index) {
+  if (!B) return fail(IBM_E_INVAL, "null batch");
+  if (index < -1 || index >= sor32_num_configs())
+    return fail(IBM_E_INVAL, "sweep shape %d out of range (-1 .. %d)", index, sor32_num_configs() - 1);
+  if (index >= 0) CUDA_TRY(sor32_batch_prepare(index));
+  B->cfg = index;
+  B->sor_us = 0.0;
+  B->drop_graphs();
+  return IBM_OK;
 }
 
 void* ibm_batch_stream(const ibm_batch* B) { return B ? (void*)B->stream : nullptr; }

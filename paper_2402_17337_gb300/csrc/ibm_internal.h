@@ -151,17 +151,18 @@ struct MgLevel {
   int cur;               // buffer holding the current correction
 };
 int mg_coarse_max();
+size_t fcg_scalars_bytes();  // device scalars of the FCG iteration (zero-initialised)
 void launch_mg_restrict(cudaStream_t s, const MgLevel& F, const float* ef, const MgLevel& C);
 void launch_mg_prolong(cudaStream_t s, const MgLevel& C, const float* ec, const MgLevel& F, float* ef);
 void launch_mg_coarse(cudaStream_t s, const MgLevel& L, float* e_out, float omega, int sweeps);
 int sor32_find_shape(int rows_per_tile, int half_sweeps, int form);
 void launch_fcg_dot(cudaStream_t s, const MgLevel& L, const float* dxv, const float* dyv, const float* z,
-                    const float* q, double* sc);
-void launch_fcg_dir(cudaStream_t s, const MgLevel& L, const float* z, float* p, const double* sc, int first);
+                    const float* q, void* sc);
+void launch_fcg_dir(cudaStream_t s, const MgLevel& L, const float* z, float* p, const void* sc, int first);
 void launch_fcg_apply(cudaStream_t s, const MgLevel& L, const float* dxv, const float* dyv, const float* p,
-                      const float* r, float* q, double* sc);
+                      const float* r, float* q, void* sc);
 void launch_fcg_update(cudaStream_t s, const MgLevel& L, const float* p, const float* q, float* x, float* r,
-                       const double* sc);
+                       const void* sc);
 
 // learned warm start (k_ws.cu): coarse features, prediction, targets; base guess
 void launch_extrapolate(cudaStream_t s, const Geo& g, double* phi, double* phi_prev);

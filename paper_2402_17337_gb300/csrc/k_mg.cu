@@ -114,59 +114,109 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(MgLevel L, float* __restrict
 
 inline dim3 grid_for(int nx, int ny) { return dim3((nx + 31) / 32, (ny + 7) / 8); }
 
+constexpr int kFcgSlots = 128;
+
 // ---- flexible conjugate gradients, FCG(1), preconditioned by the V-cycle,
 // on level 0 in the volume-weighted inner product <a, b> = sum V_ij a_ij b_ij
-// (L is self-adjoint in it).  Scalars stay on the device: sc[0] = <p, Lp>,
-// sc[1] = <p, r>, sc[2] = <z, q>.
+// (L is self-adjoint in it).  Scalars stay on the device in FcgScalars:
+// each inner product is accumulated in kFcgSlots FP64 slots (block b adds
+// into slot b mod kFcgSlots, so the atomics do not pile onto one address);
+// the last block of a reduction kernel (found by a counter after a memory
+// fence) sums the slots, derives alpha or beta, and clears the slots and
+// the counter for the next use.  Products and warp sums are FP32, block and
+// slot sums FP64.
+struct FcgScalars {
+  double slot[3][kFcgSlots];  // <p, Lp>, <p, r>, <z, q>
+  double pq;                  // <p, Lp> of the current direction
+  float alpha, beta;
+  unsigned int count;
+};
 
-__device__ inline void block_sum_add(double v, double* dst) {
+// adds the block's sum of v into slots; returns true in the block that
+// finished last (all other blocks' additions are then visible)
+__device__ inline bool block_sum_add(float v, double* slots, unsigned int* count, bool last_check) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __shared__ double ws[32];
+  __shared__ bool last;
   const int t = threadIdx.x + threadIdx.y * blockDim.x, lane = t & 31, warp = t >> 5;
   const int nw = (blockDim.x * blockDim.y + 31) >> 5;
-  if (lane == 0) ws[warp] = v;
+  __syncthreads();  // ws may still be read by a previous call
+  if (lane == 0) ws[warp] = (double)v;
   __syncthreads();
-  if (warp == 0) {
-    v = lane < nw ? ws[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) atomicAdd(dst, v);
+  if (t == 0) {
+    double a = 0.0;
+    for (int w = 0; w < nw; ++w) a += ws[w];
+    atomicAdd(&slots[(blockIdx.x + gridDim.x * blockIdx.y) % kFcgSlots], a);
+    if (last_check) {
+      __threadfence();
+      last = atomicAdd(count, 1u) == gridDim.x * gridDim.y - 1;
+    }
   }
+  __syncthreads();
+  return last_check && last;
 }
 
-// sc[2] = <z, q>
+// sum of one scalar's slots (warp 0 of the calling block), slots cleared
+__device__ inline double take_slots(double* slots) {
+  __shared__ double out;
+  const int t = threadIdx.x + threadIdx.y * blockDim.x;
+  if (t < 32) {
+    double a = 0.0;
+    for (int k = t; k < kFcgSlots; k += 32) {
+      a += *(volatile double*)&slots[k];
+      slots[k] = 0.0;
+    }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (t == 0) out = a;
+  }
+  __syncthreads();
+  return out;
+}
+
+// The two reduction kernels run a grid-stride loop over 32 x 8 tiles with at
+// most kReduceBlocks blocks, so the slot and counter atomics stay few.
+constexpr int kReduceBlocks = 608;
+
+// <z, q>; the last block sets beta = -<z, q> / <p, Lp> of the previous direction
 __global__ void k_fcg_dot(const MgLevel L, const float* __restrict__ dxv, const float* __restrict__ dyv,
-                          const float* __restrict__ z, const float* __restrict__ q, double* __restrict__ sc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  double v = 0.0;
-  if (i < L.g.nx && j < L.g.ny) {
-    const size_t o = rb_at(i, j, L.g.ny, L.g.pk);
-    v = (double)(dxv[i] * dyv[j]) * (double)z[o] * (double)q[o];
+                          const float* __restrict__ z, const float* __restrict__ q, FcgScalars* __restrict__ sc) {
+  const int tx = (L.g.nx + 31) / 32, nt = tx * ((L.g.ny + 7) / 8);
+  float v = 0.f;
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    const int i = (t % tx) * 32 + threadIdx.x, j = (t / tx) * 8 + threadIdx.y;
+    if (i < L.g.nx && j < L.g.ny) {
+      const size_t o = rb_at(i, j, L.g.ny, L.g.pk);
+      v = fmaf(dxv[i] * dyv[j] * z[o], q[o], v);
+    }
   }
-  block_sum_add(v, &sc[2]);
+  if (block_sum_add(v, sc->slot[2], &sc->count, true)) {
+    const double zq = take_slots(sc->slot[2]);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      sc->beta = sc->pq != 0.0 ? (float)(-zq / sc->pq) : 0.f;
+      sc->count = 0u;
+    }
+  }
 }
 
-// p = z (first) or p = z + beta p, beta = -<z, q> / <p, Lp> of the previous direction
+// p = z (first) or p = z + beta p
 __global__ void k_fcg_dir(const MgLevel L, const float* __restrict__ z, float* __restrict__ p,
-                          const double* __restrict__ sc, int first) {
+                          const FcgScalars* __restrict__ sc, int first) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= L.g.nx || j >= L.g.ny) return;
   const size_t o = rb_at(i, j, L.g.ny, L.g.pk);
-  if (first) {
-    p[o] = z[o];
-  } else {
-    const float beta = sc[0] != 0.0 ? (float)(-sc[2] / sc[0]) : 0.f;
-    p[o] = fmaf(beta, p[o], z[o]);
-  }
+  p[o] = first ? z[o] : fmaf(sc->beta, p[o], z[o]);
 }
 
-// q = L p, sc[0] += <p, q>, sc[1] += <p, r>
+// q = L p, <p, q>, <p, r>; the last block sets alpha = <p, r> / <p, q>
 __global__ void k_fcg_apply(const MgLevel L, const float* __restrict__ dxv, const float* __restrict__ dyv,
                             const float* __restrict__ p, const float* __restrict__ r, float* __restrict__ q,
-                            double* __restrict__ sc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  double vpq = 0.0, vpr = 0.0;
+                            FcgScalars* __restrict__ sc) {
+  float vpq = 0.f, vpr = 0.f;
   const int nx = L.g.nx, ny = L.g.ny, pk = L.g.pk;
-  if (i < nx && j < ny) {
+  const int tx = (nx + 31) / 32, nt = tx * ((ny + 7) / 8);
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    const int i = (t % tx) * 32 + threadIdx.x, j = (t / tx) * 8 + threadIdx.y;
+    if (i >= nx || j >= ny) continue;
     const size_t o = rb_at(i, j, ny, pk);
     const float x = p[o];
     const float xE = i < nx - 1 ? p[rb_at(i + 1, j, ny, pk)] : x;
@@ -178,41 +228,56 @@ __global__ void k_fcg_apply(const MgLevel L, const float* __restrict__ dxv, cons
     Lp = fmaf(L.g.pN[j], xN - x, Lp);
     Lp = fmaf(L.g.pS[j], xS - x, Lp);
     q[o] = Lp;
-    const double V = (double)(dxv[i] * dyv[j]);
-    vpq = V * (double)x * (double)Lp;
-    vpr = V * (double)x * (double)r[o];
+    const float Vx = dxv[i] * dyv[j] * x;
+    vpq = fmaf(Vx, Lp, vpq);
+    vpr = fmaf(Vx, r[o], vpr);
   }
-  block_sum_add(vpq, &sc[0]);
-  block_sum_add(vpr, &sc[1]);
+  block_sum_add(vpq, sc->slot[0], &sc->count, false);
+  if (block_sum_add(vpr, sc->slot[1], &sc->count, true)) {
+    const double pq = take_slots(sc->slot[0]);
+    const double pr = take_slots(sc->slot[1]);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      sc->pq = pq;
+      sc->alpha = pq != 0.0 ? (float)(pr / pq) : 0.f;
+      sc->count = 0u;
+    }
+  }
 }
 
-// alpha = <p, r> / <p, Lp>; x += alpha p; r -= alpha q
+// x += alpha p; r -= alpha q
 __global__ void k_fcg_update(const MgLevel L, const float* __restrict__ p, const float* __restrict__ q,
-                             float* __restrict__ x, float* __restrict__ r, const double* __restrict__ sc) {
+                             float* __restrict__ x, float* __restrict__ r, const FcgScalars* __restrict__ sc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= L.g.nx || j >= L.g.ny) return;
   const size_t o = rb_at(i, j, L.g.ny, L.g.pk);
-  const float alpha = sc[0] != 0.0 ? (float)(sc[1] / sc[0]) : 0.f;
+  const float alpha = sc->alpha;
   x[o] = fmaf(alpha, p[o], x[o]);
   r[o] = fmaf(-alpha, q[o], r[o]);
 }
 
 }  // namespace
 
-void launch_fcg_dot(cudaStream_t s, const MgLevel& L, const float* dxv, const float* dyv, const float* z,
-                    const float* q, double* sc) {
-  k_fcg_dot<<<grid_for(L.g.nx, L.g.ny), dim3(32, 8), 0, s>>>(L, dxv, dyv, z, q, sc);
+size_t fcg_scalars_bytes() { return sizeof(FcgScalars); }
+
+inline int reduce_blocks(const MgLevel& L) {
+  const int nt = ((L.g.nx + 31) / 32) * ((L.g.ny + 7) / 8);
+  return nt < kReduceBlocks ? nt : kReduceBlocks;
 }
-void launch_fcg_dir(cudaStream_t s, const MgLevel& L, const float* z, float* p, const double* sc, int first) {
-  k_fcg_dir<<<grid_for(L.g.nx, L.g.ny), dim3(32, 8), 0, s>>>(L, z, p, sc, first);
+
+void launch_fcg_dot(cudaStream_t s, const MgLevel& L, const float* dxv, const float* dyv, const float* z,
+                    const float* q, void* sc) {
+  k_fcg_dot<<<reduce_blocks(L), dim3(32, 8), 0, s>>>(L, dxv, dyv, z, q, (FcgScalars*)sc);
+}
+void launch_fcg_dir(cudaStream_t s, const MgLevel& L, const float* z, float* p, const void* sc, int first) {
+  k_fcg_dir<<<grid_for(L.g.nx, L.g.ny), dim3(32, 8), 0, s>>>(L, z, p, (const FcgScalars*)sc, first);
 }
 void launch_fcg_apply(cudaStream_t s, const MgLevel& L, const float* dxv, const float* dyv, const float* p,
-                      const float* r, float* q, double* sc) {
-  k_fcg_apply<<<grid_for(L.g.nx, L.g.ny), dim3(32, 8), 0, s>>>(L, dxv, dyv, p, r, q, sc);
+                      const float* r, float* q, void* sc) {
+  k_fcg_apply<<<reduce_blocks(L), dim3(32, 8), 0, s>>>(L, dxv, dyv, p, r, q, (FcgScalars*)sc);
 }
 void launch_fcg_update(cudaStream_t s, const MgLevel& L, const float* p, const float* q, float* x, float* r,
-                       const double* sc) {
-  k_fcg_update<<<grid_for(L.g.nx, L.g.ny), dim3(32, 8), 0, s>>>(L, p, q, x, r, sc);
+                       const void* sc) {
+  k_fcg_update<<<grid_for(L.g.nx, L.g.ny), dim3(32, 8), 0, s>>>(L, p, q, x, r, (const FcgScalars*)sc);
 }
 
 int mg_coarse_max() { return kCoarseMax; }
@@ -226,7 +291,8 @@ void launch_mg_prolong(cudaStream_t s, const MgLevel& C, const float* ec, const 
 }
 
 void launch_mg_coarse(cudaStream_t s, const MgLevel& L, float* e_out, float omega, int sweeps) {
-  k_mg_coarse<<<1, 1024, 0, s>>>(L, e_out, omega, sweeps);
+  const int n = L.g.nx * L.g.ny, threads = n >= 1024 ? 1024 : (n + 31) / 32 * 32;  // few warps: cheap barriers
+  k_mg_coarse<<<1, threads, 0, s>>>(L, e_out, omega, sweeps);
 }
 
 }  // namespace ibm

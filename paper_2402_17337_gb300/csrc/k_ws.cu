@@ -20,8 +20,28 @@ namespace ibm {
 
 namespace {
 
-__device__ inline void atomic_max_abs(unsigned long long* dst, double v) {
-  atomicMax(dst, (unsigned long long)__double_as_longlong(fabs(v)));
+// block-wide maximum of |v| (IEEE bit patterns of non-negative doubles order
+// like the values), one atomic per block
+__device__ inline void block_max_abs(double v, unsigned long long* dst) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v));
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, b, o);
+    b = w > b ? w : b;
+  }
+  __shared__ unsigned long long wm[32];
+  const int t = threadIdx.x + threadIdx.y * blockDim.x, lane = t & 31, warp = t >> 5;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+  __syncthreads();  // wm may still be read by a previous call
+  if (lane == 0) wm[warp] = b;
+  __syncthreads();
+  if (warp == 0) {
+    b = lane < nw ? wm[lane] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long w = __shfl_xor_sync(0xffffffffu, b, o);
+      b = w > b ? w : b;
+    }
+    if (lane == 0 && b) atomicMax(dst, b);
+  }
 }
 
 __device__ inline double lap_p(const Geo& g, const double* f, int i, int j) {
@@ -40,9 +60,9 @@ __global__ void k_ws_features(Geo g, int Hc, int Wc, const double* __restrict__ 
                               const double* __restrict__ p, Band B, const uint8_t* __restrict__ fc,
                               float* __restrict__ feat, unsigned long long* __restrict__ ws_max) {
   int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
-  if (I >= Wc || J >= Hc) return;
+  const bool in = I < Wc && J < Hc;
   double r0 = 0.0, bb = 0.0, body = 0.0, pp = 0.0;
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < 2 && in; ++a)
     for (int c2 = 0; c2 < 2; ++c2) {
       int i = 2 * I + a, j = 2 * J + c2;
       size_t c = at(i, j, g.pitch);
@@ -52,14 +72,16 @@ __global__ void k_ws_features(Geo g, int Hc, int Wc, const double* __restrict__ 
       int bi = i - B.i0, bj = j - B.j0;
       if (bi >= 0 && bj >= 0 && bi < B.w && bj < B.h && fc[bj * B.w + bi]) body += 1.0;
     }
-  float* f = feat + ((size_t)J * Wc + I) * 4;
-  f[0] = (float)(0.25 * r0);
-  f[1] = (float)(0.25 * bb);
-  f[2] = (float)(0.25 * body);
-  f[3] = (float)(0.25 * pp);
-  atomic_max_abs(&ws_max[0], 0.25 * r0);
-  atomic_max_abs(&ws_max[1], 0.25 * bb);
-  atomic_max_abs(&ws_max[3], 0.25 * pp);
+  if (in) {
+    float* f = feat + ((size_t)J * Wc + I) * 4;
+    f[0] = (float)(0.25 * r0);
+    f[1] = (float)(0.25 * bb);
+    f[2] = (float)(0.25 * body);
+    f[3] = (float)(0.25 * pp);
+  }
+  block_max_abs(0.25 * r0, &ws_max[0]);
+  block_max_abs(0.25 * bb, &ws_max[1]);
+  block_max_abs(0.25 * pp, &ws_max[3]);
 }
 
 __device__ inline double bits2d(unsigned long long u) { return __longlong_as_double((long long)u); }

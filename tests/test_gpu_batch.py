@@ -79,6 +79,7 @@ def test_graph_replay_is_bit_identical_to_direct_launches():
         ss = solvers(cfgs)
         B = Batch(ss)
         B.set_graphs(graphs)
+        B.set_sor_shape(0)  # the same tile shape in both runs (the autotuner may pick either)
         st = B.step(3)
         runs.append(([s.get("p") for s in ss], [s.get("u") for s in ss], [x["sweeps_p"] for x in st]))
         B.close()
