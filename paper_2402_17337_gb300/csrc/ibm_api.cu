@@ -131,6 +131,7 @@ struct ibm_ctx {
   int mg_cycles = 2;                                 // V-cycles between FP64 checks (adapted)
   int mg_coarse_sweeps = 0;
   float mg_coarse_omega = 1.f;
+  int mg_tail = -1;  // first level run by the one-CTA tail kernel (-1: none)
   cudaGraphExec_t mg_graph[2] = {nullptr, nullptr};  // one FCG iteration: first / later
   bool mg_graph_failed = false;
   float *fcg_x = nullptr, *fcg_p = nullptr, *fcg_q = nullptr;  // level-0 FCG vectors
@@ -416,6 +417,7 @@ int build_mg(ibm_ctx* c) {
   c->mg_shape = sor32_find_shape(24, 4, 4);
   if (c->mg_shape < 0) return fail(IBM_E_CUDA, "multigrid smoother shape missing");
   CUDA_TRY(sor32_batch_prepare(c->mg_shape));
+  CUDA_TRY(prepare_mg_tail());
   std::vector<double> xf = c->xf, yf = c->yf;
   int rc = 0;
   for (int l = 0;; ++l) {
@@ -513,6 +515,18 @@ int build_mg(ibm_ctx* c) {
       break;
     }
   }
+  // the tail: the coarsest levels whose cells together fit in one CTA's
+  // shared memory (level 0 stays with the FCG vectors)
+  {
+    long cells = 0;
+    int lt = -1;
+    for (int l = (int)c->mg.size() - 1; l >= 1 && (int)c->mg.size() - l <= kTailLevels; --l) {
+      cells += (long)c->mg[l].g.nx * c->mg[l].g.ny;
+      if (cells > kTailCells) break;
+      lt = l;
+    }
+    c->mg_tail = ((int)c->mg.size() - lt >= 2 && lt >= 1) ? lt : -1;
+  }
   const size_t n32 = (size_t)2 * c->ny * c->geo32.pk;
   std::vector<float> dxv(c->nx), dyv(c->ny);
   for (int i = 0; i < c->nx; ++i) dxv[i] = (float)(c->xf[i + 1] - c->xf[i]);
@@ -536,22 +550,38 @@ int build_mg(ibm_ctx* c) {
 // buffer it started in, so the launch sequence is the same every cycle.
 void mg_vcycle(ibm_ctx* c, int zero_first) {
   const int n = (int)c->mg.size();
-  for (int l = 0; l < n - 1; ++l) {
+  const int bottom = c->mg_tail >= 1 ? c->mg_tail : n - 1;  // first level not handled level by level
+  for (int l = 0; l < bottom; ++l) {
     MgLevel& A = c->mg[l];
     launch_sor32(c->stream, c->mg_shape, A.g, A.e[A.cur], A.e[A.cur ^ 1], A.r, A.invd, 1.0f, l > 0 || zero_first);
     A.cur ^= 1;
     launch_mg_restrict(c->stream, A, A.e[A.cur], c->mg[l + 1]);
   }
-  MgLevel& Z = c->mg[n - 1];
-  launch_mg_coarse(c->stream, Z, Z.e[Z.cur], c->mg_coarse_omega, c->mg_coarse_sweeps);
-  for (int l = n - 2; l >= 0; --l) {
+  if (c->mg_tail >= 1) {
+    MgTail T{};
+    T.n = n - bottom;
+    int off = 0;
+    for (int k = 0; k < T.n; ++k) {
+      T.lv[k] = c->mg[bottom + k];
+      T.off[k] = off;
+      off += T.lv[k].g.nx * T.lv[k].g.ny;
+    }
+    T.omega_c = c->mg_coarse_omega;
+    T.sweeps_c = c->mg_coarse_sweeps;
+    MgLevel& B = c->mg[bottom];
+    launch_mg_tail(c->stream, T, B.e[B.cur]);
+  } else {
+    MgLevel& Z = c->mg[n - 1];
+    launch_mg_coarse(c->stream, Z, Z.e[Z.cur], c->mg_coarse_omega, c->mg_coarse_sweeps);
+  }
+  for (int l = bottom - 1; l >= 0; --l) {
     MgLevel& A = c->mg[l];
     const MgLevel& B = c->mg[l + 1];
     launch_mg_prolong(c->stream, B, B.e[B.cur], A, A.e[A.cur]);
     launch_sor32(c->stream, c->mg_shape, A.g, A.e[A.cur], A.e[A.cur ^ 1], A.r, A.invd, 1.0f, 0);
     A.cur ^= 1;
   }
-  c->prof.launches += 4 * (n - 1) + 1;
+  c->prof.launches += 4 * bottom + 1;
 }
 
 // One iteration of flexible conjugate gradients, FCG(1), on level 0's
@@ -572,7 +602,10 @@ void fcg_iter(ibm_ctx* c, int first) {
   c->prof.launches += first ? 3 : 4;
 }
 
-int fcg_launches(const ibm_ctx* c) { return 4 * ((int)c->mg.size() - 1) + 1 + 4; }
+int fcg_launches(const ibm_ctx* c) {
+  const int bottom = c->mg_tail >= 1 ? c->mg_tail : (int)c->mg.size() - 1;
+  return 4 * bottom + 1 + 4;
+}
 
 // CUDA graphs of one FCG iteration (first and later); direct launches if the
 // stream cannot be captured.

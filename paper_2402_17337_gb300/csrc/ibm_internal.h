@@ -151,6 +151,16 @@ struct MgLevel {
   int cur;               // buffer holding the current correction
 };
 int mg_coarse_max();
+constexpr int kTailLevels = 8, kTailCells = 5632;  // 44 KB of shared memory: a larger level costs one CTA more than its launches
+struct MgTail {             // the small levels, run by one CTA (k_mg_tail)
+  MgLevel lv[kTailLevels];  // lv[0] = first tail level, its r from global memory
+  int off[kTailLevels];     // offsets of each level's cells in shared memory
+  int n;                    // number of tail levels (the last is solved by SOR)
+  float omega_c;
+  int sweeps_c;
+};
+cudaError_t prepare_mg_tail();  // dynamic shared memory limit, once, outside graph capture
+void launch_mg_tail(cudaStream_t s, const MgTail& T, float* e_top);
 size_t fcg_scalars_bytes();  // device scalars of the FCG iteration (zero-initialised)
 void launch_mg_restrict(cudaStream_t s, const MgLevel& F, const float* ef, const MgLevel& C);
 void launch_mg_prolong(cudaStream_t s, const MgLevel& C, const float* ec, const MgLevel& F, float* ef);

@@ -114,6 +114,108 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(MgLevel L, float* __restrict
 
 inline dim3 grid_for(int nx, int ny) { return dim3((nx + 31) / 32, (ny + 7) / 8); }
 
+// ---- the small levels of the hierarchy in one CTA: the V-cycle below a
+// level whose cells (with all coarser levels) fit in shared memory runs in a
+// single launch instead of four launches per level, each of which would be
+// mostly launch latency.  Same operations as the per-level kernels: two
+// red-black Gauss-Seidel sweeps before and after, residual and restriction,
+// bilinear prolongation, SOR on the coarsest level; corrections from zero.
+__device__ inline float tail_sum(const MgLevel& L, const float* e, int i, int j) {
+  const int nx = L.g.nx, ny = L.g.ny, t = j * nx + i;
+  const float xE = i < nx - 1 ? e[t + 1] : 0.f, xW = i > 0 ? e[t - 1] : 0.f;
+  const float xN = j < ny - 1 ? e[t + nx] : 0.f, xS = j > 0 ? e[t - nx] : 0.f;
+  float sum = L.pE[i] * xE;
+  sum = fmaf(L.pW[i], xW, sum);
+  sum = fmaf(L.g.pN[j], xN, sum);
+  sum = fmaf(L.g.pS[j], xS, sum);
+  return sum;
+}
+
+__device__ inline void tail_relax(const MgLevel& L, float* e, const float* r, float omega, int sweeps) {
+  const int nx = L.g.nx, n = nx * L.g.ny;
+  for (int s = 0; s < sweeps; ++s)
+    for (int c = 0; c < 2; ++c) {
+      for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int i = t % nx, j = t / nx;
+        if (((i + j) & 1) != c) continue;
+        const float gs = (tail_sum(L, e, i, j) - r[t]) * L.invd[rb_at(i, j, L.g.ny, L.g.pk)];
+        e[t] = fmaf(omega, gs - e[t], e[t]);
+      }
+      __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_mg_tail(const MgTail T, float* __restrict__ e_top) {
+  extern __shared__ float tail_smem[];
+  float* se = tail_smem;               // corrections of all tail levels
+  float* sr = tail_smem + kTailCells;  // right-hand sides
+  const MgLevel& top = T.lv[0];
+  for (int t = threadIdx.x; t < top.g.nx * top.g.ny; t += blockDim.x) {
+    const int i = t % top.g.nx, j = t / top.g.nx;
+    sr[t] = top.r[rb_at(i, j, top.g.ny, top.g.pk)];
+  }
+  for (int l = 0; l < T.n; ++l) {
+    const MgLevel& A = T.lv[l];
+    float *e = se + T.off[l], *r = sr + T.off[l];
+    const int n = A.g.nx * A.g.ny;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) e[t] = 0.f;
+    __syncthreads();
+    if (l == T.n - 1) {
+      tail_relax(A, e, r, T.omega_c, T.sweeps_c);
+      break;
+    }
+    tail_relax(A, e, r, 1.0f, 2);
+    const MgLevel& C = T.lv[l + 1];
+    float* rc = sr + T.off[l + 1];
+    for (int t = threadIdx.x; t < C.g.nx * C.g.ny; t += blockDim.x) {
+      const int I = t % C.g.nx, J = t / C.g.nx;
+      float acc = 0.f;
+      for (int b = 0; b < 2; ++b) {
+        const int j = 2 * J + b;
+        if (j >= A.g.ny) break;
+        float row = 0.f;
+        for (int a = 0; a < 2; ++a) {
+          const int i = 2 * I + a;
+          if (i >= A.g.nx) break;
+          const int u = j * A.g.nx + i;
+          const float x = e[u];
+          const float xE = i < A.g.nx - 1 ? e[u + 1] : x, xW = i > 0 ? e[u - 1] : x;
+          const float xN = j < A.g.ny - 1 ? e[u + A.g.nx] : x, xS = j > 0 ? e[u - A.g.nx] : x;
+          float Le = A.pE[i] * (xE - x);
+          Le = fmaf(A.pW[i], xW - x, Le);
+          Le = fmaf(A.g.pN[j], xN - x, Le);
+          Le = fmaf(A.g.pS[j], xS - x, Le);
+          row = fmaf(A.wx[i], r[u] - Le, row);
+        }
+        acc = fmaf(A.wy[j], row, acc);
+      }
+      rc[t] = acc;
+    }
+    __syncthreads();
+  }
+  for (int l = T.n - 2; l >= 0; --l) {
+    const MgLevel& A = T.lv[l];
+    const MgLevel& C = T.lv[l + 1];
+    float *e = se + T.off[l], *r = sr + T.off[l];
+    const float* ec = se + T.off[l + 1];
+    for (int t = threadIdx.x; t < A.g.nx * A.g.ny; t += blockDim.x) {
+      const int i = t % A.g.nx, j = t / A.g.nx;
+      const int I = i >> 1, J = j >> 1, I2 = I + A.ox[i], J2 = J + A.oy[j];
+      const float ax = A.ax[i], ay = A.ay[j];
+      const float e00 = ec[J * C.g.nx + I], e10 = ec[J * C.g.nx + I2];
+      const float e01 = ec[J2 * C.g.nx + I], e11 = ec[J2 * C.g.nx + I2];
+      const float lo = fmaf(ax, e10 - e00, e00), hi = fmaf(ax, e11 - e01, e01);
+      e[t] += fmaf(ay, hi - lo, lo);
+    }
+    __syncthreads();
+    tail_relax(A, e, r, 1.0f, 2);
+  }
+  for (int t = threadIdx.x; t < top.g.nx * top.g.ny; t += blockDim.x) {
+    const int i = t % top.g.nx, j = t / top.g.nx;
+    e_top[rb_at(i, j, top.g.ny, top.g.pk)] = se[t];
+  }
+}
+
 constexpr int kFcgSlots = 128;
 
 // ---- flexible conjugate gradients, FCG(1), preconditioned by the V-cycle,
@@ -281,6 +383,15 @@ void launch_fcg_update(cudaStream_t s, const MgLevel& L, const float* p, const f
 }
 
 int mg_coarse_max() { return kCoarseMax; }
+
+cudaError_t prepare_mg_tail() {
+  return cudaFuncSetAttribute(k_mg_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(2 * kTailCells * sizeof(float)));
+}
+
+void launch_mg_tail(cudaStream_t s, const MgTail& T, float* e_top) {
+  k_mg_tail<<<1, 1024, 2 * kTailCells * sizeof(float), s>>>(T, e_top);
+}
 
 void launch_mg_restrict(cudaStream_t s, const MgLevel& F, const float* ef, const MgLevel& C) {
   k_mg_restrict<<<grid_for(C.g.nx, C.g.ny), dim3(32, 8), 0, s>>>(F, ef, C);
