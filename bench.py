@@ -49,7 +49,14 @@ SOR_BYTES_PER_CELL_HALF = 16  # read phi (8, all cells), read b (4), write phi (
 # multigrid variant, one FCG iteration per fine cell: smoothing 2 x 12, restriction 9, prolongation 9,
 # FCG dot 8 + direction 12 + operator 12 + update 16, coarser levels a third of smoothing + transfers (14)
 MG_BYTES_PER_CELL_ITER = 104
-WORKLOADS = ("plunge_2048x1024", "batch64")
+# DRAM bytes (read + write) per launch of the FP32 sweep kernel from one ncu capture of the
+# unchanged kernel (profiles/k_sor32_rb_*.md), by workload and tile shape (rows, half-sweeps,
+# thread rows, form); cold-cache captures
+SOR32_TRAFFIC = {
+    ("plunge_2048x1024", (64, 16, 16, 4)): 25.216e6,
+    ("plunge_4096x2048", (32, 8, 16, 4)): 115.864e6,
+}
+WORKLOADS = ("plunge_2048x1024", "plunge_4096x2048", "batch64")
 METRIC = "cell-steps/s at div<1e-8: learned warm-start+mixed vs plain FP64, one GB300"
 
 
@@ -387,7 +394,7 @@ def main():
         if args.impl == "reference":
             return run_reference(args, W.batch64()[0])
         return run_batch(args)
-    cfg = W.plunge_2048x1024()
+    cfg = getattr(W, args.workload)()
     if args.impl == "reference":
         return run_reference(args, cfg)
 
@@ -446,7 +453,11 @@ def main():
             raise SystemExit(f"no U-Net weights at {path}: run paper_2402_17337_gb300.train_warmstart "
                              f"or pass --warmstart plain")
         net, cT, meta = warmstart.load(path)
-        learned = {"net": net, "cT": cT, "meta": meta}
+        if meta.get("workload") == cfg.name:
+            learned = {"net": net, "cT": cT, "meta": meta}
+        else:  # a network is trained for one grid and time step
+            print(f"bench: no U-Net weights for {cfg.name} (have {meta.get('workload')}); plain warm start",
+                  file=sys.stderr)
 
     def timed_run(precision, sample_clocks, ws=None):
         """W untimed steps, then K steps timed with CUDA events on the solver's stream."""
@@ -475,9 +486,12 @@ def main():
         ms = max_over_ranks(e0.elapsed_time(e1))
         prof = s.profile()
         ok = sum_over_ranks(sum(1 for st in stats if st["div_max"] < cfg.div_tol))
+        final = {n: s.get(n) for n in ("u", "v", "p")} if rank == 0 else None
+        forces = s.forces() if rank == 0 else None
         s.close()
         return {"value": cfg.cells * ok / (ms / 1e3), "ms": ms, "stats": stats, "ok": int(ok), "clocks": clk,
-                "launches": prof["launches"] - prof0["launches"], "prof": prof, "prof0": prof0, "state": state}
+                "launches": prof["launches"] - prof0["launches"], "prof": prof, "prof0": prof0, "state": state,
+                "final": final, "forces": forces}
 
     precision = {"fp64": 0, "mixed": 1, "mg": 2}[args.precision]
     main_run = timed_run(precision, not args.no_clocks, learned)
@@ -505,7 +519,8 @@ def main():
                     "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "iter_us": t_iter * 1e6,
                     "peak_note": f"HBM {peaks['hbm_gbs']} GB/s ({peak_src}); algorithmic "
-                                 f"{MG_BYTES_PER_CELL_ITER} B per fine cell per iteration; working set fits in L2"}
+                                 f"{MG_BYTES_PER_CELL_ITER} B per fine cell per iteration; FP32 working set "
+                                 f"{cfg.cells * 24 / 1e6:.0f} MB against 129 MB of L2"}
         elif precision == 0:
             flops = SOR_FLOPS_PER_UPDATE * cfg.cells / 2
             achieved = flops / t_launch / 1e12
@@ -517,17 +532,18 @@ def main():
         else:
             nbytes = SOR32_BYTES_PER_CELL_LAUNCH * cfg.cells
             achieved = nbytes / t_launch / 1e9
-            rows, half, _ = prof["sor_shape"]
+            rows, half, nyt = prof["sor_shape"]
             sweeps_per_launch = half / 2
+            traffic = SOR32_TRAFFIC.get((cfg.name, (rows, half, nyt, prof["sor_form"])))
             roof = {"bound": "hbm", "kernel": f"k_sor32_rb (FP32 red-black SOR, tile {rows} rows x 128 cells, "
                                               f"{half} half-sweeps per launch, chosen by the autotuner)",
                     "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / peaks["hbm_gbs"], "traffic": None, "launch_us": t_launch * 1e6,
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "launch_us": t_launch * 1e6,
                     "fp32_tflops": SOR_FLOPS_PER_UPDATE * cfg.cells * sweeps_per_launch / t_launch / 1e12,
                     "fp32_peak_tflops": fp32_peak,
                     "peak_note": f"HBM {peaks['hbm_gbs']} GB/s ({peak_src}); algorithmic bytes: read e and r, "
-                                 f"write e once per launch ({SOR32_BYTES_PER_CELL_LAUNCH} B/cell); working set "
-                                 f"fits in L2"}
+                                 f"write e once per launch ({SOR32_BYTES_PER_CELL_LAUNCH} B/cell); FP32 working set "
+                                 f"{cfg.cells * 16 / 1e6:.0f} MB against 129 MB of L2"}
 
     # ------------------------------------------------------------- end to end
     # A second context runs the same warm-up and the same window of steps
@@ -584,6 +600,17 @@ def main():
 
     if rank == 0:
         sweeps = [st["sweeps_p"] for st in stats]
+        def field_errors(run):
+            """Per-field relative error (inf-norm) against the plain FP64 run after the same steps."""
+            if not run or not fp64_run or run["final"] is None:
+                return None
+            ref = fp64_run["final"]
+            out = {n: float(np.abs(run["final"][n] - ref[n]).max() / np.abs(ref[n]).max()) for n in ref}
+            (cl, cd), (cl0, cd0) = run["forces"], fp64_run["forces"]
+            out["cl"] = float(np.abs(cl - cl0).max() / np.abs(cl0).max())
+            out["cd"] = float(np.abs(cd - cd0).max() / np.abs(cd0).max())
+            return out
+
         fp64 = None
         if fp64_run:
             fp64 = {"value": fp64_run["value"], "ms_per_step": fp64_run["ms"] / args.steps,
@@ -592,13 +619,16 @@ def main():
         plain_ws = None
         if plain_ws_run:
             plain_ws = {"value": plain_ws_run["value"], "ms_per_step": plain_ws_run["ms"] / args.steps,
+                        "error_vs_fp64": field_errors(plain_ws_run),
                         "poisson_sweeps_per_step": statistics.mean(st["sweeps_p"] for st in plain_ws_run["stats"]),
                         "speedup_of_value": value / plain_ws_run["value"]}
+        if fp64:
+            fp64["error_vs_fp64_of_value"] = field_errors(main_run)
         mg = None
         if mg_run:
             mg = {"value": mg_run["value"], "ms_per_step": mg_run["ms"] / args.steps,
                   "vcycles_per_step": statistics.mean(st["sweeps_p"] for st in mg_run["stats"]),
-                  "speedup_of_value": mg_run["value"] / value,
+                  "speedup_of_value": mg_run["value"] / value, "error_vs_fp64": field_errors(mg_run),
                   "note": "variant, not the paper's solver: FP32 geometric-multigrid V(2,2)-cycles (red-black "
                           "Gauss-Seidel smoothing, bilinear prolongation) inside the same FP64 defect correction "
                           "and stopping rule; previous-increment warm start"}
@@ -624,7 +654,8 @@ def main():
                        "mixed_plain_warmstart": plain_ws, "plain_fp64": fp64, "multigrid_variant": mg,
                        "steps_counted": total_ok, "poisson_sweeps_per_step": statistics.mean(sweeps),
                        "helm_sweeps_per_step": statistics.mean(st["sweeps_u"] + st["sweeps_v"] for st in stats),
-                       "l2": "state 14 FP64 fields x 17 MB > L2; no flush",
+                       "l2": f"state 14 FP64 fields x {cfg.cells * 8 / 1e6:.0f} MB > L2 (129 MB); FP32 sweep "
+                             f"arrays {cfg.cells * 16 / 1e6:.0f} MB; no flush",
                        "div_max": max(st["div_max"] for st in stats)},
             "gpu_launches": launches,
             "roofline": roof,

@@ -277,7 +277,7 @@ __device__ inline double take_slots(double* slots) {
 
 // The two reduction kernels run a grid-stride loop over 32 x 8 tiles with at
 // most kReduceBlocks blocks, so the slot and counter atomics stay few.
-constexpr int kReduceBlocks = 608;
+constexpr int kReduceBlocks = 1216;  // 8 CTAs of 8 warps per SM: full occupancy to hide load latency
 
 // <z, q>; the last block sets beta = -<z, q> / <p, Lp> of the previous direction
 __global__ void k_fcg_dot(const MgLevel L, const float* __restrict__ dxv, const float* __restrict__ dyv,
