@@ -122,6 +122,10 @@ struct ibm_ctx {
   // mixed precision (FP32 correction, residual and reciprocal diagonal)
   Geo32 geo32{};
   float *e32 = nullptr, *e32b = nullptr, *r32 = nullptr, *invd32 = nullptr;  // e32/e32b: ping-pong
+  // velocity systems in FP32 sweeps (precision >= 1): coefficients, reciprocal
+  // diagonals (pitched, u and v), correction and residual (pitched)
+  HelmF32 h32{};
+  float *hinv_u = nullptr, *hinv_v = nullptr, *hd32 = nullptr, *hr32 = nullptr;
   int m_inner = 32;  // inner sweeps between FP64 checks (adapted)
   int sor_cfg = -1;          // tile shape of the FP32 sweeps, -1: not tuned yet
   double sor_us = 0.0;       // its measured time per full sweep
@@ -377,6 +381,38 @@ int setup_geometry(ibm_ctx* c) {
     rc |= c->alloc(&c->r32, n32);
     if (rc) return IBM_E_CUDA;
     c->invd32 = const_cast<float*>(d32);
+    // velocity systems
+    auto f32 = [](const std::vector<double>& a) {
+      std::vector<float> o(a.size());
+      for (size_t k = 0; k < a.size(); ++k) o[k] = (float)a[k];
+      return o;
+    };
+    rc |= c->upload(&c->h32.uE, f32(uE));
+    rc |= c->upload(&c->h32.uW, f32(uW));
+    rc |= c->upload(&c->h32.uN, f32(uN));
+    rc |= c->upload(&c->h32.uS, f32(uS));
+    rc |= c->upload(&c->h32.vE, f32(vE));
+    rc |= c->upload(&c->h32.vW, f32(vW));
+    rc |= c->upload(&c->h32.vN, f32(vN));
+    rc |= c->upload(&c->h32.vS, f32(vS));
+    std::vector<float> iu32(c->nelem, 0.f), iv32(c->nelem, 0.f);
+    const float b32 = (float)beta;
+    for (int j = 0; j < ny; ++j)
+      for (int i = 1; i < nx; ++i)
+        iu32[at(i, j, c->pitch)] =
+            1.0f / (1.0f + b32 * ((float)uE[i] + (float)uW[i] + (float)uN[j] + (float)uS[j]));
+    for (int j = 1; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        iv32[at(i, j, c->pitch)] =
+            1.0f / (1.0f + b32 * ((float)vE[i] + (float)vW[i] + (float)vN[j] + (float)vS[j]));
+    const float *hu, *hv;
+    rc |= c->upload(&hu, iu32);
+    rc |= c->upload(&hv, iv32);
+    rc |= c->alloc(&c->hd32, c->nelem);
+    rc |= c->alloc(&c->hr32, c->nelem);
+    if (rc) return IBM_E_CUDA;
+    c->hinv_u = const_cast<float*>(hu);
+    c->hinv_v = const_cast<float*>(hv);
   }
   if (c->P.precision == 2) return build_mg(c);
   return IBM_OK;
@@ -945,7 +981,43 @@ int solve_poisson_mixed(ibm_ctx* c, double tol, int maxs, int* sweeps, double* r
   }
 }
 
+// Velocity system in FP32 sweeps inside FP64 defect correction: FP64
+// residual (stored in FP32) and norm, 8 FP32 red-black sweeps on the
+// correction equation from zero, FP64 update; *sweeps counts FP32 sweeps.
+int solve_helm_mixed(ibm_ctx* c, int grid, double beta, double Ub, int* sweeps, double* res) {
+  const Geo& g = c->geo;
+  double* x = grid == 0 ? c->uh : c->vh;
+  const double* R = grid == 0 ? c->Ru : c->Rv;
+  const float* invd = grid == 0 ? c->hinv_u : c->hinv_v;
+  const uint8_t* fl = grid == 0 ? c->fu : c->fv;
+  const double* al = grid == 0 ? c->au : c->av;
+  const int m = 8;
+  for (int s = 0;; s += m) {
+    CUDA_TRY(cudaMemsetAsync(&c->sc->res_bits, 0, 8, c->stream));
+    launch_helm_dc_res(c->stream, g, grid, x, R, c->band, fl, al, beta, Ub, c->hr32, &c->sc->res_bits);
+    c->prof.launches += 1;
+    double r;
+    int rc = read_norm(c, &c->sc->res_bits, &r);
+    if (rc) return rc;
+    *sweeps = s;
+    *res = r;
+    if (!std::isfinite(r)) return fail(IBM_E_DIVERGED, "velocity residual is not finite");
+    if (r <= c->P.helm_tol) return IBM_OK;
+    if (s >= c->P.max_sweeps) return fail(IBM_E_NOCONV, "velocity solve (grid %d) did not converge", grid);
+    CUDA_TRY(cudaMemsetAsync(c->hd32, 0, c->nelem * sizeof(float), c->stream));
+    for (int k = 0; k < m; ++k) {
+      launch_helm32_half(c->stream, g, c->h32, grid, c->hd32, c->hr32, invd, c->band, fl, al, 0,
+                         (float)c->P.omega_h, (float)beta);
+      launch_helm32_half(c->stream, g, c->h32, grid, c->hd32, c->hr32, invd, c->band, fl, al, 1,
+                         (float)c->P.omega_h, (float)beta);
+    }
+    launch_helm_add(c->stream, g, grid, x, c->hd32);
+    c->prof.launches += 2 * m + 1;
+  }
+}
+
 int solve_helm(ibm_ctx* c, int grid, double beta, double Ub, int* sweeps, double* res) {
+  if (c->P.precision >= 1) return solve_helm_mixed(c, grid, beta, Ub, sweeps, res);
   const Geo& g = c->geo;
   double* x = grid == 0 ? c->uh : c->vh;
   const double* R = grid == 0 ? c->Ru : c->Rv;

@@ -108,6 +108,17 @@ void launch_fill_hash(cudaStream_t s, const Geo& g, double* x);
 void launch_helm_half(cudaStream_t s, const Geo& g, int grid, double* x, const double* R, const double* invd,
                       const Band& band, const uint8_t* fl, const double* al, int colour, double omega,
                       double beta, double Ub);
+// velocity systems in FP32 sweeps inside FP64 defect correction (k_sor.cu)
+struct HelmF32 {
+  const float *uE, *uW, *uN, *uS, *vE, *vW, *vN, *vS;  // FP32 copies of Geo's velocity coefficients
+};
+void launch_helm_dc_res(cudaStream_t s, const Geo& g, int grid, const double* x, const double* R, const Band& band,
+                        const uint8_t* fl, const double* al, double beta, double Ub, float* r32,
+                        unsigned long long* res_bits);
+void launch_helm32_half(cudaStream_t s, const Geo& g, const HelmF32& h32, int grid, float* d, const float* r,
+                        const float* invd, const Band& band, const uint8_t* fl, const double* al, int colour,
+                        float omega, float beta);
+void launch_helm_add(cudaStream_t s, const Geo& g, int grid, double* x, const float* d);
 void launch_helm_res(cudaStream_t s, const Geo& g, int grid, const double* x, const double* R,
                      const Band& band, const uint8_t* fl, const double* al, double beta, double Ub,
                      unsigned long long* res_bits);

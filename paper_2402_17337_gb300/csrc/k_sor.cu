@@ -244,4 +244,112 @@ void launch_helm_res(cudaStream_t s, const Geo& g, int grid, const double* x, co
   k_helm_res<<<grid2(ni, nj), dim3(TBX, TBY), 0, s>>>(g, grid, x, R, band, fl, al, beta, Ub, res_bits);
 }
 
+// ---- velocity systems in FP32 sweeps inside FP64 defect correction
+// (precision >= 1).  The FP64 residual r = R - A x of the system above
+// (forcing rows: U_b + alpha (x_opp - U_b) - x; solid rows: U_b - x) is
+// stored in FP32, FP32 red-black Gauss-Seidel sweeps solve the correction
+// equation A d = r from d = 0, with the homogeneous forms of the side
+// conditions (forcing rows d = r + alpha d_opp, solid rows d = r), and the
+// FP64 update x += d follows.  Same stopping rule as the FP64 solve.
+namespace {
+
+__global__ void k_helm_dc_res(Geo g, int grid, const double* __restrict__ x, const double* __restrict__ R, Band B,
+                              const uint8_t* __restrict__ fl, const double* __restrict__ al, double beta, double Ub,
+                              float* __restrict__ r32, unsigned long long* res_bits) {
+  HelmCoef h = helm_coef(g, grid);
+  int i = blockIdx.x * blockDim.x + threadIdx.x + h.ilo, j = blockIdx.y * blockDim.y + threadIdx.y + h.jlo;
+  unsigned long long bits = 0ull;
+  if (i <= h.ihi && j <= h.jhi) {
+    const int P = g.pitch;
+    size_t c = at(i, j, P);
+    int bi = i - B.i0, bj = j - B.j0;
+    int kind = K_FLUID;
+    uint8_t f = 0;
+    if (bi >= 0 && bj >= 0 && bi < B.w && bj < B.h) {
+      f = fl[bj * B.w + bi];
+      kind = f & 3;
+    }
+    double r;
+    double xp = x[c];
+    if (kind == K_SOLID) {
+      r = Ub - xp;
+    } else if (kind == K_FORCE) {
+      double a = al[bj * B.w + bi];
+      double xo = a != 0.0 ? x[c + opp_offset(f >> 2, P)] : Ub;
+      r = fma(a, xo - Ub, Ub) - xp;
+    } else {
+      double L = lap5(h.E[i], h.W[i], h.N[j], h.S[j], x[c + 1], x[c - 1], x[c + P], x[c - P], xp);
+      r = R[c] - fma(-beta, L, xp);
+    }
+    r32[c] = (float)r;
+    bits = abs_bits(r);
+  }
+  warp_block_max(bits, res_bits);
+}
+
+__global__ void k_helm32_half(Geo g, HelmF32 h32, int grid, float* __restrict__ d, const float* __restrict__ r,
+                              const float* __restrict__ invd, Band B, const uint8_t* __restrict__ fl,
+                              const double* __restrict__ al, int colour, float omega, float beta) {
+  HelmCoef h = helm_coef(g, grid);
+  const float *E = grid == 0 ? h32.uE : h32.vE, *W = grid == 0 ? h32.uW : h32.vW;
+  const float *N = grid == 0 ? h32.uN : h32.vN, *S = grid == 0 ? h32.uS : h32.vS;
+  int j = blockIdx.y * blockDim.y + threadIdx.y + h.jlo;
+  int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((colour + j) & 1);
+  if (j > h.jhi || i > h.ihi || i < h.ilo) return;
+  const int P = g.pitch;
+  size_t c = at(i, j, P);
+  int bi = i - B.i0, bj = j - B.j0;
+  if (bi >= 0 && bj >= 0 && bi < B.w && bj < B.h) {
+    uint8_t f = fl[bj * B.w + bi];
+    int kind = f & 3;
+    if (kind == K_SOLID) {
+      d[c] = r[c];
+      return;
+    }
+    if (kind == K_FORCE) {
+      float a = (float)al[bj * B.w + bi];
+      float dop = a != 0.f ? d[c + opp_offset(f >> 2, P)] : 0.f;
+      d[c] = fmaf(a, dop, r[c]);
+      return;
+    }
+  }
+  float sum = E[i] * d[c + 1];
+  sum = fmaf(W[i], d[c - 1], sum);
+  sum = fmaf(N[j], d[c + P], sum);
+  sum = fmaf(S[j], d[c - P], sum);
+  float gs = fmaf(beta, sum, r[c]) * invd[c];
+  float dp = d[c];
+  d[c] = fmaf(omega, gs - dp, dp);
+}
+
+__global__ void k_helm_add(Geo g, int grid, double* __restrict__ x, const float* __restrict__ d) {
+  HelmCoef h = helm_coef(g, grid);
+  int i = blockIdx.x * blockDim.x + threadIdx.x + h.ilo, j = blockIdx.y * blockDim.y + threadIdx.y + h.jlo;
+  if (i > h.ihi || j > h.jhi) return;
+  size_t c = at(i, j, g.pitch);
+  x[c] += (double)d[c];
+}
+
+}  // namespace
+
+void launch_helm_dc_res(cudaStream_t s, const Geo& g, int grid, const double* x, const double* R, const Band& band,
+                        const uint8_t* fl, const double* al, double beta, double Ub, float* r32,
+                        unsigned long long* res_bits) {
+  int ni = grid == 0 ? g.nx - 1 : g.nx, nj = grid == 0 ? g.ny : g.ny - 1;
+  k_helm_dc_res<<<grid2(ni, nj), dim3(TBX, TBY), 0, s>>>(g, grid, x, R, band, fl, al, beta, Ub, r32, res_bits);
+}
+
+void launch_helm32_half(cudaStream_t s, const Geo& g, const HelmF32& h32, int grid, float* d, const float* r,
+                        const float* invd, const Band& band, const uint8_t* fl, const double* al, int colour,
+                        float omega, float beta) {
+  int ni = grid == 0 ? g.nx - 1 : g.nx, nj = grid == 0 ? g.ny : g.ny - 1;
+  k_helm32_half<<<grid2((ni + 1) / 2, nj), dim3(TBX, TBY), 0, s>>>(g, h32, grid, d, r, invd, band, fl, al, colour,
+                                                                   omega, beta);
+}
+
+void launch_helm_add(cudaStream_t s, const Geo& g, int grid, double* x, const float* d) {
+  int ni = grid == 0 ? g.nx - 1 : g.nx, nj = grid == 0 ? g.ny : g.ny - 1;
+  k_helm_add<<<grid2(ni, nj), dim3(TBX, TBY), 0, s>>>(g, grid, x, d);
+}
+
 }  // namespace ibm
