@@ -388,15 +388,148 @@ __device__ __forceinline__ void sor32_tile_v4(const Geo32& g, const float* __res
   }
 }
 
+// Third form: like the second, but a thread owns RPT consecutive rows (not
+// rows NY apart), so the N and S neighbours of its cells of the other
+// colour come from its own registers except at the ends of its run; only
+// those end rows and the W/E neighbour of the other colour are read from
+// shared memory.  The colour parity now alternates along a thread's rows; it
+// is fixed per warp and half-sweep (the start row parity), so each half-sweep
+// is compiled for both start parities and picked by a warp-uniform branch.
+// Same arithmetic in the same order as the other forms: identical iterates.
+template <int TY, int K, int NY, bool RDREG>
+__device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __restrict__ e_in, float* __restrict__ e_out,
+                                              const float* __restrict__ r, const float* __restrict__ invd,
+                                              float omega, int zero_init, int bx, int by, float* smem) {
+  using S = Sor32ShapeV4<TY, K, NY, RDREG>;
+  constexpr int HK = S::HK, TK = S::TK, LY = S::LY, RPT = S::RPT, PY = S::PY, PK = S::PK;
+  float(*se)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem);  // [2][PY][PK], cell (ly, kk) at [ly+1][kk+1]
+  float(*sr)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem + 2 * PY * PK);
+  float(*sd)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem + 4 * PY * PK);
+  const int nx = g.nx, ny = g.ny, pk = g.pk;
+  const int k0 = bx * TK - HK, j0 = by * TY - K;
+  const int tx = threadIdx.x, ty = threadIdx.y, ly0 = ty * RPT;
+  for (int t = ty * 32 + tx; t < 2 * (2 * PK + 2 * LY); t += 32 * NY) {
+    const int c = t / (2 * PK + 2 * LY), u = t % (2 * PK + 2 * LY);
+    if (u < 2 * PK)
+      se[c][u < PK ? 0 : PY - 1][u % PK] = 0.f;
+    else
+      se[c][1 + (u - 2 * PK) / 2][(u & 1) ? PK - 1 : 0] = 0.f;
+  }
+  float ev[2][RPT][2];
+  float rv[RDREG ? 2 : 1][RDREG ? RPT : 1][2], dv[RDREG ? 2 : 1][RDREG ? RPT : 1][2];
+  float cE[2][2], cW[2][2], cN[RPT], cS[RPT];  // cE[m][s]: coefficient of the cell at i = 2k + s
+  unsigned long long live = 0ull;              // bit (c, q, m): inside the domain (written back)
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const int k = k0 + tx + 32 * m;
+    const bool ok = k >= 0 && k < pk;
+    cE[m][0] = ok ? g.cE0[k] : 0.f;
+    cE[m][1] = ok ? g.cE1[k] : 0.f;
+    cW[m][0] = ok ? g.cW0[k] : 0.f;
+    cW[m][1] = ok ? g.cW1[k] : 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int ly = ly0 + q, j = j0 + ly;
+    const bool rowok = j >= 0 && j < ny;
+    cN[q] = rowok ? g.pN[j] : 0.f;
+    cS[q] = rowok ? g.pS[j] : 0.f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int kk = tx + 32 * m, k = k0 + kk, i = 2 * k + ((c + j) & 1);
+        const bool in = rowok && k >= 0 && i < nx;
+        const size_t o = (size_t)(c * ny + j) * pk + k;
+        const float x = (in && !zero_init) ? e_in[o] : 0.f;
+        const float rr = in ? r[o] : 0.f, dd = in ? invd[o] : 0.f;
+        ev[c][q][m] = x;
+        se[c][ly + 1][kk + 1] = x;
+        if constexpr (RDREG) {
+          rv[c][q][m] = rr;
+          dv[c][q][m] = dd;
+        } else {
+          sr[c][ly + 1][kk + 1] = rr;
+          sd[c][ly + 1][kk + 1] = dd;
+        }
+        if (in) live |= 1ull << ((c * RPT + q) * 2 + m);
+      }
+  }
+  __syncthreads();
+  // one half-sweep of colour C whose first row has parity S0 (both compile-time)
+  auto half = [&](auto colour, auto start) {
+    constexpr int c = decltype(colour)::value, oc = c ^ 1, S0 = decltype(start)::value;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int s = S0 ^ (q & 1);
+      const int ly = ly0 + q;
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int kk = tx + 32 * m;
+        const float xSelf = ev[oc][q][m];
+        const float xOther = se[oc][ly + 1][kk + (s ? 2 : 0)];
+        const float xN = q < RPT - 1 ? ev[oc][q < RPT - 1 ? q + 1 : q][m] : se[oc][ly + 2][kk + 1];
+        const float xS = q > 0 ? ev[oc][q > 0 ? q - 1 : q][m] : se[oc][ly][kk + 1];
+        const float xE = s ? xOther : xSelf, xW = s ? xSelf : xOther;
+        float sum = (s ? cE[m][1] : cE[m][0]) * xE;
+        sum = fmaf(s ? cW[m][1] : cW[m][0], xW, sum);
+        sum = fmaf(cN[q], xN, sum);
+        sum = fmaf(cS[q], xS, sum);
+        float rr, dd;
+        if constexpr (RDREG) {
+          rr = rv[c][q][m];
+          dd = dv[c][q][m];
+        } else {
+          rr = sr[c][ly + 1][kk + 1];
+          dd = sd[c][ly + 1][kk + 1];
+        }
+        const float gs = (sum - rr) * dd;
+        const float x = ev[c][q][m];
+        const float nxv = fmaf(omega, gs - x, x);
+        ev[c][q][m] = nxv;
+        se[c][ly + 1][kk + 1] = nxv;
+      }
+    }
+    __syncthreads();
+  };
+  const int p0 = (j0 + ly0) & 1;  // parity of this thread's first row
+#pragma unroll 1
+  for (int h = 0; h < K; h += 2) {
+    if (p0) {
+      half(std::integral_constant<int, 0>{}, std::integral_constant<int, 1>{});
+      half(std::integral_constant<int, 1>{}, std::integral_constant<int, 0>{});
+    } else {
+      half(std::integral_constant<int, 0>{}, std::integral_constant<int, 0>{});
+      half(std::integral_constant<int, 1>{}, std::integral_constant<int, 1>{});
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int ly = ly0 + q;
+    if (ly < K || ly >= K + TY) continue;
+    const int j = j0 + ly;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int kk = tx + 32 * m;
+        if (kk < HK || kk >= HK + TK) continue;
+        if (!(live >> ((c * RPT + q) * 2 + m) & 1ull)) continue;
+        e_out[(size_t)(c * ny + j) * pk + (k0 + kk)] = ev[c][q][m];
+      }
+  }
+}
+
 // A tile shape: rows per tile, half-sweeps per launch, thread rows, form
 // (3: sor32_tile; 4: sor32_tile_v4 with r and 1/d in shared memory; 5: with
-// r and 1/d in registers) and minimum resident CTAs per SM.
+// r and 1/d in registers; 6, 7: sor32_tile_v6 likewise) and minimum
+// resident CTAs per SM.
 template <int TY_, int K_, int NY_, int V_, int MINB_>
 struct Cfg {
   static constexpr int TY = TY_, K = K_, NY = NY_, V = V_, MINB = MINB_;
   static constexpr int HK = (K + 1) / 2, TK = 64 - 2 * HK;
   static constexpr size_t smem =
-      std::conditional_t<V == 3, Sor32Shape<TY, K, NY>, Sor32ShapeV4<TY, K, NY, V == 5>>::smem;
+      std::conditional_t<V == 3, Sor32Shape<TY, K, NY>, Sor32ShapeV4<TY, K, NY, V == 5 || V == 7>>::smem;
 };
 
 template <class C>
@@ -404,8 +537,10 @@ __device__ __forceinline__ void tile(const Geo32& g, const float* e_in, float* e
                                      const float* invd, float omega, int zero_init, int bx, int by, float* smem) {
   if constexpr (C::V == 3)
     sor32_tile<C::TY, C::K, C::NY>(g, e_in, e_out, r, invd, omega, zero_init, bx, by, smem);
-  else
+  else if constexpr (C::V == 4 || C::V == 5)
     sor32_tile_v4<C::TY, C::K, C::NY, C::V == 5>(g, e_in, e_out, r, invd, omega, zero_init, bx, by, smem);
+  else
+    sor32_tile_v6<C::TY, C::K, C::NY, C::V == 7>(g, e_in, e_out, r, invd, omega, zero_init, bx, by, smem);
 }
 
 template <class C>
@@ -491,6 +626,9 @@ const Sor32Config kConfigs[] = {
     shape<Cfg<32, 8, 16, 4, 2>>(),  shape<Cfg<48, 8, 16, 4, 2>>(),  shape<Cfg<40, 12, 16, 4, 2>>(),
     shape<Cfg<16, 8, 8, 4, 3>>(),   shape<Cfg<24, 4, 8, 4, 3>>(),   shape<Cfg<64, 16, 16, 4, 1>>(),
     shape<Cfg<16, 8, 8, 5, 2>>(),   shape<Cfg<32, 8, 16, 5, 1>>(),  shape<Cfg<24, 4, 8, 5, 2>>(),
+    shape<Cfg<32, 8, 8, 6, 3>>(),   shape<Cfg<48, 8, 16, 6, 2>>(),  shape<Cfg<40, 12, 16, 6, 2>>(),
+    shape<Cfg<64, 16, 16, 6, 1>>(), shape<Cfg<24, 4, 8, 6, 3>>(),   shape<Cfg<32, 8, 8, 7, 2>>(),
+    shape<Cfg<48, 8, 16, 7, 1>>(),  shape<Cfg<24, 4, 8, 7, 2>>(),
 };
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
