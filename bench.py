@@ -54,6 +54,7 @@ MG_BYTES_PER_CELL_ITER = 104
 # thread rows, form); cold-cache captures
 SOR32_TRAFFIC = {
     ("plunge_2048x1024", (64, 16, 16, 4)): 25.216e6,
+    ("plunge_2048x1024", (80, 16, 16, 6)): 25.228e6,
     ("plunge_4096x2048", (32, 8, 16, 4)): 115.864e6,
 }
 WORKLOADS = ("plunge_2048x1024", "plunge_4096x2048", "batch64")
@@ -385,6 +386,9 @@ def main():
     ap.add_argument("--weights", default=None, help="U-Net weights (default: the package's trained weights)")
     ap.add_argument("--workload", choices=WORKLOADS, default=WORKLOADS[0])
     ap.add_argument("--cases", type=int, default=64, help="batch64: number of cases")
+    ap.add_argument("--sor-shape", type=int, default=-1,
+                    help="fixed FP32 sweep tile shape (index into the library's table; -1: autotuner). "
+                         "For profiler runs, whose per-launch overhead distorts the autotuner's timings")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
@@ -466,6 +470,8 @@ def main():
         s.set("u", cfg.initial_u(s.shape("u")))
         if ws is not None:
             s.set_warmstart(1, ws["net"], ws["cT"])
+        if args.sor_shape >= 0 and precision == 1:
+            s.set_sor_shape(args.sor_shape)
         for _ in range(args.warmup):
             s.step(1)
         state = {n: s.get(n) for n in ("u", "v", "p", "phi")} if rank == 0 else None
