@@ -645,7 +645,7 @@ def main():
             applied = prof["ws_applied"] - main_run["prof0"]["ws_applied"]
             ws_desc = (f"learned: U-Net widths {tuple(m.get('widths', ()))} on the 2x coarsened grid, trained on "
                        f"{m.get('samples')} snapshots of {m.get('runs')} seeded runs (h, k, Re drawn), BF16 "
-                       f"tensor-core kernels; the learned guess is kept only when its residual is below the "
+                       f"tensor-core kernels; the learned guess is kept only when its residual is below half the "
                        f"previous increment's: kept in {kept} of {applied} timed steps")
         line = {
             "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world,

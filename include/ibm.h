@@ -295,7 +295,7 @@ int ibm_unet_train_step(ibm_unet* net, const float* feat_dev, const float* targe
  * from a starting guess): mode 0, the previous increment; mode 1, the
  * previous increment plus the U-Net's prediction of its change (the net is
  * borrowed, not owned), kept only if its residual ||b - L_p phi||_inf is
- * below that of the previous increment (counted in ibm_profile); mode 2, the previous increment and, every step, a
+ * below half that of the previous increment (counted in ibm_profile); mode 2, the previous increment and, every step, a
  * training sample recorded for ibm_get_sample.  The network works on the
  * grid coarsened 2x (nx, ny must be divisible by 16) with four features per
  * coarse cell (initial residual b - L_p phi^n, b, body-cell fraction, p^n,

@@ -1100,8 +1100,9 @@ int step_pre(ibm_ctx* c, ibm_step_stats* st, double* thr) {
       CUDA_TRY(cudaMemcpyAsync(c->phi_old, c->phi, c->nelem * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     if (c->ws_mode == 1) {
       // the plain guess is kept; the learned one replaces it only if it
-      // starts the solve with a smaller residual (the plain iteration is the
-      // fallback and the judge)
+      // starts the solve with less than half the residual (the plain
+      // iteration is the fallback and the judge; a merely smaller maximum
+      // residual did not mean fewer sweeps)
       rc = ibm_unet_forward(c->ws_net, c->ws_feat, c->Hc, c->Wc, c->ws_out, c->stream);
       if (rc) return rc;
       CUDA_TRY(cudaMemcpyAsync(c->phi_old, c->phi, c->nelem * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
@@ -1117,7 +1118,7 @@ int step_pre(ibm_ctx* c, ibm_step_stats* st, double* thr) {
       if (rc) return rc;
       c->prof.launches += 18;
       c->prof.ws_applied += 1;
-      if (r_learned < r_plain)
+      if (r_learned < 0.5 * r_plain)
         c->prof.ws_kept += 1;
       else
         std::swap(c->phi, c->phi_old);

@@ -47,6 +47,8 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=2402)
     ap.add_argument("--eval-start", type=int, default=3)
     ap.add_argument("--eval-steps", type=int, default=10)
+    ap.add_argument("--widths", type=int, nargs=4, default=list(WIDTHS),
+                    help="channels of the four levels (multiples of 16)")
     ap.add_argument("--out", required=True)
     args = ap.parse_args(argv)
 
@@ -62,14 +64,14 @@ def main(argv=None):
         samples.sweeps += s.sweeps
         print(f"captured {len(s.feat)} samples of {c.name} (h={c.h:.3f} k={c.k:.3f} Re={c.Re:.0f}), "
               f"{time.perf_counter() - t0:.0f} s", flush=True)
-    net = ibm.UNet(WIDTHS, seed=args.seed)
+    net = ibm.UNet(tuple(args.widths), seed=args.seed)
     t1 = time.perf_counter()
     cT, hist = warmstart.train(net, samples, epochs=args.epochs, lr=args.lr, seed=args.seed,
                                log=lambda m: print(m, flush=True))
     t_train = time.perf_counter() - t1
     res = warmstart.evaluate(cfg, net, cT, steps=args.eval_steps, start=args.eval_start)
     plain, learned = sum(res["plain"]["sweeps"]), sum(res["learned"]["sweeps"])
-    meta = {"workload": cfg.name, "widths": WIDTHS, "runs": args.runs, "steps_per_run": args.steps,
+    meta = {"workload": cfg.name, "widths": list(args.widths), "runs": args.runs, "steps_per_run": args.steps,
             "samples": len(samples.feat), "epochs": args.epochs, "lr": args.lr, "seed": args.seed,
             "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "train_seconds": t_train,
             "eval": {"steps": [args.eval_start, args.eval_start + args.eval_steps],
