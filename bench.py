@@ -57,7 +57,7 @@ SOR32_TRAFFIC = {
     ("plunge_2048x1024", (80, 16, 16, 6)): 25.228e6,
     ("plunge_4096x2048", (32, 8, 16, 4)): 115.864e6,
 }
-WORKLOADS = ("plunge_2048x1024", "plunge_4096x2048", "batch64")
+WORKLOADS = ("plunge_2048x1024", "plunge_4096x2048", "unet_1024x512", "batch64")
 METRIC = "cell-steps/s at div<1e-8: learned warm-start+mixed vs plain FP64, one GB300"
 
 
@@ -452,7 +452,9 @@ def main():
     learned = None
     if args.warmstart == "learned" and args.precision in ("mixed", "mg"):
         from paper_2402_17337_gb300 import warmstart
-        path = args.weights or warmstart.DEFAULT_WEIGHTS
+        path = args.weights or warmstart.weights_for(cfg.name)
+        if not os.path.exists(path):
+            path = warmstart.DEFAULT_WEIGHTS
         if not os.path.exists(path):
             raise SystemExit(f"no U-Net weights at {path}: run paper_2402_17337_gb300.train_warmstart "
                              f"or pass --warmstart plain")

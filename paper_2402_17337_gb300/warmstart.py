@@ -28,6 +28,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "unet_plunge_2048x1024.npz")
 
 
+def weights_for(workload):
+    """Path of the package's trained weights for a workload (may not exist)."""
+    return os.path.join(HERE, "weights", f"unet_{workload}.npz")
+
+
 @dataclasses.dataclass
 class Samples:
     feat: list
