@@ -68,6 +68,27 @@ def env_int(k, d):
         return d
 
 
+def reduce_over_ranks(x, dist, op, device):
+    """x reduced over the ranks of the process group (sum or max; x itself
+    with no group).  device: where the reduction tensor lives (cuda for NCCL,
+    cpu for gloo)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_throughput(cells_ok, ms, dist=None, device="cuda"):
+    """Whole-job throughput of independent replicas (one per rank, weak
+    scaling): the cells of every rank's counted steps over the slowest
+    rank's time.  Returns (cell-steps/s, total cells, max ms)."""
+    cells = reduce_over_ranks(cells_ok, dist, "sum", device)
+    t_max = reduce_over_ranks(ms, dist, "max", device)
+    return cells / (t_max / 1e3), cells, t_max
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -233,12 +254,6 @@ def run_batch(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def reduce(x, op):
-        if not dist:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=op)
-        return float(t.item())
 
     omegas = []
     for c in cfgs:  # each case's relaxation factor from the device probe (untimed)
@@ -273,11 +288,9 @@ def run_batch(args):
     barrier()
     torch.cuda.profiler.stop()
     clk = clocks.stop() if not args.no_clocks else None
-    ms = reduce(e0.elapsed_time(e1), dist.ReduceOp.MAX if dist else None)
     prof = batch.profile()
-    ok_cells = sum(n for st in stats for n, c, x in zip(cells, cfgs, st) if x["div_max"] < c.div_tol)
-    ok_cells = reduce(ok_cells, dist.ReduceOp.SUM if dist else None)
-    value = ok_cells / (ms / 1e3)
+    ok_local = sum(n for st in stats for n, c, x in zip(cells, cfgs, st) if x["div_max"] < c.div_tol)
+    value, ok_cells, ms = replica_throughput(ok_local, e0.elapsed_time(e1), dist, "cuda")
     batch.close()
     for s in ss:
         s.close()
@@ -321,12 +334,11 @@ def run_batch(args):
                     pn[n][...] = s.get(n)
             ok2 += sum(n for n, c, x in zip(cells, cfgs, st) if x["div_max"] < c.div_tol)
         barrier()
-        te = reduce(time.perf_counter() - t0, dist.ReduceOp.MAX if dist else None)
-        ok2 = reduce(ok2, dist.ReduceOp.SUM if dist else None)
+        e2e_value, _, _ = replica_throughput(ok2, 1e3 * (time.perf_counter() - t0), dist, "cuda")
         batch2.close()
         for s in ss2:
             s.close()
-        e2e = {"value": ok2 / te, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+        e2e = {"value": e2e_value, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                "note": "a second batch over the same steps; per step every case's u, v, p, phi copied in from "
                        "pinned host memory, batch step, copied back; host wall clock"}
 
@@ -428,19 +440,6 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t)
-        return float(t.item())
 
     # pressure relaxation factor of this grid from the device probe (untimed),
     # used by every timed run below
@@ -491,13 +490,15 @@ def main():
         barrier()
         torch.cuda.profiler.stop()
         clk = clocks.stop() if sample_clocks else None
-        ms = max_over_ranks(e0.elapsed_time(e1))
+        ms_local = e0.elapsed_time(e1)
         prof = s.profile()
-        ok = sum_over_ranks(sum(1 for st in stats if st["div_max"] < cfg.div_tol))
+        ok_local = sum(1 for st in stats if st["div_max"] < cfg.div_tol)
+        value, cells_ok, ms = replica_throughput(cfg.cells * ok_local, ms_local, dist, "cuda")
+        ok = cells_ok / cfg.cells
         final = {n: s.get(n) for n in ("u", "v", "p")} if rank == 0 else None
         forces = s.forces() if rank == 0 else None
         s.close()
-        return {"value": cfg.cells * ok / (ms / 1e3), "ms": ms, "stats": stats, "ok": int(ok), "clocks": clk,
+        return {"value": value, "ms": ms, "stats": stats, "ok": int(ok), "clocks": clk,
                 "launches": prof["launches"] - prof0["launches"], "prof": prof, "prof0": prof0, "state": state,
                 "final": final, "forces": forces}
 
@@ -584,11 +585,8 @@ def main():
         barrier()
         te = time.perf_counter() - t0
         s2.close()
-        if dist:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": cfg.cells * ok_e2e * world / te, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d,
+        e2e_value, _, _ = replica_throughput(cfg.cells * ok_e2e, 1e3 * te, dist, "cuda")
+        e2e = {"value": e2e_value, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": h2d,
                "note": "same steps as the timed window on a second context; per step u, v, p, phi copied "
                        "in from pinned host memory, step, copied back; host wall clock"}
