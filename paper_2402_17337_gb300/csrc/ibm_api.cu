@@ -982,8 +982,10 @@ int solve_poisson_mixed(ibm_ctx* c, double tol, int maxs, int* sweeps, double* r
 }
 
 // Velocity system in FP32 sweeps inside FP64 defect correction: FP64
-// residual (stored in FP32) and norm, 8 FP32 red-black sweeps on the
-// correction equation from zero, FP64 update; *sweeps counts FP32 sweeps.
+// residual (stored in FP32) and norm, 4 FP32 red-black sweeps on the
+// correction equation from zero (the Gauss-Seidel contraction of these
+// systems, (I - beta L) with beta / h^2 small, reaches the resolution of an
+// FP32 correction in a few sweeps), FP64 update; *sweeps counts FP32 sweeps.
 int solve_helm_mixed(ibm_ctx* c, int grid, double beta, double Ub, int* sweeps, double* res) {
   const Geo& g = c->geo;
   double* x = grid == 0 ? c->uh : c->vh;
@@ -991,7 +993,7 @@ int solve_helm_mixed(ibm_ctx* c, int grid, double beta, double Ub, int* sweeps, 
   const float* invd = grid == 0 ? c->hinv_u : c->hinv_v;
   const uint8_t* fl = grid == 0 ? c->fu : c->fv;
   const double* al = grid == 0 ? c->au : c->av;
-  const int m = 8;
+  const int m = 4;
   for (int s = 0;; s += m) {
     CUDA_TRY(cudaMemsetAsync(&c->sc->res_bits, 0, 8, c->stream));
     launch_helm_dc_res(c->stream, g, grid, x, R, c->band, fl, al, beta, Ub, c->hr32, &c->sc->res_bits);

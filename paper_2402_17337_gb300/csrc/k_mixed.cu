@@ -51,31 +51,35 @@ __device__ inline void block_max_bits(unsigned long long v, unsigned long long* 
 // solve is added (phi_out = phi_in + e, neighbours included on the fly, so
 // phi_out must differ from phi_in); r is stored in FP32, split by colour, as
 // the next inner right-hand side.
-__global__ void k_dc_residual(Geo g, int pk, const double* __restrict__ phi_in, double* __restrict__ phi_out,
-                              const float* __restrict__ e, const double* __restrict__ b, float* __restrict__ r32,
-                              int add_e, unsigned long long* __restrict__ res_bits) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+// phi_out = phi_in + e (the update; one conversion and one FP64 add a cell)
+__global__ void k_dc_update(Geo g, int pk, const double* __restrict__ phi_in, double* __restrict__ phi_out,
+                            const float* __restrict__ e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  const size_t c = at(i, j, g.pitch);
+  phi_out[c] = phi_in[c] + (double)e[rb_at(i, j, g.ny, pk)];
+}
+
+// r = b - L_p phi in FP64 (stored in FP32, split by colour) and its norm;
+// grid-stride over 32 x 8 tiles with a bounded number of blocks
+__global__ void k_dc_residual(Geo g, int pk, const double* __restrict__ phi, const double* __restrict__ b,
+                              float* __restrict__ r32, unsigned long long* __restrict__ res_bits) {
   unsigned long long bits = 0ull;
-  const int nx = g.nx, ny = g.ny;
-  if (i < nx && j < ny) {
-    const int P = g.pitch;
-    size_t c = at(i, j, P);
-    double fP = phi_in[c], fE = phi_in[c + 1], fW = phi_in[c - 1], fN = phi_in[c + P], fS = phi_in[c - P];
-    if (add_e) {
-      fP += (double)e[rb_at(i, j, ny, pk)];
-      if (i < nx - 1) fE += (double)e[rb_at(i + 1, j, ny, pk)];
-      if (i > 0) fW += (double)e[rb_at(i - 1, j, ny, pk)];
-      if (j < ny - 1) fN += (double)e[rb_at(i, j + 1, ny, pk)];
-      if (j > 0) fS += (double)e[rb_at(i, j - 1, ny, pk)];
-      phi_out[c] = fP;
-    }
-    double L = g.pE[i] * (fE - fP);
-    L = fma(g.pW[i], fW - fP, L);
-    L = fma(g.pN[j], fN - fP, L);
-    L = fma(g.pS[j], fS - fP, L);
-    double r = b[c] - L;
+  const int nx = g.nx, ny = g.ny, P = g.pitch;
+  const int tx = (nx + 31) / 32, nt = tx * ((ny + 7) / 8);
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    const int i = (t % tx) * 32 + threadIdx.x, j = (t / tx) * 8 + threadIdx.y;
+    if (i >= nx || j >= ny) continue;
+    const size_t c = at(i, j, P);
+    const double fP = phi[c];
+    double L = g.pE[i] * (phi[c + 1] - fP);
+    L = fma(g.pW[i], phi[c - 1] - fP, L);
+    L = fma(g.pN[j], phi[c + P] - fP, L);
+    L = fma(g.pS[j], phi[c - P] - fP, L);
+    const double r = b[c] - L;
     r32[rb_at(i, j, ny, pk)] = (float)r;
-    bits = abs_bits(r);
+    const unsigned long long rb = abs_bits(r);
+    bits = rb > bits ? rb : bits;
   }
   block_max_bits(bits, res_bits);
 }
@@ -652,8 +656,9 @@ void sor32_describe(int cfg, int* ty, int* k, int* ny, int* form) {
 
 void launch_dc_residual(cudaStream_t s, const Geo& g, int pk, const double* phi_in, double* phi_out, const float* e,
                         const double* b, float* r32, int add_e, unsigned long long* res_bits) {
-  dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
-  k_dc_residual<<<grd, blk, 0, s>>>(g, pk, phi_in, phi_out, e, b, r32, add_e, res_bits);
+  const int nt = ((g.nx + 31) / 32) * ((g.ny + 7) / 8);
+  if (add_e) k_dc_update<<<dim3((g.nx + 31) / 32, (g.ny + 7) / 8), dim3(32, 8), 0, s>>>(g, pk, phi_in, phi_out, e);
+  k_dc_residual<<<nt < 1216 ? nt : 1216, dim3(32, 8), 0, s>>>(g, pk, add_e ? phi_out : phi_in, b, r32, res_bits);
 }
 
 void launch_sor32(cudaStream_t s, int cfg, const Geo32& g, const float* e_in, float* e_out, const float* r,
