@@ -45,3 +45,33 @@ def test_product_path_never_imports_the_oracle():
                 txt = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, fn
                 assert "ibm_oracle" not in txt, fn
+
+
+def test_create_grid_rejects_invalid_parameters_before_touching_the_device():
+    """Parameter validation of ibm_create_grid runs on the host before any
+    CUDA call, so it is checked here without a GPU: sizes below 4, ny above
+    the 8192 limit of the outflow-flux reduction, an unknown precision,
+    non-positive Re or dt, no pressure tolerance, omega outside (0, 2)."""
+    import ctypes as C
+    from paper_2402_17337_gb300 import build
+    build.build()
+    import paper_2402_17337_gb300 as ibm
+    L = ibm.lib()
+
+    def create(**over):
+        kw = dict(x0=-2.0, x1=5.0, y0=-2.0, y1=2.0, nx=70, ny=45, hmin=0.0, ubox=(-1.0, 2.0, -0.75, 0.75), bc=0,
+                  u_in=1.0, Re=100.0, dt=1e-3, precision=0, ptol=1e-8, prtol=0.0, htol=1e-12, check_p=8,
+                  check_h=2, max_sweeps=1000, omega_p=1.9, omega_h=1.0, stream=None)
+        kw.update(over)
+        P = ibm.GridParams(kw["x0"], kw["x1"], kw["y0"], kw["y1"], kw["nx"], kw["ny"], kw["hmin"],
+                           (C.c_double * 4)(*kw["ubox"]), kw["bc"], kw["u_in"], kw["Re"], kw["dt"], kw["precision"],
+                           kw["ptol"], kw["prtol"], kw["htol"], kw["check_p"], kw["check_h"], kw["max_sweeps"],
+                           kw["omega_p"], kw["omega_h"], kw["stream"])
+        h = C.c_void_p()
+        rc = L.ibm_create_grid(C.byref(P), C.byref(h))
+        return rc, L.ibm_last_error().decode()
+
+    for over in (dict(nx=3), dict(ny=3), dict(ny=8193), dict(precision=3), dict(precision=-1), dict(Re=0.0),
+                 dict(dt=-1.0), dict(ptol=0.0), dict(bc=2), dict(omega_p=2.0), dict(omega_h=2.5)):
+        rc, msg = create(**over)
+        assert rc == -1 and msg, (over, rc, msg)

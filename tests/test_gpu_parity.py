@@ -60,9 +60,14 @@ def check_flags(o, g):
     assert np.array_equal(o.flags(2), g.flags(2))
 
 
-@pytest.mark.parametrize("idx", [0, 1])
-def test_steps_match_oracle_small_grids(idx):
-    cfg = W.small_cases()[idx]
+@pytest.mark.parametrize("case", ["plunging_uniform", "plunging_stretched", "stationary_stretched"])
+def test_steps_match_oracle_small_grids(case):
+    """Small grids, several thread tiles with ragged edges; the last case is
+    the degenerate stationary foil (h = 0: no body velocity, fixed forcing
+    nodes) in the free stream."""
+    import dataclasses
+    cfg = {"plunging_uniform": W.small_cases()[0], "plunging_stretched": W.small_cases()[1],
+           "stationary_stretched": dataclasses.replace(W.small_cases()[1], h=0.0, k=0.0)}[case]
     o, g = pair(cfg)
     o.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
     g.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
@@ -188,18 +193,21 @@ def test_nan_rhs_reports_diverged_and_cap_reports_noconv():
     assert rc == -3 and s == 3
 
 
-def test_full_size_2048x1024_step_properties():
-    """At the 2048x1024 stretched size the oracle cannot run a step, so the
-    GPU step is checked with the oracle's operators applied to the GPU's own
+@pytest.mark.parametrize("workload,precision", [("plunge_2048x1024", 0), ("plunge_2048x1024", 1),
+                                                ("plunge_2048x1024", 2), ("plunge_4096x2048", 1)])
+def test_full_size_step_properties(workload, precision):
+    """At the full stretched sizes the oracle cannot run a step, so the GPU
+    step is checked with the oracle's operators applied to the GPU's own
     fields: the explicit predictor, the velocity-system residuals, the
     right-hand side, the Poisson residual, the projection and the
-    classification, all at full size."""
-    cfg = W.plunge_2048x1024()
+    classification, at full size, for the plain FP64 path, the mixed path
+    (the configuration bench.py times) and the multigrid variant."""
+    cfg = getattr(W, workload)()
     Solver = gpu()
     kw = dict(x0=cfg.x0, x1=cfg.x1, y0=cfg.y0, y1=cfg.y1, nx=cfg.nx, ny=cfg.ny, hmin=cfg.hmin,
               ubox=cfg.ubox, Re=cfg.Re, dt=cfg.dt, ptol=cfg.ptol, htol=cfg.htol, check_p=cfg.check_p,
               check_h=cfg.check_h, omega_p=cfg.omega())
-    g = Solver(**kw)
+    g = Solver(**kw, precision=precision)
     g.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
     o = oracle.Sim(**kw)
     o.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
