@@ -309,6 +309,22 @@ int ibm_set_warmstart(ibm_ctx* ctx, int mode, ibm_unet* net, double target_scale
  * phi^n).  The learned form predicts the change from the base guess. */
 int ibm_set_warmstart_base(ibm_ctx* ctx, int base);
 
+/* Preconditioner of the FCG iteration of precision 2 (the multigrid
+ * variant; a network used as preconditioner rather than warm start).
+ * kind 0: one V(2,2)-cycle (default).  kind 1: a two-level cycle whose
+ * coarse level is the U-Net: pre_smooth (0 or 1) launches of two red-black
+ * Gauss-Seidel sweeps from zero, the residual restricted (volume-weighted)
+ * to the 2x coarsened grid, there replaced by net's prediction from the
+ * features of ibm_set_warmstart with channel 0 the restricted residual over
+ * its infinity norm s (channels 1-3 taken when the solve starts), the
+ * prediction times s * target_scale prolonged bilinearly, two
+ * post-smoothing sweeps.  The FP64 defect correction and its tolerance are
+ * unchanged, so the result meets the same residual bound whatever the
+ * network predicts.  net stays owned by the caller and must outlive its use
+ * here; nx and ny divisible by 16.  Errors: IBM_E_INVAL (precision not 2,
+ * bad kind, missing net, sizes), IBM_E_CUDA. */
+int ibm_set_preconditioner(ibm_ctx* ctx, int kind, ibm_unet* net, double target_scale, int pre_smooth);
+
 /* Last recorded sample (mode 2): feat [Hc][Wc][4] and target [Hc][Wc]
  * (host, FP32); either may be NULL; *Hc, *Wc receive the coarse sizes. */
 int ibm_get_sample(const ibm_ctx* ctx, float* feat, float* target, int* Hc, int* Wc);

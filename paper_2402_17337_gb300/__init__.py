@@ -98,6 +98,7 @@ def lib():
                                               C.POINTER(C.c_double), _VP]
             L.ibm_set_warmstart.argtypes = [_VP, C.c_int, _VP, C.c_double]
             L.ibm_set_warmstart_base.argtypes = [_VP, C.c_int]
+            L.ibm_set_preconditioner.argtypes = [_VP, C.c_int, _VP, C.c_double, C.c_int]
             L.ibm_get_sample.argtypes = [_VP, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_int),
                                          C.POINTER(C.c_int)]
             L.ibm_tune_omega.argtypes = [_VP, C.c_int, _D]
@@ -267,6 +268,12 @@ class Solver:
         """0: previous increment; 1: learned (U-Net net); 2: previous increment + samples."""
         self._ws_net = net  # keep the network alive while the context uses it
         _check(lib().ibm_set_warmstart(self._h, mode, net._h if net is not None else None, target_scale))
+
+    def set_preconditioner(self, kind, net=None, target_scale=1.0, pre_smooth=1):
+        """Precision 2: 0 V-cycle; 1 two-level cycle with the U-Net net as coarse level."""
+        self._pc_net = net  # keep the network alive while the context uses it
+        _check(lib().ibm_set_preconditioner(self._h, kind, net._h if net is not None else None, target_scale,
+                                            pre_smooth))
 
     def set_warmstart_base(self, base):
         """0: previous increment; 1: linear extrapolation 2 phi^n - phi^(n-1)."""

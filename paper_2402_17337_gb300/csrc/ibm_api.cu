@@ -141,6 +141,14 @@ struct ibm_ctx {
   float *fcg_x = nullptr, *fcg_p = nullptr, *fcg_q = nullptr;  // level-0 FCG vectors
   void* fcg_sc = nullptr;                                     // device scalars of the FCG iteration
   const float *mg_dxv = nullptr, *mg_dyv = nullptr;           // level-0 cell widths (inner products)
+  // preconditioner of the FCG iteration: 0 the V-cycle, 1 a two-level cycle
+  // whose coarse level (level 1) is corrected by a U-Net
+  int pc_kind = 0;
+  int pc_pre = 1;  // pre-smoothing launches (0 or 1) of the two-level cycle
+  ibm_unet* pc_net = nullptr;
+  double pc_cT = 1.0;
+  float *pc_feat = nullptr, *pc_out = nullptr;
+  unsigned long long* pc_max = nullptr;
   // body and band
   bool has_body = false;
   double chord = 1, tc = 0.12, h = 0, k = 0, xb = 0, yb0 = 0;
@@ -620,6 +628,34 @@ void mg_vcycle(ibm_ctx* c, int zero_first) {
   c->prof.launches += 4 * bottom + 1;
 }
 
+// Two-level cycle with the U-Net as the coarse level (the preconditioner
+// the network provides): optional pre-smoothing by two red-black
+// Gauss-Seidel sweeps from zero, the residual restricted to level 1 (the
+// grid the network works on), the network's correction of level 1 from that
+// residual (channel 0) and the values of b, body fraction and p taken at the
+// start of the solve (channels 1-3), bilinear prolongation, two
+// post-smoothing sweeps.  The network replaces the whole coarse hierarchy of
+// the V-cycle; FCG tolerates a preconditioner that is neither linear nor
+// symmetric.
+void nn_cycle(ibm_ctx* c) {
+  MgLevel& A = c->mg[0];
+  MgLevel& B = c->mg[1];
+  if (c->pc_pre) {
+    launch_sor32(c->stream, c->mg_shape, A.g, A.e[A.cur], A.e[A.cur ^ 1], A.r, A.invd, 1.0f, 1);
+    A.cur ^= 1;
+  } else {
+    cudaMemsetAsync(A.e[A.cur], 0, (size_t)2 * A.g.ny * A.g.pk * sizeof(float), c->stream);
+  }
+  launch_mg_restrict(c->stream, A, A.e[A.cur], B);
+  launch_nnp_features(c->stream, B, c->pc_feat, c->pc_max);
+  ibm_unet_forward(c->pc_net, c->pc_feat, B.g.ny, B.g.nx, c->pc_out, c->stream);
+  launch_nnp_correction(c->stream, B, c->pc_out, c->pc_cT, c->pc_max, B.e[B.cur]);
+  launch_mg_prolong(c->stream, B, B.e[B.cur], A, A.e[A.cur]);
+  launch_sor32(c->stream, c->mg_shape, A.g, A.e[A.cur], A.e[A.cur ^ 1], A.r, A.invd, 1.0f, 0);
+  A.cur ^= 1;
+  c->prof.launches += c->pc_pre + 6 + unet_forward_launches();
+}
+
 // One iteration of flexible conjugate gradients, FCG(1), on level 0's
 // correction equation L x = r (r is level 0's right-hand side, updated in
 // place), preconditioned by one V-cycle: z = V(r); p = z + beta p with
@@ -629,7 +665,10 @@ void mg_vcycle(ibm_ctx* c, int zero_first) {
 // the stretched directions cross).
 void fcg_iter(ibm_ctx* c, int first) {
   MgLevel& L0 = c->mg[0];
-  mg_vcycle(c, 1);
+  if (c->pc_kind == 1)
+    nn_cycle(c);
+  else
+    mg_vcycle(c, 1);
   const float* z = L0.e[L0.cur];
   if (!first) launch_fcg_dot(c->stream, L0, c->mg_dxv, c->mg_dyv, z, c->fcg_q, c->fcg_sc);
   launch_fcg_dir(c->stream, L0, z, c->fcg_p, c->fcg_sc, first);
@@ -639,6 +678,7 @@ void fcg_iter(ibm_ctx* c, int first) {
 }
 
 int fcg_launches(const ibm_ctx* c) {
+  if (c->pc_kind == 1) return c->pc_pre + 6 + unet_forward_launches() + 4;
   const int bottom = c->mg_tail >= 1 ? c->mg_tail : (int)c->mg.size() - 1;
   return 4 * bottom + 1 + 4;
 }
@@ -646,7 +686,10 @@ int fcg_launches(const ibm_ctx* c) {
 // CUDA graphs of one FCG iteration (first and later); direct launches if the
 // stream cannot be captured.
 void mg_capture(ibm_ctx* c) {
-  if (c->mg_graph[0] || c->mg_graph_failed) return;
+  // the two-level cycle runs as direct launches: its graph would hold
+  // pointers into the network's buffers, which another use of the same
+  // network at other sizes reallocates
+  if (c->mg_graph[0] || c->mg_graph_failed || c->pc_kind == 1) return;
   for (int z = 0; z < 2; ++z) {
     cudaGraph_t g = nullptr;
     const long long launches = c->prof.launches;
@@ -671,7 +714,7 @@ void mg_capture(ibm_ctx* c) {
 int fcg_iters(ibm_ctx* c, int m) {
   CUDA_TRY(cudaMemsetAsync(c->fcg_x, 0, (size_t)2 * c->ny * c->geo32.pk * sizeof(float), c->stream));
   for (int k = 0; k < m; ++k) {
-    if (c->mg_graph[0]) {
+    if (c->mg_graph[0] && c->pc_kind == 0) {
       CUDA_TRY(cudaGraphLaunch(c->mg_graph[k == 0 ? 0 : 1], c->stream));
       c->prof.launches += fcg_launches(c) - (k == 0 ? 1 : 0);
     } else {
@@ -692,6 +735,10 @@ int solve_poisson_mg(ibm_ctx* c, double tol, int maxc, int* cycles, double* res)
   const Geo& g = c->geo;
   mg_capture(c);
   MgLevel& L0 = c->mg[0];
+  if (c->pc_kind == 1) {  // channels 1-3 of the network's features, fixed during the solve
+    launch_ws_features(c->stream, g, c->Hc, c->Wc, c->b, c->phi, c->p, c->band, c->fc, c->pc_feat, c->pc_max);
+    c->prof.launches += 2;
+  }
   double* cur = c->phi;
   double* alt = c->phi2;
   int s = 0, add = 0, m = 0;
@@ -724,7 +771,11 @@ int solve_poisson_mg(ibm_ctx* c, double tol, int maxc, int* cycles, double* res)
       double target = std::log(tol / r);
       if (target < std::log(1e-4)) target = std::log(1e-4);
       const int want = (int)std::ceil(target / rate);
-      c->mg_cycles = want < 1 ? 1 : (want > 64 ? 64 : want);
+      // a V-cycle reduces the residual by about 0.5 or better, so 64 cycles
+      // always reach 1e-4; the two-level cycle without a coarse hierarchy
+      // needs longer Krylov runs
+      const int run_max = c->pc_kind == 1 ? 512 : 64;
+      c->mg_cycles = want < 1 ? 1 : (want > run_max ? run_max : want);
     }
     m = c->mg_cycles;
     if (s + m > maxc) m = maxc - s;
@@ -1124,7 +1175,7 @@ int step_pre(ibm_ctx* c, ibm_step_stats* st, double* thr) {
       launch_poisson_res(c->stream, g, c->phi_old, c->b, &c->sc->res_bits);
       rc = read_norm(c, &c->sc->res_bits, &r_plain);
       if (rc) return rc;
-      c->prof.launches += 18;
+      c->prof.launches += unet_forward_launches() + 3;
       c->prof.ws_applied += 1;
       if (r_learned < 0.5 * r_plain)
         c->prof.ws_kept += 1;
@@ -1823,6 +1874,35 @@ int ibm_set_warmstart(ibm_ctx* c, int mode, ibm_unet* net, double target_scale) 
   c->ws_net = net;
   c->ws_cT = mode ? target_scale : 1.0;
   c->has_sample = false;
+  return IBM_OK;
+}
+
+int ibm_set_preconditioner(ibm_ctx* c, int kind, ibm_unet* net, double target_scale, int pre_smooth) {
+  if (!c) return fail(IBM_E_INVAL, "null context");
+  if (c->P.precision != 2) return fail(IBM_E_INVAL, "the preconditioner applies to precision 2 (FCG) only");
+  if (kind < 0 || kind > 1) return fail(IBM_E_INVAL, "preconditioner kind must be 0 or 1");
+  if (kind == 1) {
+    if (!net) return fail(IBM_E_INVAL, "the two-level preconditioner needs a network");
+    if (c->nx % 16 || c->ny % 16) return fail(IBM_E_INVAL, "the two-level preconditioner needs nx and ny divisible by 16");
+    if (!(target_scale > 0.0)) return fail(IBM_E_INVAL, "target_scale must be positive");
+    if (pre_smooth < 0 || pre_smooth > 1) return fail(IBM_E_INVAL, "pre_smooth must be 0 or 1");
+    if (c->mg.size() < 2 || c->mg[1].g.nx != c->nx / 2 || c->mg[1].g.ny != c->ny / 2)
+      return fail(IBM_E_INVAL, "level 1 of the hierarchy is not the 2x coarsened grid");
+    if (!c->pc_feat) {
+      c->Hc = c->ny / 2;
+      c->Wc = c->nx / 2;
+      const size_t nc = (size_t)c->Hc * c->Wc;
+      int rc = 0;
+      rc |= c->alloc(&c->pc_feat, 4 * nc);
+      rc |= c->alloc(&c->pc_out, nc);
+      rc |= c->alloc(&c->pc_max, 4);
+      if (rc) return IBM_E_CUDA;
+    }
+  }
+  c->pc_kind = kind;
+  c->pc_net = kind ? net : nullptr;
+  c->pc_cT = kind ? target_scale : 1.0;
+  c->pc_pre = kind ? pre_smooth : 1;
   return IBM_OK;
 }
 

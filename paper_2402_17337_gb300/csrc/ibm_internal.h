@@ -194,6 +194,13 @@ void launch_ws_apply(cudaStream_t s, const Geo& g, int Hc, int Wc, const float* 
                      const unsigned long long* ws_max, double* phi);
 void launch_ws_target(cudaStream_t s, const Geo& g, int Hc, int Wc, const double* phi_new, const double* phi_old,
                       const DevScalars* sc, double cT, const unsigned long long* ws_max, float* target);
+// kernels launched by one ibm_unet_forward
+int unet_forward_launches();
+// U-Net coarse level of the two-level preconditioner: channel 0 of feat from
+// level C's residual (max into *smax), and C's correction from the output
+void launch_nnp_features(cudaStream_t s, const MgLevel& C, float* feat, unsigned long long* smax);
+void launch_nnp_correction(cudaStream_t s, const MgLevel& C, const float* out, double cT,
+                           const unsigned long long* smax, float* e);
 
 // message for ibm_last_error() on the calling thread
 void set_last_error(const char* msg);

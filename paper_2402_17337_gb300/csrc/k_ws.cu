@@ -131,7 +131,50 @@ __global__ void k_extrapolate(Geo g, double* __restrict__ phi, double* __restric
   phi_prev[c] = a;
 }
 
+// ---- the U-Net as the coarse level of a two-level preconditioner (FCG,
+// precision 2).  Channel 0 of the features is the level-1 residual (the
+// volume-weighted restriction of the fine residual, colour-split layout)
+// over its infinity norm s; channels 1-3 keep the values taken at the start
+// of the solve.  The network's output times s c_T is the level-1 correction.
+__global__ void k_nnp_features(const MgLevel C, float* __restrict__ feat, unsigned long long* __restrict__ smax) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+  float v = 0.f;
+  if (I < C.g.nx && J < C.g.ny) {
+    v = C.r[rb_at(I, J, C.g.ny, C.g.pk)];
+    feat[((size_t)J * C.g.nx + I) * 4] = v;
+  }
+  block_max_abs((double)v, smax);
+}
+
+__global__ void k_nnp_normalize(long npix, float* __restrict__ feat, const unsigned long long* __restrict__ smax) {
+  const double s = bits2d(*smax);
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < npix; k += (long)gridDim.x * blockDim.x)
+    feat[4 * k] = s > 0.0 ? (float)(feat[4 * k] / s) : 0.f;
+}
+
+__global__ void k_nnp_correction(const MgLevel C, const float* __restrict__ out, double cT,
+                                 const unsigned long long* __restrict__ smax, float* __restrict__ e) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= C.g.nx || J >= C.g.ny) return;
+  const double s = bits2d(*smax);
+  e[rb_at(I, J, C.g.ny, C.g.pk)] = (float)(s * cT * (double)out[(size_t)J * C.g.nx + I]);
+}
+
 }  // namespace
+
+void launch_nnp_features(cudaStream_t s, const MgLevel& C, float* feat, unsigned long long* smax) {
+  cudaMemsetAsync(smax, 0, sizeof(unsigned long long), s);
+  dim3 blk(32, 8), grd((C.g.nx + 31) / 32, (C.g.ny + 7) / 8);
+  k_nnp_features<<<grd, blk, 0, s>>>(C, feat, smax);
+  const long npix = (long)C.g.nx * C.g.ny;
+  k_nnp_normalize<<<(unsigned)((npix + 255) / 256 > 1216 ? 1216 : (npix + 255) / 256), 256, 0, s>>>(npix, feat, smax);
+}
+
+void launch_nnp_correction(cudaStream_t s, const MgLevel& C, const float* out, double cT,
+                           const unsigned long long* smax, float* e) {
+  dim3 blk(32, 8), grd((C.g.nx + 31) / 32, (C.g.ny + 7) / 8);
+  k_nnp_correction<<<grd, blk, 0, s>>>(C, out, cT, smax, e);
+}
 
 void launch_extrapolate(cudaStream_t s, const Geo& g, double* phi, double* phi_prev) {
   dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);

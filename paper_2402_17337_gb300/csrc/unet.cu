@@ -342,6 +342,16 @@ int ibm_unet_grads(const ibm_unet* n, float* host, long long count) {
   return IBM_OK;
 }
 
+}  // extern "C"
+
+namespace ibm {
+// kernels one forward pass launches: input packing, 15 convolutions, 3
+// poolings, 3 upsamplings
+int unet_forward_launches() { return 1 + 15 + 3 + 3; }
+}  // namespace ibm
+
+extern "C" {
+
 int ibm_unet_forward(ibm_unet* n, const float* feat, int H, int W, float* out, void* stream) {
   if (!n || !feat || !out) return ufail(IBM_E_INVAL, "null argument");
   if (H < 8 || W < 8 || H % 8 || W % 8) return ufail(IBM_E_INVAL, "U-Net input sizes must be multiples of 8");

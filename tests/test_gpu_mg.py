@@ -77,6 +77,60 @@ def test_mg_steps_match_fp64_oracle(idx):
     assert max(errs.values()) <= MIXED_TOL, errs
 
 
+def test_unet_two_level_preconditioner_meets_the_same_tolerance():
+    """The U-Net as the coarse level of the FCG preconditioner (random
+    weights, their output scaled small: whatever the network predicts, the
+    FP64 defect correction stops at the same residual), two steps on a
+    uniform 128x64 grid against the FP64 oracle, to the bound of the other
+    FP32 paths.  Without a coarse hierarchy the iteration count grows with
+    the grid, hence the small uniform case; without pre-smoothing (with it,
+    the FCG(1) iteration stalled near 1e-5 on this case)."""
+    pre_smooth = 0
+    import dataclasses
+    from paper_2402_17337_gb300 import Solver, UNet, build
+    build.build()
+    c = dataclasses.replace(W.plunge_192x128(), name="uniform_128x64", x0=-4.0, x1=8.0, y0=-3.0, y1=3.0, nx=128,
+                            ny=64, steps=2, div_tol=1e-8)
+    o = oracle.Sim(**kwargs(c))
+    o.set_body(c.chord, c.tc, c.h, c.k, c.xc, c.yc)
+    o.set("u", c.initial_u(o.shape("u")))
+    rc, _ = o.step(2)
+    assert rc == 0
+    net = UNet((16, 16, 32, 32), seed=3)
+    g = Solver(**kwargs(c), precision=2, max_sweeps=20000)
+    g.set_body(c.chord, c.tc, c.h, c.k, c.xc, c.yc)
+    g.set("u", c.initial_u(g.shape("u")))
+    g.set_preconditioner(1, net, 1e-4, pre_smooth)
+    st = g.step(2)
+    assert st["res_p"] <= c.ptol and st["div_max"] <= c.div_tol * 1.001, st
+    errs = {n: rel(g.get(n), o.get(n)) for n in ("u", "v", "p")}
+    print(f"two-level U-Net preconditioner (pre-smoothing {pre_smooth}): {st['sweeps_p']} FCG iterations, "
+          f"errors {errs}")
+    assert max(errs.values()) <= MIXED_TOL, errs
+    g.close()
+    net.close()
+
+
+def test_preconditioner_rejects_invalid_use():
+    from paper_2402_17337_gb300 import IbmError, Solver, UNet, build
+    build.build()
+    c = W.batch_small(1)[0]
+    net = UNet((16, 16, 32, 32), seed=3)
+    for precision, kind, nn, pre in ((1, 1, net, 1), (2, 2, net, 1), (2, 1, None, 1), (2, 1, net, 2)):
+        s = Solver(**kwargs(c), precision=precision)
+        with pytest.raises(IbmError) as e:
+            s.set_preconditioner(kind, nn, 1.0, pre)
+        assert e.value.code == -1
+        s.close()
+    odd = dict(kwargs(W.small_cases()[1]))
+    s = Solver(**odd, precision=2)
+    with pytest.raises(IbmError):
+        s.set_preconditioner(1, net, 1.0, 1)
+    s.set_preconditioner(0)  # the V-cycle is always available
+    s.close()
+    net.close()
+
+
 def test_mg_full_size_steps_agree_with_sor_mixed_path():
     """Two steps of the 2048x1024 workload: divergence below 1e-8 and the same
     fields, to the solve tolerance, as the SOR mixed path."""
