@@ -296,7 +296,6 @@ __device__ __forceinline__ void sor32_tile_v4(const Geo32& g, const float* __res
   float ev[2][RPT][2];
   float rv[RDREG ? 2 : 1][RDREG ? RPT : 1][2], dv[RDREG ? 2 : 1][RDREG ? RPT : 1][2];
   float ce[2][2], cw[2][2], cN[RPT], cS[RPT];
-  unsigned live = 0u;  // bit (c, q, m): inside the domain (written back)
 #pragma unroll
   for (int m = 0; m < 2; ++m) {
     const int k = k0 + tx + 32 * m;
@@ -331,7 +330,6 @@ __device__ __forceinline__ void sor32_tile_v4(const Geo32& g, const float* __res
           sr[c][ly + 1][kk + 1] = rr;
           sd[c][ly + 1][kk + 1] = dd;
         }
-        if (in) live |= 1u << ((c * RPT + q) * 2 + m);
       }
   }
   __syncthreads();
@@ -385,8 +383,8 @@ __device__ __forceinline__ void sor32_tile_v4(const Geo32& g, const float* __res
 #pragma unroll
       for (int m = 0; m < 2; ++m) {
         const int kk = tx + 32 * m;
-        if (kk < HK || kk >= HK + TK) continue;
-        if (!(live >> ((c * RPT + q) * 2 + m) & 1u)) continue;
+        const int k = k0 + kk;
+        if (kk < HK || kk >= HK + TK || j < 0 || j >= ny || k < 0 || 2 * k + ((c + j) & 1) >= nx) continue;
         e_out[(size_t)(c * ny + j) * pk + (k0 + kk)] = ev[c][q][m];
       }
   }
@@ -422,7 +420,6 @@ __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __res
   float ev[2][RPT][2];
   float rv[RDREG ? 2 : 1][RDREG ? RPT : 1][2], dv[RDREG ? 2 : 1][RDREG ? RPT : 1][2];
   float cE[2][2], cW[2][2], cN[RPT], cS[RPT];  // cE[m][s]: coefficient of the cell at i = 2k + s
-  unsigned long long live = 0ull;              // bit (c, q, m): inside the domain (written back)
 #pragma unroll
   for (int m = 0; m < 2; ++m) {
     const int k = k0 + tx + 32 * m;
@@ -456,7 +453,6 @@ __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __res
           sr[c][ly + 1][kk + 1] = rr;
           sd[c][ly + 1][kk + 1] = dd;
         }
-        if (in) live |= 1ull << ((c * RPT + q) * 2 + m);
       }
   }
   __syncthreads();
@@ -517,8 +513,8 @@ __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __res
 #pragma unroll
       for (int m = 0; m < 2; ++m) {
         const int kk = tx + 32 * m;
-        if (kk < HK || kk >= HK + TK) continue;
-        if (!(live >> ((c * RPT + q) * 2 + m) & 1ull)) continue;
+        const int k = k0 + kk;
+        if (kk < HK || kk >= HK + TK || j < 0 || j >= ny || k < 0 || 2 * k + ((c + j) & 1) >= nx) continue;
         e_out[(size_t)(c * ny + j) * pk + (k0 + kk)] = ev[c][q][m];
       }
   }
