@@ -598,6 +598,7 @@ def main():
                                               f"{half} half-sweeps per launch, chosen by the autotuner)",
                     "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "launch_us": t_launch * 1e6,
+                    "shape": [rows, half, nyt, prof["sor_form"]], "shape_index": prof["sor_index"],
                     "fp32_tflops": SOR_FLOPS_PER_UPDATE * cfg.cells * sweeps_per_launch / t_launch / 1e12,
                     "fp32_peak_tflops": fp32_peak,
                     "peak_note": f"HBM {peaks['hbm_gbs']} GB/s ({peak_src}); algorithmic bytes: read e and r, "

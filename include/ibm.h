@@ -225,9 +225,10 @@ typedef struct {
                                 half-sweeps per launch, thread rows (0 if not tuned) */
   double sor_us_per_sweep;   /* its measured time per full sweep, microseconds */
   long long sweep_cells;     /* cells covered by the timed sweep launches, summed over launches */
-  int sor_form;              /* form of that sweep kernel (3, 4 or 5; 0 if not tuned) */
+  int sor_form;              /* form of that sweep kernel (3 to 7; 0 if not tuned) */
   long long ws_applied;      /* steps that evaluated the learned warm start */
   long long ws_kept;         /* of those, steps whose learned guess had the smaller residual and was kept */
+  int sor_index;             /* index of that shape for ibm_set_sor_shape (-1 if not tuned) */
 } ibm_profile;
 
 /* Autotuner of the FP32 sweep kernel (precision 1): times each tile shape on

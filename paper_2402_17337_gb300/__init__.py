@@ -52,7 +52,8 @@ class Profile(C.Structure):
     _fields_ = [("launches", C.c_longlong), ("sweep_launches", C.c_longlong), ("sweep_ms", C.c_double),
                 ("steps", C.c_longlong), ("poisson_sweeps", C.c_longlong), ("helm_sweeps", C.c_longlong),
                 ("sor_shape", C.c_int * 3), ("sor_us_per_sweep", C.c_double), ("sweep_cells", C.c_longlong),
-                ("sor_form", C.c_int), ("ws_applied", C.c_longlong), ("ws_kept", C.c_longlong)]
+                ("sor_form", C.c_int), ("ws_applied", C.c_longlong), ("ws_kept", C.c_longlong),
+                ("sor_index", C.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

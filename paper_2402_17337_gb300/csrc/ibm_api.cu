@@ -1846,6 +1846,7 @@ int ibm_get_profile(const ibm_ctx* c, ibm_profile* out) {
   *out = c->prof;
   out->sor_shape[0] = out->sor_shape[1] = out->sor_shape[2] = 0;
   out->sor_us_per_sweep = c->sor_us;
+  out->sor_index = c->sor_cfg;
   if (c->sor_cfg >= 0)
     sor32_describe(c->sor_cfg, &out->sor_shape[0], &out->sor_shape[1], &out->sor_shape[2], &out->sor_form);
   return IBM_OK;
@@ -2051,6 +2052,7 @@ int ibm_batch_set_profiling(ibm_batch* B, int on) {
 int ibm_batch_get_profile(const ibm_batch* B, ibm_profile* out) {
   if (!B || !out) return fail(IBM_E_INVAL, "null argument");
   *out = B->prof;
+  out->sor_index = B->cfg;
   if (B->cfg >= 0) sor32_describe(B->cfg, &out->sor_shape[0], &out->sor_shape[1], &out->sor_shape[2], &out->sor_form);
   out->sor_us_per_sweep = B->sor_us;
   for (ibm_ctx* c : B->cs) {

@@ -630,7 +630,7 @@ const Sor32Config kConfigs[] = {
     shape<Cfg<64, 16, 16, 6, 1>>(), shape<Cfg<24, 4, 8, 6, 3>>(),   shape<Cfg<32, 8, 8, 7, 2>>(),
     shape<Cfg<48, 8, 16, 7, 1>>(),  shape<Cfg<24, 4, 8, 7, 2>>(),   shape<Cfg<48, 8, 8, 6, 2>>(),
     shape<Cfg<48, 8, 8, 7, 1>>(),   shape<Cfg<40, 12, 8, 6, 2>>(),  shape<Cfg<80, 16, 16, 6, 1>>(),
-    shape<Cfg<96, 16, 16, 6, 1>>(),
+    shape<Cfg<96, 16, 16, 6, 1>>(), shape<Cfg<64, 16, 16, 7, 1>>(), shape<Cfg<80, 16, 16, 7, 1>>(),
 };
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
