@@ -53,9 +53,8 @@ MG_BYTES_PER_CELL_ITER = 104
 # unchanged kernel (profiles/k_sor32_rb_*.md), by workload and tile shape (rows, half-sweeps,
 # thread rows, form); cold-cache captures
 SOR32_TRAFFIC = {
-    ("plunge_2048x1024", (64, 16, 16, 4)): 25.216e6,
-    ("plunge_2048x1024", (80, 16, 16, 6)): 25.228e6,
-    ("plunge_4096x2048", (32, 8, 16, 4)): 115.864e6,
+    ("plunge_2048x1024", (80, 16, 16, 7)): 25.221e6,
+    ("plunge_4096x2048", (32, 8, 8, 7)): 117.465e6,
 }
 WORKLOADS = ("plunge_2048x1024", "plunge_4096x2048", "unet_1024x512", "batch64")
 METRIC = "cell-steps/s at div<1e-8: learned warm-start+mixed vs plain FP64, one GB300"
