@@ -55,6 +55,7 @@ MG_BYTES_PER_CELL_ITER = 104
 SOR32_TRAFFIC = {
     ("plunge_2048x1024", (80, 16, 16, 7)): 25.221e6,
     ("plunge_4096x2048", (32, 8, 8, 7)): 117.465e6,
+    ("plunge_4096x2048", (64, 16, 16, 7)): 115.556e6,
 }
 WORKLOADS = ("plunge_2048x1024", "plunge_4096x2048", "unet_1024x512", "batch64")
 METRIC = "cell-steps/s at div<1e-8: learned warm-start+mixed vs plain FP64, one GB300"
@@ -317,7 +318,10 @@ def run_batch(args):
             s = ibm.Solver.from_config(c, precision=1)
             s.set("u", c.initial_u(s.shape("u")))
             ss.append(s)
-        return ss, ibm.Batch(ss)
+        b = ibm.Batch(ss)
+        if args.sor_shape >= 0:
+            b.set_sor_shape(args.sor_shape)
+        return ss, b
 
     ss, batch = make()
     for _ in range(args.warmup):
@@ -354,6 +358,7 @@ def run_batch(args):
                                           f"case, tile {rows} rows x 128 cells, {half} half-sweeps per launch)",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                 "traffic": None, "launch_us": 1e3 * prof["sweep_ms"] / prof["sweep_launches"],
+                "shape": list(prof["sor_shape"]) + [prof["sor_form"]], "shape_index": prof["sor_index"],
                 "peak_note": f"HBM {peaks['hbm_gbs']} GB/s ({peak_src}); algorithmic bytes {SOR32_BYTES_PER_CELL_LAUNCH}"
                              f" B per covered cell per launch, summed over the timed sweep launches (cases leave "
                              f"the launches as they converge)"}
