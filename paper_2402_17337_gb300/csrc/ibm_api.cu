@@ -867,12 +867,12 @@ int tune_sor32(ibm_ctx* c) {
   for (int cfg = 0; cfg < sor32_num_configs(); ++cfg) {
     const int reps = 8;
     for (int w = 0; w < 2; ++w) {
-      launch_sor32(c->stream, cfg, c->geo32, c->e32, c->e32b, c->r32, c->invd32, omega, 1);
+      launch_sor32(c->stream, cfg, c->geo32, c->e32, c->e32b, c->r32, c->invd32, omega, 1, 1);
       std::swap(c->e32, c->e32b);
     }
     CUDA_TRY(cudaEventRecord(a, c->stream));
     for (int l = 0; l < reps; ++l) {
-      launch_sor32(c->stream, cfg, c->geo32, c->e32, c->e32b, c->r32, c->invd32, omega, l == 0 ? 1 : 0);
+      launch_sor32(c->stream, cfg, c->geo32, c->e32, c->e32b, c->r32, c->invd32, omega, l == 0 ? 1 : 0, 1);
       std::swap(c->e32, c->e32b);
     }
     CUDA_TRY(cudaEventRecord(b, c->stream));
@@ -1027,7 +1027,7 @@ int solve_poisson_mixed(ibm_ctx* c, double tol, int maxs, int* sweeps, double* r
     if (c->profiling) CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
     for (int l = 0; l < inner / K2; ++l) {
       // read e32, write e32b, swap: the final correction ends in e32
-      launch_sor32(c->stream, cfg, c->geo32, c->e32, c->e32b, c->r32, c->invd32, omega, l == 0 ? 1 : 0);
+      launch_sor32(c->stream, cfg, c->geo32, c->e32, c->e32b, c->r32, c->invd32, omega, l == 0 ? 1 : 0, 1);
       std::swap(c->e32, c->e32b);
       c->prof.launches += 1;
       if (c->profiling) pending += 1;

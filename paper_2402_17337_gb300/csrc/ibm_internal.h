@@ -211,7 +211,9 @@ int sor32_half_sweeps(int cfg);  // half-sweeps per launch of tile shape cfg (ev
 void sor32_describe(int cfg, int* rows_per_tile, int* half_sweeps, int* thread_rows, int* form);
 void launch_dc_residual(cudaStream_t s, const Geo& g, int pk, const double* phi_in, double* phi_out,
                         const float* e, const double* b, float* r32, int add_e, unsigned long long* res_bits);
+// pdl: launch as a programmatic dependent of the previous sweep launch on
+// the stream (consecutive sweep launches outside graph capture)
 void launch_sor32(cudaStream_t s, int cfg, const Geo32& g, const float* e_in, float* e_out, const float* r,
-                  const float* invd, float omega, int zero_init);
+                  const float* invd, float omega, int zero_init, int pdl = 0);
 
 }  // namespace ibm

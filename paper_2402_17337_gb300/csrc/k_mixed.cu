@@ -548,6 +548,12 @@ __global__ void __launch_bounds__(32 * C::NY, C::MINB)
     k_sor32_rb(const Geo32 g, const float* __restrict__ e_in, float* __restrict__ e_out, const float* __restrict__ r,
                const float* __restrict__ invd, float omega, int zero_init) {
   extern __shared__ float smem[];
+  // programmatic dependent launch (a no-op unless the launch asks for it):
+  // the next sweep launch may be scheduled once every CTA of this one is
+  // resident, and this launch touches e only after the previous launch has
+  // completed and its writes are visible
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   tile<C>(g, e_in, e_out, r, invd, omega, zero_init, blockIdx.x, blockIdx.y, smem);
 }
 
@@ -575,7 +581,7 @@ __global__ void __launch_bounds__(32 * C::NY, C::MINB)
 // Tile shapes the autotuner chooses from.
 struct Sor32Config {
   int TY, K, NY, V;
-  void (*launch)(cudaStream_t, const Geo32&, const float*, float*, const float*, const float*, float, int);
+  void (*launch)(cudaStream_t, const Geo32&, const float*, float*, const float*, const float*, float, int, int);
   void (*launch_batch)(cudaStream_t, const Sor32Case*, int, int, int);
   cudaError_t (*prepare)();
   void (*tiles)(const Geo32&, int*, int*);
@@ -592,7 +598,7 @@ cudaError_t prepare_shape() {
 
 template <class C>
 void launch_shape(cudaStream_t s, const Geo32& g, const float* e_in, float* e_out, const float* r, const float* invd,
-                  float omega, int zero_init) {
+                  float omega, int zero_init, int pdl) {
   static bool attr = false;
   if (!attr) {
     prepare_shape<C>();
@@ -600,7 +606,21 @@ void launch_shape(cudaStream_t s, const Geo32& g, const float* e_in, float* e_ou
   }
   const int ncol = (g.nx + 1) / 2;
   dim3 grd((ncol + C::TK - 1) / C::TK, (g.ny + C::TY - 1) / C::TY);
-  k_sor32_rb<C><<<grd, dim3(32, C::NY), C::smem, s>>>(g, e_in, e_out, r, invd, omega, zero_init);
+  if (!pdl) {
+    k_sor32_rb<C><<<grd, dim3(32, C::NY), C::smem, s>>>(g, e_in, e_out, r, invd, omega, zero_init);
+    return;
+  }
+  cudaLaunchConfig_t lc{};
+  lc.gridDim = grd;
+  lc.blockDim = dim3(32, C::NY);
+  lc.dynamicSmemBytes = C::smem;
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  cudaLaunchKernelEx(&lc, k_sor32_rb<C>, g, e_in, e_out, r, invd, omega, zero_init);
 }
 
 template <class C>
@@ -658,8 +678,8 @@ void launch_dc_residual(cudaStream_t s, const Geo& g, int pk, const double* phi_
 }
 
 void launch_sor32(cudaStream_t s, int cfg, const Geo32& g, const float* e_in, float* e_out, const float* r,
-                  const float* invd, float omega, int zero_init) {
-  kConfigs[cfg].launch(s, g, e_in, e_out, r, invd, omega, zero_init);
+                  const float* invd, float omega, int zero_init, int pdl) {
+  kConfigs[cfg].launch(s, g, e_in, e_out, r, invd, omega, zero_init, pdl);
 }
 
 void sor32_tiles(int cfg, const Geo32& g, int* tiles_x, int* tiles_y) { kConfigs[cfg].tiles(g, tiles_x, tiles_y); }
