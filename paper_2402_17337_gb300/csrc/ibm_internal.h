@@ -211,8 +211,10 @@ int sor32_half_sweeps(int cfg);  // half-sweeps per launch of tile shape cfg (ev
 void sor32_describe(int cfg, int* rows_per_tile, int* half_sweeps, int* thread_rows, int* form);
 void launch_dc_residual(cudaStream_t s, const Geo& g, int pk, const double* phi_in, double* phi_out,
                         const float* e, const double* b, float* r32, int add_e, unsigned long long* res_bits);
-// pdl: launch as a programmatic dependent of the previous sweep launch on
-// the stream (consecutive sweep launches outside graph capture)
+// pdl: launch as a programmatic dependent of the previous kernel on the
+// stream (consecutive sweep launches outside graph capture).  With
+// zero_init = 0 the previous kernel must be a sweep launch of the same run:
+// forms 6 and 7 then read r and 1/d before waiting for it.
 void launch_sor32(cudaStream_t s, int cfg, const Geo32& g, const float* e_in, float* e_out, const float* r,
                   const float* invd, float omega, int zero_init, int pdl = 0);
 

@@ -398,6 +398,13 @@ __device__ __forceinline__ void sor32_tile_v4(const Geo32& g, const float* __res
 // is fixed per warp and half-sweep (the start row parity), so each half-sweep
 // is compiled for both start parities and picked by a warp-uniform branch.
 // Same arithmetic in the same order as the other forms: identical iterates.
+// waits until the previous grid on the stream has completed and its writes
+// are visible (a no-op unless launched as a programmatic dependent)
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// lets the next programmatic dependent launch start once every CTA of this
+// grid has released it
+__device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <int TY, int K, int NY, bool RDREG>
 __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __restrict__ e_in, float* __restrict__ e_out,
                                               const float* __restrict__ r, const float* __restrict__ invd,
@@ -429,6 +436,19 @@ __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __res
     cW[m][0] = ok ? g.cW0[k] : 0.f;
     cW[m][1] = ok ? g.cW1[k] : 0.f;
   }
+  // Under a programmatic dependent launch a CTA waits for the previous
+  // kernel (griddep_wait) before it releases the next launch
+  // (griddep_release), so a launch starts only when every CTA of the launch
+  // before it is past its wait: a launch that follows a sweep launch
+  // (zero_init = 0) can load 1/d and r, which only kernels before the
+  // previous launch wrote, while the previous launch is still running.  The
+  // loads go to L2 (ld.global.cg): no line an earlier kernel left in this
+  // SM's L1 can answer them.  The first launch of a run follows the kernel
+  // that wrote r and waits first.
+  if (zero_init) {
+    griddep_wait();
+    griddep_release();
+  }
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     const int ly = ly0 + q, j = j0 + ly;
@@ -442,10 +462,7 @@ __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __res
         const int kk = tx + 32 * m, k = k0 + kk, i = 2 * k + ((c + j) & 1);
         const bool in = rowok && k >= 0 && i < nx;
         const size_t o = (size_t)(c * ny + j) * pk + k;
-        const float x = (in && !zero_init) ? e_in[o] : 0.f;
-        const float rr = in ? r[o] : 0.f, dd = in ? invd[o] : 0.f;
-        ev[c][q][m] = x;
-        se[c][ly + 1][kk + 1] = x;
+        const float rr = in ? __ldcg(r + o) : 0.f, dd = in ? __ldcg(invd + o) : 0.f;
         if constexpr (RDREG) {
           rv[c][q][m] = rr;
           dv[c][q][m] = dd;
@@ -453,6 +470,28 @@ __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __res
           sr[c][ly + 1][kk + 1] = rr;
           sd[c][ly + 1][kk + 1] = dd;
         }
+      }
+  }
+  if (!zero_init) {
+    griddep_wait();
+    griddep_release();
+  }
+  // e of this thread's cells, addressed from one row pointer per colour
+  const float* e_row[2] = {e_in + ((size_t)(j0 + ly0) * pk + (k0 + tx)),
+                           e_in + ((size_t)(ny + j0 + ly0) * pk + (k0 + tx))};
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int ly = ly0 + q, j = j0 + ly;
+    const bool rowok = j >= 0 && j < ny;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int kk = tx + 32 * m, k = k0 + kk, i = 2 * k + ((c + j) & 1);
+        const bool in = rowok && k >= 0 && i < nx;
+        const float x = (in && !zero_init) ? __ldcg(e_row[c] + ((size_t)q * pk + 32 * m)) : 0.f;
+        ev[c][q][m] = x;
+        se[c][ly + 1][kk + 1] = x;
       }
   }
   __syncthreads();
@@ -549,11 +588,13 @@ __global__ void __launch_bounds__(32 * C::NY, C::MINB)
                const float* __restrict__ invd, float omega, int zero_init) {
   extern __shared__ float smem[];
   // programmatic dependent launch (a no-op unless the launch asks for it):
-  // the next sweep launch may be scheduled once every CTA of this one is
-  // resident, and this launch touches e only after the previous launch has
-  // completed and its writes are visible
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // this launch reads what the previous kernel wrote only after that kernel
+  // has completed and its writes are visible, and then lets the next sweep
+  // launch start (forms 6 and 7 do both inside, after loading r and 1/d)
+  if constexpr (C::V < 6) {
+    griddep_wait();
+    griddep_release();
+  }
   tile<C>(g, e_in, e_out, r, invd, omega, zero_init, blockIdx.x, blockIdx.y, smem);
 }
 
