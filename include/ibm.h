@@ -310,6 +310,24 @@ int ibm_set_warmstart(ibm_ctx* ctx, int mode, ibm_unet* net, double target_scale
  * phi^n).  The learned form predicts the change from the base guess. */
 int ibm_set_warmstart_base(ibm_ctx* ctx, int base);
 
+/* Checkpoint and resume.  A state holds everything a step carries to the
+ * next: u, v, p, the last pressure increment (the next solve's start), the
+ * AB2 convection history, the momentum inside the body (the added-mass term
+ * of the force), the C_l/C_d histories, the step count, the adapted inner
+ * run lengths of the FP32 solves and, when the warm start extrapolates in
+ * time, the increment before, and the FP32 sweep shape chosen by the
+ * autotuner (its sweeps per launch round the inner runs).  ibm_state_bytes gives the size of the
+ * context's state; ibm_save_state copies it into the caller's host buffer
+ * of at least that size (waits for the stream).  ibm_load_state restores
+ * one into a context created with the same grid, Re and dt, with the same
+ * body set (and the same warm-start base); stepping on from it repeats the
+ * saved run's steps bit for bit.  The layout is the library's own (native
+ * byte order).  Errors: IBM_E_INVAL (small buffer, another format, grid,
+ * dt, Re or body), IBM_E_CUDA. */
+int ibm_state_bytes(const ibm_ctx* ctx, size_t* bytes);
+int ibm_save_state(const ibm_ctx* ctx, void* host, size_t bytes);
+int ibm_load_state(ibm_ctx* ctx, const void* host, size_t bytes);
+
 /* Preconditioner of the FCG iteration of precision 2 (the multigrid
  * variant; a network used as preconditioner rather than warm start).
  * kind 0: one V(2,2)-cycle (default).  kind 1: a two-level cycle whose

@@ -100,6 +100,9 @@ def lib():
             L.ibm_set_warmstart.argtypes = [_VP, C.c_int, _VP, C.c_double]
             L.ibm_set_warmstart_base.argtypes = [_VP, C.c_int]
             L.ibm_set_preconditioner.argtypes = [_VP, C.c_int, _VP, C.c_double, C.c_int]
+            L.ibm_state_bytes.argtypes = [_VP, C.POINTER(C.c_size_t)]
+            L.ibm_save_state.argtypes = [_VP, _VP, C.c_size_t]
+            L.ibm_load_state.argtypes = [_VP, _VP, C.c_size_t]
             L.ibm_get_sample.argtypes = [_VP, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_int),
                                          C.POINTER(C.c_int)]
             L.ibm_tune_omega.argtypes = [_VP, C.c_int, _D]
@@ -269,6 +272,19 @@ class Solver:
         """0: previous increment; 1: learned (U-Net net); 2: previous increment + samples."""
         self._ws_net = net  # keep the network alive while the context uses it
         _check(lib().ibm_set_warmstart(self._h, mode, net._h if net is not None else None, target_scale))
+
+    def save_state(self):
+        """The context's state (bytes) for load_state: fields, histories, step count."""
+        n = C.c_size_t(0)
+        _check(lib().ibm_state_bytes(self._h, C.byref(n)))
+        buf = np.zeros(n.value, np.uint8)
+        _check(lib().ibm_save_state(self._h, buf.ctypes.data, n.value))
+        return buf.tobytes()
+
+    def load_state(self, state):
+        """Restores a state from save_state (same grid, Re, dt and body)."""
+        buf = np.frombuffer(state, np.uint8)
+        _check(lib().ibm_load_state(self._h, buf.ctypes.data, buf.size))
 
     def set_preconditioner(self, kind, net=None, target_scale=1.0, pre_smooth=1):
         """Precision 2: 0 V-cycle; 1 two-level cycle with the U-Net net as coarse level."""

@@ -1878,6 +1878,121 @@ int ibm_set_warmstart(ibm_ctx* c, int mode, ibm_unet* net, double target_scale) 
   return IBM_OK;
 }
 
+namespace {
+
+// Checkpoint layout: this header, then the pitched FP64 arrays u, v, p, phi
+// (the last pressure increment, the next solve's start), H^n of u and v
+// (AB2 history), the C_l and C_d histories (n values each) and, when the
+// warm start extrapolates in time, the increment of the step before.
+struct StateHeader {
+  char magic[8];
+  int32_t version, nx, ny, pitch;
+  int64_t nelem;
+  int32_t n, has_body, m_inner, mg_cycles, has_phi_prev, precision;
+  int32_t sor_cfg, reserved;  // FP32 sweep shape (its sweeps per launch round the inner runs)
+  double body[6];  // chord, thickness ratio, h, k, x and y of the centre
+  double dt, Re;
+  double S_prev[2];  // momentum inside the body at step n (added-mass term of the force)
+};
+constexpr char kStateMagic[8] = {'I', 'B', 'M', 'S', 'T', 'A', 'T', 'E'};
+
+size_t state_bytes(const ibm_ctx* c) {
+  const size_t fields = 6 + (c->phi_prev ? 1 : 0);
+  return sizeof(StateHeader) + fields * c->nelem * sizeof(double) + 2 * (size_t)c->n * sizeof(double);
+}
+
+}  // namespace
+
+int ibm_state_bytes(const ibm_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return fail(IBM_E_INVAL, "null argument");
+  *bytes = state_bytes(c);
+  return IBM_OK;
+}
+
+int ibm_save_state(const ibm_ctx* c, void* host, size_t bytes) {
+  if (!c || !host) return fail(IBM_E_INVAL, "null argument");
+  if (bytes < state_bytes(c)) return fail(IBM_E_INVAL, "state buffer too small: %zu < %zu", bytes, state_bytes(c));
+  StateHeader h{};
+  std::memcpy(h.magic, kStateMagic, 8);
+  h.version = 1;
+  h.nx = c->nx;
+  h.ny = c->ny;
+  h.pitch = c->pitch;
+  h.nelem = (int64_t)c->nelem;
+  h.n = c->n;
+  h.has_body = c->has_body ? 1 : 0;
+  h.m_inner = c->m_inner;
+  h.mg_cycles = c->mg_cycles;
+  h.has_phi_prev = c->phi_prev ? 1 : 0;
+  h.precision = c->P.precision;
+  h.sor_cfg = c->sor_cfg;
+  const double body[6] = {c->chord, c->tc, c->h, c->k, c->xb, c->yb0};
+  std::memcpy(h.body, body, sizeof body);
+  h.dt = c->P.dt;
+  h.Re = c->P.Re;
+  CUDA_TRY(cudaMemcpyAsync(&c->sc_host->S_prev, &c->sc->S_prev, sizeof(h.S_prev), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  std::memcpy(h.S_prev, c->sc_host->S_prev, sizeof(h.S_prev));
+  unsigned char* out = static_cast<unsigned char*>(host);
+  std::memcpy(out, &h, sizeof h);
+  out += sizeof h;
+  const double* fields[7] = {c->u, c->v, c->p, c->phi, c->Huo, c->Hvo, c->phi_prev};
+  const size_t fb = c->nelem * sizeof(double);
+  for (int f = 0; f < 6 + h.has_phi_prev; ++f, out += fb)
+    CUDA_TRY(cudaMemcpyAsync(out, fields[f], fb, cudaMemcpyDeviceToHost, c->stream));
+  if (c->n > 0) {
+    CUDA_TRY(cudaMemcpyAsync(out, c->cl_d, (size_t)c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    out += (size_t)c->n * sizeof(double);
+    CUDA_TRY(cudaMemcpyAsync(out, c->cd_d, (size_t)c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return IBM_OK;
+}
+
+int ibm_load_state(ibm_ctx* c, const void* host, size_t bytes) {
+  if (!c || !host) return fail(IBM_E_INVAL, "null argument");
+  if (bytes < sizeof(StateHeader)) return fail(IBM_E_INVAL, "state buffer too small for its header");
+  StateHeader h;
+  std::memcpy(&h, host, sizeof h);
+  if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1) return fail(IBM_E_INVAL, "not a state of this format");
+  if (h.nx != c->nx || h.ny != c->ny || h.pitch != c->pitch || h.nelem != (int64_t)c->nelem)
+    return fail(IBM_E_INVAL, "state of a %dx%d grid, context %dx%d", h.nx, h.ny, c->nx, c->ny);
+  if (h.dt != c->P.dt || h.Re != c->P.Re) return fail(IBM_E_INVAL, "state taken with another dt or Re");
+  if (h.n < 0) return fail(IBM_E_INVAL, "bad step count in the state");
+  const double body[6] = {c->chord, c->tc, c->h, c->k, c->xb, c->yb0};
+  if (h.has_body != (c->has_body ? 1 : 0) || (h.has_body && std::memcmp(h.body, body, sizeof body) != 0))
+    return fail(IBM_E_INVAL, "the context's body differs from the state's (set the same body first)");
+  if ((c->phi_prev != nullptr) && !h.has_phi_prev)
+    return fail(IBM_E_INVAL, "the context extrapolates the warm start in time but the state has no history for it");
+  const size_t fb = c->nelem * sizeof(double);
+  const size_t need = sizeof h + (6 + (size_t)h.has_phi_prev) * fb + 2 * (size_t)h.n * sizeof(double);
+  if (bytes < need) return fail(IBM_E_INVAL, "state buffer too small: %zu < %zu", bytes, need);
+  int rc = ensure_history(c, h.n > 0 ? h.n : 1);
+  if (rc) return rc;
+  const unsigned char* in = static_cast<const unsigned char*>(host) + sizeof h;
+  double* fields[6] = {c->u, c->v, c->p, c->phi, c->Huo, c->Hvo};
+  for (int f = 0; f < 6; ++f, in += fb) CUDA_TRY(cudaMemcpyAsync(fields[f], in, fb, cudaMemcpyHostToDevice, c->stream));
+  if (h.has_phi_prev) {
+    if (c->phi_prev) CUDA_TRY(cudaMemcpyAsync(c->phi_prev, in, fb, cudaMemcpyHostToDevice, c->stream));
+    in += fb;
+  }
+  if (h.n > 0) {
+    CUDA_TRY(cudaMemcpyAsync(c->cl_d, in, (size_t)h.n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    in += (size_t)h.n * sizeof(double);
+    CUDA_TRY(cudaMemcpyAsync(c->cd_d, in, (size_t)h.n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  }
+  std::memcpy(c->sc_host->S_prev, h.S_prev, sizeof(h.S_prev));
+  CUDA_TRY(cudaMemcpyAsync(&c->sc->S_prev, c->sc_host->S_prev, sizeof(h.S_prev), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (h.sor_cfg >= sor32_num_configs()) return fail(IBM_E_INVAL, "unknown sweep shape in the state");
+  c->n = h.n;
+  c->m_inner = h.m_inner;
+  c->mg_cycles = h.mg_cycles;
+  if (h.sor_cfg >= 0) c->sor_cfg = h.sor_cfg;
+  c->has_sample = false;
+  return IBM_OK;
+}
+
 int ibm_set_preconditioner(ibm_ctx* c, int kind, ibm_unet* net, double target_scale, int pre_smooth) {
   if (!c) return fail(IBM_E_INVAL, "null context");
   if (c->P.precision != 2) return fail(IBM_E_INVAL, "the preconditioner applies to precision 2 (FCG) only");
