@@ -68,33 +68,79 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
-            L.or_build_axis.argtypes = [C.c_double] * 4 + [C.c_int, C.c_double, _D]
-            L.or_create.argtypes = [C.POINTER(Params)]
-            L.or_create.restype = C.c_void_p
-            L.or_destroy.argtypes = [C.c_void_p]
-            L.or_set_threads.argtypes = [C.c_void_p, C.c_int]
-            L.or_get_grid.argtypes = [C.c_void_p, _D, _D]
-            L.or_set_body.argtypes = [C.c_void_p] + [C.c_double] * 6
-            L.or_step.argtypes = [C.c_void_p, C.c_int, C.POINTER(Stats)]
-            L.or_get.argtypes = [C.c_void_p, C.c_int, _D]
-            L.or_set.argtypes = [C.c_void_p, C.c_int, _D]
-            L.or_get_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
-            L.or_forces.argtypes = [C.c_void_p, _D, _D, C.c_int, C.POINTER(C.c_int)]
-            L.or_classify.argtypes = [C.c_void_p, C.c_double]
-            L.or_get_flags.argtypes = [C.c_void_p, C.c_int, _U8, _U8, _D]
-            for name in ("or_lap_p", "or_lap_u", "or_lap_v"):
-                getattr(L, name).argtypes = [C.c_void_p, _D, _D]
-            L.or_conv.argtypes = [C.c_void_p, _D, _D, _D, _D]
-            L.or_grad.argtypes = [C.c_void_p, _D, _D, _D]
-            L.or_div.argtypes = [C.c_void_p, _D, _D, _D]
-            L.or_poisson.argtypes = [C.c_void_p, _D, _D, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
-                                     C.POINTER(C.c_int), C.POINTER(C.c_double)]
-            L.or_helm_solve.argtypes = [C.c_void_p, C.c_int, _D, _D, C.c_double, C.c_double,
-                                        C.POINTER(C.c_int), C.POINTER(C.c_double)]
-            L.or_clear_flags.argtypes = [C.c_void_p]
-            _lib = L
+            _lib = _configure(C.CDLL(build()))
     return _lib
+
+
+def _configure(L):
+    """Declares the argument types of the oracle's C entry points on L."""
+    L.or_build_axis.argtypes = [C.c_double] * 4 + [C.c_int, C.c_double, _D]
+    L.or_create.argtypes = [C.POINTER(Params)]
+    L.or_create.restype = C.c_void_p
+    L.or_destroy.argtypes = [C.c_void_p]
+    L.or_set_threads.argtypes = [C.c_void_p, C.c_int]
+    L.or_get_grid.argtypes = [C.c_void_p, _D, _D]
+    L.or_set_body.argtypes = [C.c_void_p] + [C.c_double] * 6
+    L.or_step.argtypes = [C.c_void_p, C.c_int, C.POINTER(Stats)]
+    L.or_get.argtypes = [C.c_void_p, C.c_int, _D]
+    L.or_set.argtypes = [C.c_void_p, C.c_int, _D]
+    L.or_get_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
+    L.or_forces.argtypes = [C.c_void_p, _D, _D, C.c_int, C.POINTER(C.c_int)]
+    L.or_classify.argtypes = [C.c_void_p, C.c_double]
+    L.or_get_flags.argtypes = [C.c_void_p, C.c_int, _U8, _U8, _D]
+    for name in ("or_lap_p", "or_lap_u", "or_lap_v"):
+        getattr(L, name).argtypes = [C.c_void_p, _D, _D]
+    L.or_conv.argtypes = [C.c_void_p, _D, _D, _D, _D]
+    L.or_grad.argtypes = [C.c_void_p, _D, _D, _D]
+    L.or_div.argtypes = [C.c_void_p, _D, _D, _D]
+    L.or_poisson.argtypes = [C.c_void_p, _D, _D, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
+                             C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    L.or_helm_solve.argtypes = [C.c_void_p, C.c_int, _D, _D, C.c_double, C.c_double,
+                                C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    L.or_clear_flags.argtypes = [C.c_void_p]
+    return L
+
+
+def build_variant(name, replacements):
+    """Compiles a copy of the oracle with textual replacements (each `old`
+    must occur exactly once) into its own library; for tests that plant a
+    mistake in the oracle and check that a pin catches it."""
+    with open(_SRC) as fh:
+        src = fh.read()
+    for old, new in replacements:
+        if src.count(old) != 1:
+            raise ValueError(f"{name}: {old!r} occurs {src.count(old)} times")
+        src = src.replace(old, new)
+    d = os.path.join(_BUILD, "variants")
+    os.makedirs(d, exist_ok=True)
+    c_path = os.path.join(d, f"{name}.c")
+    so_path = os.path.join(d, f"lib{name}.so")
+    with open(c_path, "w") as fh:
+        fh.write(src)
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+                    "-o", so_path, c_path, "-lm"], check=True)
+    return so_path
+
+
+class use_library:
+    """Context manager: oracle calls made inside go to the library at `path`
+    (a variant from build_variant)."""
+
+    def __init__(self, path):
+        self.L = _configure(C.CDLL(path))
+
+    def __enter__(self):
+        global _lib
+        lib()
+        with _lock:
+            self.saved, _lib = _lib, self.L
+        return self.L
+
+    def __exit__(self, *exc):
+        global _lib
+        with _lock:
+            _lib = self.saved
+        return False
 
 
 def _dp(a):
@@ -125,15 +171,16 @@ class Sim:
                    prtol, htol, check_p, check_h, max_sweeps, omega_p, omega_h)
         self.P = P
         self.nx, self.ny = nx, ny
-        self._h = lib().or_create(C.byref(P))
+        self._L = lib()
+        self._h = self._L.or_create(C.byref(P))
         if not self._h:
             raise ValueError("or_create rejected the parameters")
-        lib().or_set_threads(self._h, threads)
+        self._L.or_set_threads(self._h, threads)
 
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().or_destroy(h)
+            self._L.or_destroy(h)
             self._h = None
 
     # shapes in canonical (row = j) layout
@@ -148,40 +195,40 @@ class Sim:
     def grid(self):
         xf = np.zeros(self.nx + 1)
         yf = np.zeros(self.ny + 1)
-        lib().or_get_grid(self._h, _dp(xf), _dp(yf))
+        self._L.or_get_grid(self._h, _dp(xf), _dp(yf))
         return xf, yf
 
     def set_body(self, chord=1.0, tc=0.12, h=0.0, k=0.0, xc=0.0, yc=0.0):
-        rc = lib().or_set_body(self._h, chord, tc, h, k, xc, yc)
+        rc = self._L.or_set_body(self._h, chord, tc, h, k, xc, yc)
         if rc:
             raise ValueError("or_set_body failed")
 
     def step(self, n=1):
         st = Stats()
-        rc = lib().or_step(self._h, n, C.byref(st))
+        rc = self._L.or_step(self._h, n, C.byref(st))
         return rc, st.as_dict()
 
     def get(self, name):
         out = np.zeros(self.shape(name))
-        lib().or_get(self._h, FIELDS[name], _dp(out))
+        self._L.or_get(self._h, FIELDS[name], _dp(out))
         return out
 
     def set(self, name, arr):
         a = np.ascontiguousarray(arr, dtype=np.float64).reshape(self.shape(name))
-        rc = lib().or_set(self._h, FIELDS[name], _dp(a))
+        rc = self._L.or_set(self._h, FIELDS[name], _dp(a))
         if rc:
             raise ValueError("or_set failed")
 
     def forces(self):
         n = C.c_int(0)
-        lib().or_forces(self._h, None, None, 0, C.byref(n))
+        self._L.or_forces(self._h, None, None, 0, C.byref(n))
         cl = np.zeros(max(n.value, 1))
         cd = np.zeros(max(n.value, 1))
-        lib().or_forces(self._h, _dp(cl), _dp(cd), n.value, C.byref(n))
+        self._L.or_forces(self._h, _dp(cl), _dp(cd), n.value, C.byref(n))
         return cl[:n.value], cd[:n.value]
 
     def classify(self, t):
-        if lib().or_classify(self._h, t):
+        if self._L.or_classify(self._h, t):
             raise ValueError("no body")
 
     def flags(self, grid):
@@ -189,30 +236,30 @@ class Sim:
         shp = self.shape("u" if grid == 0 else ("v" if grid == 1 else "p"))
         fl = np.zeros(shp, np.uint8)
         if grid == 2:
-            lib().or_get_flags(self._h, 2, fl.ctypes.data_as(_U8), None, None)
+            self._L.or_get_flags(self._h, 2, fl.ctypes.data_as(_U8), None, None)
             return fl
         dr = np.zeros(shp, np.uint8)
         al = np.zeros(shp)
-        lib().or_get_flags(self._h, grid, fl.ctypes.data_as(_U8), dr.ctypes.data_as(_U8), _dp(al))
+        self._L.or_get_flags(self._h, grid, fl.ctypes.data_as(_U8), dr.ctypes.data_as(_U8), _dp(al))
         return fl, dr, al
 
     # operators
     def lap_p(self, f):
         f = np.ascontiguousarray(f, np.float64)
         out = np.zeros(self.shape("p"))
-        lib().or_lap_p(self._h, _dp(f), _dp(out))
+        self._L.or_lap_p(self._h, _dp(f), _dp(out))
         return out
 
     def lap_u(self, u):
         u = np.ascontiguousarray(u, np.float64)
         out = np.zeros(self.shape("u"))
-        lib().or_lap_u(self._h, _dp(u), _dp(out))
+        self._L.or_lap_u(self._h, _dp(u), _dp(out))
         return out
 
     def lap_v(self, v):
         v = np.ascontiguousarray(v, np.float64)
         out = np.zeros(self.shape("v"))
-        lib().or_lap_v(self._h, _dp(v), _dp(out))
+        self._L.or_lap_v(self._h, _dp(v), _dp(out))
         return out
 
     def conv(self, u, v):
@@ -220,21 +267,21 @@ class Sim:
         v = np.ascontiguousarray(v, np.float64)
         Hu = np.zeros(self.shape("u"))
         Hv = np.zeros(self.shape("v"))
-        lib().or_conv(self._h, _dp(u), _dp(v), _dp(Hu), _dp(Hv))
+        self._L.or_conv(self._h, _dp(u), _dp(v), _dp(Hu), _dp(Hv))
         return Hu, Hv
 
     def grad(self, f):
         f = np.ascontiguousarray(f, np.float64)
         gu = np.zeros(self.shape("u"))
         gv = np.zeros(self.shape("v"))
-        lib().or_grad(self._h, _dp(f), _dp(gu), _dp(gv))
+        self._L.or_grad(self._h, _dp(f), _dp(gu), _dp(gv))
         return gu, gv
 
     def div(self, u, v):
         u = np.ascontiguousarray(u, np.float64)
         v = np.ascontiguousarray(v, np.float64)
         out = np.zeros(self.shape("p"))
-        lib().or_div(self._h, _dp(u), _dp(v), _dp(out))
+        self._L.or_div(self._h, _dp(u), _dp(v), _dp(out))
         return out
 
     def poisson(self, b, phi0=None, omega=None, tol=1e-10, rtol=0.0, check=10, maxs=200000):
@@ -244,7 +291,7 @@ class Sim:
             omega = self.P.omega_p
         s = C.c_int(0)
         r = C.c_double(0)
-        rc = lib().or_poisson(self._h, _dp(b), _dp(phi), omega, tol, rtol, check, maxs, C.byref(s),
+        rc = self._L.or_poisson(self._h, _dp(b), _dp(phi), omega, tol, rtol, check, maxs, C.byref(s),
                              C.byref(r))
         return rc, phi, s.value, r.value
 
@@ -254,11 +301,11 @@ class Sim:
         x = np.array(x0, np.float64, copy=True)
         s = C.c_int(0)
         r = C.c_double(0)
-        rc = lib().or_helm_solve(self._h, grid, _dp(x), _dp(R), beta, Ub, C.byref(s), C.byref(r))
+        rc = self._L.or_helm_solve(self._h, grid, _dp(x), _dp(R), beta, Ub, C.byref(s), C.byref(r))
         return rc, x, s.value, r.value
 
     def clear_flags(self):
-        lib().or_clear_flags(self._h)
+        self._L.or_clear_flags(self._h)
 
 
 def omega_from_rate(omega, rho):

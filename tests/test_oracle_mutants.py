@@ -1,0 +1,55 @@
+"""Planted mistakes in the oracle: each variant changes one expression of
+the FP64 oracle the way a plausible slip would (a dropped term, a flipped
+sign, a wrong factor, a one-sided average), is compiled into its own
+library, and must fail the pin named beside it.  This shows that the pins in
+test_oracle_pins.py constrain every part of the step they are meant to:
+AB2 and Crank-Nicolson weights (Sec. 2.2), the pressure gradient, the
+convective face average, the ellipse of Sec. 2.1, the mass source, the
+added-mass term of the force and the SOR update.  CPU only.
+"""
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+MUTANTS = {
+    "ab2_as_euler": (
+        [("-1.5 * S->Hu[id] + 0.5 * S->Huo[id]", "-1.0 * S->Hu[id] + 0.0 * S->Huo[id]")],
+        pins.test_time_integration_second_order, ()),
+    "explicit_viscous_half_doubled": (
+        [("beta * lap_u_at(S, S->u, i, j)", "2.0 * beta * lap_u_at(S, S->u, i, j)")],
+        pins.test_taylor_green_decay_second_order, ()),
+    "pressure_gradient_sign": (
+        [("+ 0.5 * S->Huo[id] - gp)", "+ 0.5 * S->Huo[id] + gp)")],
+        pins.test_taylor_green_decay_second_order, ()),
+    "one_sided_face_velocity": (
+        [("double ue = 0.5 * (u[UI(i, j)] + u[UI(i + 1, j)]);", "double ue = u[UI(i, j)];")],
+        pins.test_convection_and_diffusion_operators_second_order, ()),
+    "ellipse_minor_axis_doubled": (
+        [("bb = 0.5 * S->tc * S->chord", "bb = S->tc * S->chord")],
+        pins.test_solid_area_converges_first_order, ()),
+    "mass_source_without_body_mean": (
+        [("S->cut[id] ? S->D[id] - cbar : 0.0", "S->cut[id] ? S->D[id] : 0.0")],
+        pins.test_step_divergence_bound_and_zero_net_mass_source_in_body_cells, ()),
+    "added_mass_sign": (
+        [("(sy - S->S_prev[1]) * idt", "(S->S_prev[1] - sy) * idt")],
+        pins.test_plunging_circle_feels_added_mass_force, ()),
+    "sor_step_reversed": (
+        [("fma(omega, gs - phi[id], phi[id])", "fma(omega, phi[id] - gs, phi[id])")],
+        pins.test_poisson_sor_matches_dense_solve, (7, 5, False)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_fails_its_pin(name):
+    replacements, pin, args = MUTANTS[name]
+    path = oracle.build_variant(name, replacements)
+    with oracle.use_library(path):
+        with pytest.raises((AssertionError, ValueError, FloatingPointError)):
+            pin(*args)
+
+
+def test_unchanged_oracle_passes_the_same_pins():
+    # the pins used above hold for the oracle as written
+    for _, pin, args in MUTANTS.values():
+        pin(*args)
