@@ -4,8 +4,9 @@ sign, a wrong factor, a one-sided average), is compiled into its own
 library, and must fail the pin named beside it.  This shows that the pins in
 test_oracle_pins.py constrain every part of the step they are meant to:
 AB2 and Crank-Nicolson weights (Sec. 2.2), the pressure gradient, the
-convective face average, the ellipse of Sec. 2.1, the mass source, the
-added-mass term of the force and the SOR update.  CPU only.
+convective face average, the ellipse of Sec. 2.1, the forcing-node
+interpolation, the mass source, the added-mass term of the force and the
+SOR update.  CPU only.
 """
 import pytest
 
@@ -34,6 +35,13 @@ MUTANTS = {
     "added_mass_sign": (
         [("(sy - S->S_prev[1]) * idt", "(S->S_prev[1] - sy) * idt")],
         pins.test_plunging_circle_feels_added_mass_force, ()),
+    "interpolation_weight_inverted": (
+        [("al[id] = best / (best + D);", "al[id] = D / (best + D);")],
+        pins.test_classification_matches_brute_force, (0.37,)),
+    "forcing_from_the_wrong_neighbour": (
+        [("int oi = i + (d == 0) - (d == 1), oj = j + (d == 2) - (d == 3);",
+          "int oi = i - (d == 0) + (d == 1), oj = j - (d == 2) + (d == 3);")],
+        pins.test_velocity_sor_matches_dense_solve, (0,)),
     "sor_step_reversed": (
         [("fma(omega, gs - phi[id], phi[id])", "fma(omega, phi[id] - gs, phi[id])")],
         pins.test_poisson_sor_matches_dense_solve, (7, 5, False)),
