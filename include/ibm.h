@@ -276,7 +276,14 @@ int ibm_get_profile(const ibm_ctx* ctx, ibm_profile* out);
  * samples the solver generates.  widths: channels of the four levels
  * (multiples of 16).  Inputs are 4 FP32 feature channels [H][W][4], the
  * output one FP32 channel [H][W]; H and W must be multiples of 8.  Device
- * pointers; stream may be NULL. */
+ * pointers; stream may be NULL.  The network owns its device memory
+ * (ibm_unet_create allocates the parameters, ibm_unet_destroy frees all);
+ * activation buffers are allocated by the first forward or training step
+ * at a given H x W and reallocated when the size changes, so a size change
+ * must not happen while a stream that uses the network is being captured.
+ * Errors: IBM_E_INVAL (widths not positive multiples of 16, n different
+ * from ibm_unet_num_params, H or W not multiples of 8, NULL pointers),
+ * IBM_E_CUDA. */
 typedef struct ibm_unet ibm_unet;
 int ibm_unet_create(const int widths[4], unsigned long long seed, ibm_unet** out);
 void ibm_unet_destroy(ibm_unet* net);
@@ -296,8 +303,9 @@ int ibm_unet_train_step(ibm_unet* net, const float* feat_dev, const float* targe
  * from a starting guess): mode 0, the previous increment; mode 1, the
  * previous increment plus the U-Net's prediction of its change (the net is
  * borrowed, not owned), kept only if its residual ||b - L_p phi||_inf is
- * below half that of the previous increment (counted in ibm_profile); mode 2, the previous increment and, every step, a
- * training sample recorded for ibm_get_sample.  The network works on the
+ * below half that of the previous increment (counted in ibm_profile);
+ * mode 2, the previous increment and, every step, a training sample
+ * recorded for ibm_get_sample.  The network works on the
  * grid coarsened 2x (nx, ny must be divisible by 16) with four features per
  * coarse cell (initial residual b - L_p phi^n, b, body-cell fraction, p^n,
  * each over its infinity norm) and predicts (phi^{n+1} - phi^n) / (s0 c_T),
@@ -316,9 +324,9 @@ int ibm_set_warmstart_base(ibm_ctx* ctx, int base);
  * of the force), the C_l/C_d histories, the step count, the adapted inner
  * run lengths of the FP32 solves and, when the warm start extrapolates in
  * time, the increment before, and the FP32 sweep shape chosen by the
- * autotuner (its sweeps per launch round the inner runs).  ibm_state_bytes gives the size of the
- * context's state; ibm_save_state copies it into the caller's host buffer
- * of at least that size (waits for the stream).  ibm_load_state restores
+ * autotuner (its sweeps per launch round the inner runs).  ibm_state_bytes
+ * gives the size of the context's state; ibm_save_state copies it into the
+ * caller's host buffer of at least that size (waits for the stream).  ibm_load_state restores
  * one into a context created with the same grid, Re and dt, with the same
  * body set (and the same warm-start base); stepping on from it repeats the
  * saved run's steps bit for bit.  The layout is the library's own (native
