@@ -5,8 +5,8 @@ library, and must fail the pin named beside it.  This shows that the pins in
 test_oracle_pins.py constrain every part of the step they are meant to:
 AB2 and Crank-Nicolson weights (Sec. 2.2), the pressure gradient, the
 convective face average, the ellipse of Sec. 2.1, the forcing-node
-interpolation, the mass source, the added-mass term of the force and the
-SOR update.  CPU only.
+interpolation, the outflow flux balance, the mass source, the projection,
+the pressure update, the added-mass term of the force and the SOR update.  CPU only.
 """
 import pytest
 
@@ -42,6 +42,16 @@ MUTANTS = {
         [("int oi = i + (d == 0) - (d == 1), oj = j + (d == 2) - (d == 3);",
           "int oi = i - (d == 0) + (d == 1), oj = j - (d == 2) + (d == 3);")],
         pins.test_velocity_sor_matches_dense_solve, (0,)),
+    "outflow_flux_correction_dropped": (
+        [("for (int j = 0; j < ny; ++j) S->uh[UI(nx, j)] += corr;", "(void)corr;")],
+        pins.test_step_divergence_bound_and_zero_net_mass_source_in_body_cells, ()),
+    "projection_sign": (
+        [("S->u[id] = S->uh[id] - dt * ((S->phi[PI_(i, j)] - S->phi[PI_(i - 1, j)]) * S->idxc[i]);",
+          "S->u[id] = S->uh[id] + dt * ((S->phi[PI_(i, j)] - S->phi[PI_(i - 1, j)]) * S->idxc[i]);")],
+        pins.test_step_divergence_bound_and_zero_net_mass_source_in_body_cells, ()),
+    "pressure_not_accumulated": (
+        [("S->p[id] += S->phi[id];", "S->p[id] = S->phi[id];")],
+        pins.test_taylor_green_decay_second_order, ()),
     "sor_step_reversed": (
         [("fma(omega, gs - phi[id], phi[id])", "fma(omega, phi[id] - gs, phi[id])")],
         pins.test_poisson_sor_matches_dense_solve, (7, 5, False)),
