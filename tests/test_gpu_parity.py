@@ -265,3 +265,34 @@ def test_full_size_step_properties(workload, precision):
     d1 = o.div(u1, v1)
     assert np.abs(d1[~body]).max() <= cfg.div_tol
     assert abs(np.abs(d1[~body]).max() - st["div_max"]) <= 1e-15 + 1e-9 * st["div_max"]
+
+
+def test_tallest_grid_step_properties():
+    """ny = 8192, the largest the ordered outflow-flux sums accept (256
+    chunks of 32 rows), on a tall uniform 64x8192 grid with the foil at the
+    centre, mixed path: after a step from the free stream the outflow flux
+    equals the inflow flux, the pressure residual (the oracle's operator on
+    the GPU's fields) is below the tolerance and the fluid-cell divergence
+    below div_tol."""
+    import dataclasses
+    Solver = gpu()
+    cfg = dataclasses.replace(W.plunge_192x128(), name="tall_64x8192", x0=-4.0, x1=4.0, y0=-512.0, y1=512.0,
+                              nx=64, ny=8192, dt=2e-3, div_tol=1e-8, init="uniform")
+    kw = dict(x0=cfg.x0, x1=cfg.x1, y0=cfg.y0, y1=cfg.y1, nx=cfg.nx, ny=cfg.ny, hmin=cfg.hmin, ubox=cfg.ubox,
+              Re=cfg.Re, dt=cfg.dt, ptol=cfg.ptol, htol=cfg.htol, check_p=cfg.check_p, check_h=cfg.check_h,
+              omega_p=cfg.omega())
+    g = Solver(**kw, precision=1)
+    g.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
+    g.set("u", cfg.initial_u(g.shape("u")))
+    st = g.step(1)
+    xf, yf = g.grid()
+    dy = np.diff(yf)
+    u = g.get("u")
+    q_in, q_out = np.sum(u[:, 0] * dy), np.sum(u[:, -1] * dy)
+    assert abs(q_out - q_in) <= 1e-12 * abs(q_in)
+    o = oracle.Sim(**kw)
+    phi, b = g.get("phi"), g.get("b")
+    assert np.abs(b - o.lap_p(phi)).max() <= cfg.ptol * 1.01
+    body = g.flags(2).astype(bool)
+    d = o.div(u, g.get("v"))
+    assert np.abs(d[~body]).max() <= cfg.div_tol and st["div_max"] <= cfg.div_tol
