@@ -75,3 +75,61 @@ def test_create_grid_rejects_invalid_parameters_before_touching_the_device():
                  dict(dt=-1.0), dict(ptol=0.0), dict(bc=2), dict(omega_p=2.0), dict(omega_h=2.5)):
         rc, msg = create(**over)
         assert rc == -1 and msg, (over, rc, msg)
+
+
+def test_entry_points_reject_null_handles_before_touching_the_device():
+    """Every entry point checks its handle and pointer arguments first and
+    answers IBM_E_INVAL with a message (no CUDA call is made), so this runs
+    without a GPU; ibm_destroy and ibm_batch_destroy accept NULL."""
+    import ctypes as C
+    from paper_2402_17337_gb300 import build
+    build.build()
+    import paper_2402_17337_gb300 as ibm
+    L = ibm.lib()
+    n = C.c_int(0)
+    size = C.c_size_t(0)
+    stats = ibm.StepStats()
+    prof = ibm.Profile()
+    buf = (C.c_double * 4)()
+    calls = {
+        "ibm_create_grid": (None, None),
+        "ibm_set_body": (None, 1.0, 0.12, 0.25, 2.0, 0.0, 0.0),
+        "ibm_step": (None, 1, C.byref(stats)),
+        "ibm_forces": (None, None, None, 0, C.byref(n)),
+        "ibm_get_field": (None, 0, buf, 4),
+        "ibm_set_field": (None, 0, buf, 4),
+        "ibm_get_flags": (None, 0, None, None, None, 0),
+        "ibm_get_grid": (None, None, None),
+        "ibm_set_profiling": (None, 1),
+        "ibm_get_profile": (None, C.byref(prof)),
+        "ibm_tune": (None,),
+        "ibm_tune_omega": (None, 0, None),
+        "ibm_set_sor_shape": (None, 0),
+        "ibm_set_warmstart": (None, 0, None, 1.0),
+        "ibm_set_warmstart_base": (None, 0),
+        "ibm_set_preconditioner": (None, 0, None, 1.0, 1),
+        "ibm_state_bytes": (None, C.byref(size)),
+        "ibm_save_state": (None, None, 0),
+        "ibm_load_state": (None, None, 0),
+        "ibm_batch_create": (None, 0, None),
+        "ibm_batch_step": (None, 1, C.byref(stats)),
+        "ibm_batch_set_graphs": (None, 1),
+        "ibm_batch_set_sor_shape": (None, 0),
+        "ibm_batch_set_profiling": (None, 1),
+        "ibm_batch_get_profile": (None, C.byref(prof)),
+        "ibm_unet_create": (None, 0, None),
+        "ibm_unet_params": (None, None, 0, 0),
+        "ibm_unet_grads": (None, None, 0),
+        "ibm_unet_forward": (None, None, 8, 8, None, None),
+    }
+    for name, args in calls.items():
+        rc = getattr(L, name)(*args)
+        assert rc == -1, (name, rc)
+        assert L.ibm_last_error().decode(), name
+    bad = (C.c_int * 4)(16, 24, 32, 32)
+    h = C.c_void_p()
+    assert L.ibm_unet_create(bad, 0, C.byref(h)) == -1 and not h.value
+    assert L.ibm_unet_num_params(None) == 0
+    assert L.ibm_batch_stream(None) is None
+    L.ibm_destroy(None)
+    L.ibm_batch_destroy(None)
