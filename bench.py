@@ -321,6 +321,7 @@ def run_batch(args):
         b = ibm.Batch(ss)
         if args.sor_shape >= 0:
             b.set_sor_shape(args.sor_shape)
+        b.set_graphs(args.batch_launch == "graphs")
         return ss, b
 
     ss, batch = make()
@@ -416,7 +417,8 @@ def run_batch(args):
             "config": {"workload": "batch64" if args.cases == 64 else f"batch64[:{args.cases}]",
                        "cases": args.cases, "cells_per_step": sum(cells),
                        "grids": sorted({f"{c.nx}x{c.ny}" for c in cfgs}), "global_batch": args.cases * world,
-                       "parallelism": f"replicas x{world}", "path": "mixed, batched, graph replay",
+                       "parallelism": f"replicas x{world}", "path": "mixed, batched, " + ("graph replay" if args.batch_launch == "graphs" else
+                                                                 "direct programmatic dependent launches"),
                        "warm_start": "previous increment", "sor_us_per_sweep_whole_batch": prof["sor_us_per_sweep"],
                        "poisson_sweeps_per_step_sum": statistics.mean(sum(x["sweeps_p"] for x in st) for st in stats),
                        "l2": f"{sum(cells) * 16 / 1e6:.0f} MB of FP32 sweep arrays per launch set; no flush",
@@ -452,6 +454,9 @@ def main():
     ap.add_argument("--weights", default=None, help="U-Net weights (default: the package's trained weights)")
     ap.add_argument("--workload", choices=WORKLOADS, default=WORKLOADS[0])
     ap.add_argument("--cases", type=int, default=64, help="batch64: number of cases")
+    ap.add_argument("--batch-launch", choices=("graphs", "direct"), default="graphs",
+                    help="batch sweep pairs replayed from CUDA graphs, or launched directly as programmatic "
+                         "dependents")
     ap.add_argument("--sor-shape", type=int, default=-1,
                     help="fixed FP32 sweep tile shape (index into the library's table; -1: autotuner). "
                          "For profiler runs, whose per-launch overhead distorts the autotuner's timings")

@@ -1337,16 +1337,16 @@ int batch_sor_tables(ibm_batch* B, int cfg, const std::vector<int>& act, int* ti
   return IBM_OK;
 }
 
-void batch_launch_pair(ibm_batch* B, int na, int tiles, int zero_first) {
+void batch_launch_pair(ibm_batch* B, int na, int tiles, int zero_first, int pdl) {
   const int n = (int)B->cs.size();
-  launch_sor32_batch(B->stream, B->cfg, B->d_sor, na, tiles, zero_first);
-  launch_sor32_batch(B->stream, B->cfg, B->d_sor + n, na, tiles, 0);
+  launch_sor32_batch(B->stream, B->cfg, B->d_sor, na, tiles, zero_first, pdl);
+  launch_sor32_batch(B->stream, B->cfg, B->d_sor + n, na, tiles, 0, pdl);
 }
 
 int batch_capture(ibm_batch* B, int na, int tiles, int pairs, int zero_first, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   CUDA_TRY(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
-  for (int q = 0; q < pairs; ++q) batch_launch_pair(B, na, tiles, q == 0 ? zero_first : 0);
+  for (int q = 0; q < pairs; ++q) batch_launch_pair(B, na, tiles, q == 0 ? zero_first : 0, 0);
   CUDA_TRY(cudaStreamEndCapture(B->stream, &g));
   cudaError_t e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
@@ -1358,8 +1358,8 @@ int batch_capture(ibm_batch* B, int na, int tiles, int pairs, int zero_first, cu
 // the first one starting from e = 0.
 int batch_sweeps(ibm_batch* B, int na, int tiles, int pairs) {
   B->prof.launches += 2 * pairs;
-  if (!B->use_graphs) {
-    for (int q = 0; q < pairs; ++q) batch_launch_pair(B, na, tiles, q == 0);
+  if (!B->use_graphs) {  // direct launches, as programmatic dependents
+    for (int q = 0; q < pairs; ++q) batch_launch_pair(B, na, tiles, q == 0, 1);
     CUDA_TRY(cudaGetLastError());
     return IBM_OK;
   }

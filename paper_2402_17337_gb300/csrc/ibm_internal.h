@@ -145,8 +145,10 @@ struct DcCase {
 };
 void sor32_tiles(int cfg, const Geo32& g, int* tiles_x, int* tiles_y);
 cudaError_t sor32_batch_prepare(int cfg);
+// pdl: launch as a programmatic dependent of the previous kernel on the
+// stream (direct launches; the kernel waits for it before its first load)
 void launch_sor32_batch(cudaStream_t s, int cfg, const Sor32Case* cases_dev, int ncases, int total_tiles,
-                        int zero_init);
+                        int zero_init, int pdl = 0);
 void launch_dc_residual_batch(cudaStream_t s, const DcCase* cases_dev, int ncases, int total_blocks);
 
 // geometric multigrid on the FP32 correction equation (k_mg.cu)

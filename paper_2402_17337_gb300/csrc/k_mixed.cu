@@ -605,6 +605,13 @@ __global__ void __launch_bounds__(32 * C::NY, C::MINB)
     k_sor32_rb_batch(const Sor32Case* __restrict__ cases, int ncases, int zero_init) {
   extern __shared__ float smem[];
   __shared__ Sor32Case c;  // the case's descriptor, read from shared memory where needed
+  // programmatic dependent launch (a no-op unless the launch asks for it):
+  // the descriptor tables are rewritten between rounds, so every CTA waits
+  // for the previous kernel before its first load and then lets the next
+  // launch start (forms 6 and 7 wait and release again inside; both return
+  // at once the second time)
+  griddep_wait();
+  griddep_release();
   const int b = blockIdx.x;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     int lo = 0, hi = ncases - 1;
@@ -623,7 +630,7 @@ __global__ void __launch_bounds__(32 * C::NY, C::MINB)
 struct Sor32Config {
   int TY, K, NY, V;
   void (*launch)(cudaStream_t, const Geo32&, const float*, float*, const float*, const float*, float, int, int);
-  void (*launch_batch)(cudaStream_t, const Sor32Case*, int, int, int);
+  void (*launch_batch)(cudaStream_t, const Sor32Case*, int, int, int, int);
   cudaError_t (*prepare)();
   void (*tiles)(const Geo32&, int*, int*);
 };
@@ -665,9 +672,24 @@ void launch_shape(cudaStream_t s, const Geo32& g, const float* e_in, float* e_ou
 }
 
 template <class C>
-void launch_shape_batch(cudaStream_t s, const Sor32Case* cases, int ncases, int total_tiles, int zero_init) {
+void launch_shape_batch(cudaStream_t s, const Sor32Case* cases, int ncases, int total_tiles, int zero_init,
+                        int pdl) {
   if (total_tiles <= 0) return;
-  k_sor32_rb_batch<C><<<total_tiles, dim3(32, C::NY), C::smem, s>>>(cases, ncases, zero_init);
+  if (!pdl) {
+    k_sor32_rb_batch<C><<<total_tiles, dim3(32, C::NY), C::smem, s>>>(cases, ncases, zero_init);
+    return;
+  }
+  cudaLaunchConfig_t lc{};
+  lc.gridDim = dim3(total_tiles);
+  lc.blockDim = dim3(32, C::NY);
+  lc.dynamicSmemBytes = C::smem;
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  cudaLaunchKernelEx(&lc, k_sor32_rb_batch<C>, cases, ncases, zero_init);
 }
 
 template <class C>
@@ -728,8 +750,8 @@ void sor32_tiles(int cfg, const Geo32& g, int* tiles_x, int* tiles_y) { kConfigs
 cudaError_t sor32_batch_prepare(int cfg) { return kConfigs[cfg].prepare(); }
 
 void launch_sor32_batch(cudaStream_t s, int cfg, const Sor32Case* cases_dev, int ncases, int total_tiles,
-                        int zero_init) {
-  kConfigs[cfg].launch_batch(s, cases_dev, ncases, total_tiles, zero_init);
+                        int zero_init, int pdl) {
+  kConfigs[cfg].launch_batch(s, cases_dev, ncases, total_tiles, zero_init, pdl);
 }
 
 void launch_dc_residual_batch(cudaStream_t s, const DcCase* cases_dev, int ncases, int total_blocks) {
