@@ -71,3 +71,38 @@ def test_unchanged_oracle_passes_the_same_pins():
     # the pins used above hold for the oracle as written
     for _, pin, args in MUTANTS.values():
         pin(*args)
+
+
+# The U-Net oracle (numpy) is pinned by central finite differences of its
+# loss; a slip in any backward rule must break that pin.
+import numpy as np  # noqa: E402
+
+from oracle import unet_oracle as U  # noqa: E402
+import test_unet  # noqa: E402
+
+
+def _conv_backward_flipped_taps(x, W, gy):
+    gx, gW, gb = _REAL_CONV_BACKWARD(x, W[:, ::-1, :], gy)
+    return gx, gW, gb
+
+
+def _conv_backward_no_bias(x, W, gy):
+    gx, gW, gb = _REAL_CONV_BACKWARD(x, W, gy)
+    return gx, gW, 0.0 * gb
+
+
+_REAL_CONV_BACKWARD = U.conv_backward
+UNET_MUTANTS = {
+    "pool_backward_unscaled": ("pool_backward", lambda g: np.repeat(np.repeat(g, 2, axis=0), 2, axis=1)),
+    "up_backward_one_child": ("up_backward", lambda g: g[0::2, 0::2] * 4.0),
+    "conv_backward_flipped_taps": ("conv_backward", _conv_backward_flipped_taps),
+    "conv_backward_no_bias": ("conv_backward", _conv_backward_no_bias),
+}
+
+
+@pytest.mark.parametrize("name", sorted(UNET_MUTANTS))
+def test_planted_unet_backward_mistake_fails_finite_differences(name, monkeypatch):
+    attr, fn = UNET_MUTANTS[name]
+    monkeypatch.setattr(U, attr, fn)
+    with pytest.raises(AssertionError):
+        test_unet.test_oracle_gradient_matches_finite_differences()

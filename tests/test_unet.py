@@ -31,8 +31,13 @@ def test_oracle_gradient_matches_finite_differences():
     loss, g = U.loss_and_grad(params, w, feat, target)
     rng = np.random.default_rng(4)
     idx = rng.choice(params.size, 40, replace=False)
-    # include the first and last layers explicitly
-    idx = np.concatenate([idx, [0, 5, params.size - 1, params.size - 20]])
+    # include the first and last layers explicitly, and one weight and one
+    # bias of every convolution
+    per_layer, off = [], 0
+    for cin, cout, _ in U.layers(w):
+        per_layer += [off + (cout * 9 * cin) // 2, off + cout * 9 * cin + cout // 2]
+        off += cout * 9 * cin + cout
+    idx = np.concatenate([idx, [0, 5, params.size - 1, params.size - 20], per_layer])
     eps = 1e-6
     for k in idx:
         pp, pm = params.copy(), params.copy()
