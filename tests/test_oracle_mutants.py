@@ -52,6 +52,16 @@ MUTANTS = {
     "pressure_not_accumulated": (
         [("S->p[id] += S->phi[id];", "S->p[id] = S->phi[id];")],
         pins.test_taylor_green_decay_second_order, ()),
+    "u_east_diffusion_wrong_cell": (
+        [("    S->uE[i] = 1.0 / (S->dx[i] * S->dxc[i]);", "    S->uE[i] = 1.0 / (S->dx[i - 1] * S->dxc[i]);")],
+        pins.test_velocity_laplacians_on_a_stretched_grid, ()),
+    "u_north_diffusion_wrong_spacing": (
+        [("S->uN[j] = j < ny - 1 ? 1.0 / (S->dyc[j + 1] * S->dy[j]) : 0.0;",
+          "S->uN[j] = j < ny - 1 ? 1.0 / (S->dyc[j + 1] * S->dy[j + 1]) : 0.0;")],
+        pins.test_velocity_laplacians_on_a_stretched_grid, ()),
+    "v_south_diffusion_wrong_cell": (
+        [("S->vS[j] = 1.0 / (S->dy[j - 1] * S->dyc[j]);", "S->vS[j] = 1.0 / (S->dy[j] * S->dyc[j]);")],
+        pins.test_velocity_laplacians_on_a_stretched_grid, ()),
     "sor_step_reversed": (
         [("fma(omega, gs - phi[id], phi[id])", "fma(omega, phi[id] - gs, phi[id])")],
         pins.test_poisson_sor_matches_dense_solve, (7, 5, False)),
