@@ -62,6 +62,12 @@ MUTANTS = {
     "v_south_diffusion_wrong_cell": (
         [("S->vS[j] = 1.0 / (S->dy[j - 1] * S->dyc[j]);", "S->vS[j] = 1.0 / (S->dy[j] * S->dyc[j]);")],
         pins.test_velocity_laplacians_on_a_stretched_grid, ()),
+    "u_cross_flux_midpoint_weights": (
+        [("  double w = S->wx[i];\n  if (j < ny - 1) {", "  double w = 0.5;\n  if (j < ny - 1) {")],
+        pins.test_convection_cross_terms_on_a_stretched_grid, ()),
+    "v_cross_flux_midpoint_weights": (
+        [("  double w = S->wy[j];\n  double ue", "  double w = 0.5;\n  double ue")],
+        pins.test_convection_cross_terms_on_a_stretched_grid, ()),
     "sor_step_reversed": (
         [("fma(omega, gs - phi[id], phi[id])", "fma(omega, phi[id] - gs, phi[id])")],
         pins.test_poisson_sor_matches_dense_solve, (7, 5, False)),

@@ -113,6 +113,23 @@ def test_velocity_laplacians_on_a_stretched_grid():
         assert np.sum((V * phi * lap(phi))[interior]) < 0
 
 
+def test_convection_cross_terms_on_a_stretched_grid():
+    """The cross fluxes of the convection operator interpolate linearly in
+    the coordinate (Sec. 2.3 grid; reading 13): with u = 1 and v = x y the
+    u-equation's flux divergence d(uv)/dy is x exactly at interior u nodes,
+    and with u = x y and v = 1 the v-equation's d(uv)/dx is y exactly at
+    interior v nodes, however uneven the spacing."""
+    s = stretched_small(17, 13)
+    xf, yf = s.grid()
+    xc, yc = 0.5 * (xf[1:] + xf[:-1]), 0.5 * (yf[1:] + yf[:-1])
+    Xu, Yu = np.meshgrid(xf, yc)
+    Xv, Yv = np.meshgrid(xc, yf)
+    Hu, _ = s.conv(np.ones(s.shape("u")), Xv * Yv)
+    np.testing.assert_allclose(Hu[1:-1, 1:-1], Xu[1:-1, 1:-1], rtol=1e-11, atol=1e-12)
+    _, Hv = s.conv(Xu * Yu, np.ones(s.shape("v")))
+    np.testing.assert_allclose(Hv[1:-1, 1:-1], Yv[1:-1, 1:-1], rtol=1e-11, atol=1e-12)
+
+
 def _mms_error(n, stretched):
     # phi = cos(pi x) cos(pi y) on [0,1]^2 has zero normal derivative on the boundary
     if stretched:
