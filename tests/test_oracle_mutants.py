@@ -68,6 +68,9 @@ MUTANTS = {
     "v_cross_flux_midpoint_weights": (
         [("  double w = S->wy[j];\n  double ue", "  double w = 0.5;\n  double ue")],
         pins.test_convection_cross_terms_on_a_stretched_grid, ()),
+    "lift_coefficient_half": (
+        [("st.cl = 2.0 * Fy / S->chord;", "st.cl = Fy / S->chord;")],
+        pins.test_plunging_circle_feels_added_mass_force, ()),
     "sor_step_reversed": (
         [("fma(omega, gs - phi[id], phi[id])", "fma(omega, phi[id] - gs, phi[id])")],
         pins.test_poisson_sor_matches_dense_solve, (7, 5, False)),
