@@ -17,6 +17,12 @@ MUTANTS = {
     "ab2_as_euler": (
         [("-1.5 * S->Hu[id] + 0.5 * S->Huo[id]", "-1.0 * S->Hu[id] + 0.0 * S->Huo[id]")],
         pins.test_time_integration_second_order, ()),
+    "ab2_as_euler_in_v": (
+        [("-1.5 * S->Hv[id] + 0.5 * S->Hvo[id]", "-1.0 * S->Hv[id] + 0.0 * S->Hvo[id]")],
+        pins.test_time_integration_second_order, ()),
+    "pressure_gradient_sign_in_v": (
+        [("+ 0.5 * S->Hvo[id] - gp)", "+ 0.5 * S->Hvo[id] + gp)")],
+        pins.test_taylor_green_decay_second_order, ()),
     "explicit_viscous_half_doubled": (
         [("beta * lap_u_at(S, S->u, i, j)", "2.0 * beta * lap_u_at(S, S->u, i, j)")],
         pins.test_taylor_green_decay_second_order, ()),
