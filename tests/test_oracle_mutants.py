@@ -131,3 +131,18 @@ def test_planted_unet_backward_mistake_fails_finite_differences(name, monkeypatc
     monkeypatch.setattr(U, attr, fn)
     with pytest.raises(AssertionError):
         test_unet.test_oracle_gradient_matches_finite_differences()
+
+
+_REAL_CONV = U.conv
+UNET_FORWARD_MUTANTS = {
+    "conv_forward_flipped_taps": ("conv", lambda x, W, b: _REAL_CONV(x, W[:, ::-1, :], b)),
+    "pool_forward_two_children": ("pool", lambda x: 0.5 * (x[0::2, 0::2] + x[1::2, 1::2])),
+}
+
+
+@pytest.mark.parametrize("name", sorted(UNET_FORWARD_MUTANTS))
+def test_planted_unet_forward_mistake_fails_the_torch_reference(name, monkeypatch):
+    attr, fn = UNET_FORWARD_MUTANTS[name]
+    monkeypatch.setattr(U, attr, fn)
+    with pytest.raises(AssertionError):
+        test_unet.test_oracle_forward_matches_torch_cpu_reference()

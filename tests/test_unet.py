@@ -108,3 +108,40 @@ def test_gpu_unet_training_reduces_loss():
     for _ in range(200):
         l = net.train_step(fd.data_ptr(), td.data_ptr(), H, W, lr=2e-3, apply=True)
     assert l < 0.2 * l0, (l0, l)
+
+
+def test_oracle_forward_matches_torch_cpu_reference():
+    """The oracle's forward pass against the same network assembled from
+    PyTorch CPU library operations in FP64 (cross-correlation conv2d with
+    zero padding 1, 2x2 average pooling, nearest 2x upsampling, channel
+    concatenation [upsampled deeper level, skip], ReLU, a head without
+    ReLU whose channel 0 is the output): pins the oracle's own convolution,
+    pooling and upsampling code and the wiring of the levels."""
+    torch = pytest.importorskip("torch")
+    import torch.nn.functional as F
+    w = WIDTHS_TINY
+    params = rand_params(w, 7)
+    feat = Wk.random_field((16, 24, 4), seed=8)
+    out, _ = U.forward(params, w, feat)
+    P = U.unpack(params, w)
+
+    def conv(x, k):
+        Wk_, b, relu = P[k]
+        weight = torch.tensor(Wk_.reshape(Wk_.shape[0], 3, 3, Wk_.shape[2])).permute(0, 3, 1, 2)
+        y = F.conv2d(x, weight, torch.tensor(b), padding=1)
+        return F.relu(y) if relu else y
+
+    x = torch.zeros((1, 16) + feat.shape[:2], dtype=torch.float64)
+    x[0, :4] = torch.tensor(feat).permute(2, 0, 1)
+    e = []
+    h = x
+    for l in range(4):
+        if l > 0:
+            h = F.avg_pool2d(e[-1], 2)
+        e.append(conv(conv(h, 2 * l), 2 * l + 1))
+    d = e[3]
+    for l, k in zip((2, 1, 0), (8, 10, 12)):
+        cat = torch.cat([F.interpolate(d, scale_factor=2, mode="nearest"), e[l]], dim=1)
+        d = conv(conv(cat, k), k + 1)
+    ref = conv(d, 14)[0, 0].numpy()
+    np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
