@@ -26,18 +26,32 @@ _lock = threading.Lock()
 _lib = None
 
 
+_PLAIN_PATH = os.path.join(_BUILD, "liboracle_plain.so")
+
+
+def _compile(out_path, force, defines=()):
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(out_path)
+            and os.path.getmtime(out_path) >= os.path.getmtime(_SRC)):
+        return out_path
+    tmp = out_path + f".tmp{os.getpid()}"
+    cmd = (["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-Wall"]
+           + [f"-D{d}" for d in defines] + ["-o", tmp, _SRC, "-lm"])
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out_path)
+    return out_path
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, no FP contraction, OpenMP)."""
-    os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
-           "-Wall", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    return _compile(_LIB_PATH, force)
+
+
+def build_plain(force: bool = False) -> str:
+    """Compile the oracle's textbook-arithmetic form (-DORACLE_PLAIN: divisions
+    by spacings, no fused multiply-add, flux-form Laplacians, one-pass sums)
+    into its own library, for use with `use_library`."""
+    return _compile(_PLAIN_PATH, force, ("ORACLE_PLAIN",))
 
 
 class Params(C.Structure):

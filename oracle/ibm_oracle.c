@@ -38,6 +38,16 @@
  * index order (outflow flux: rows within chunks of 32, then the chunks;
  * body-cell source: along each row, then the rows).  Everything else is a
  * plain expression.
+ *
+ * Textbook form.  Compiled with -DORACLE_PLAIN the same file computes every
+ * operator in its textbook form instead: flux differences divided by the
+ * spacings, every product and sum rounded on its own (no fused
+ * multiply-add), SOR updates written as (1 - omega) x + omega GS with the
+ * Gauss-Seidel value divided by the diagonal, and the feedback sums in one
+ * pass in index order.  The two forms are the same mathematics; the tests
+ * compare them operator by operator and over whole steps, so a slip shared
+ * by the recipe's two implementations (oracle and GPU) cannot hide in the
+ * recipe itself.
  */
 #include <math.h>
 #include <stdint.h>
@@ -315,8 +325,21 @@ int or_get_grid(const or_sim* S, double* xf, double* yf) {
 #define VI(i, j) ((size_t)(j) * nx + (i))
 #define PI_(i, j) ((size_t)(j) * nx + (i))
 
+/* The two arithmetic forms (see the file header).  MULADD(a, b, c) is
+ * a*b + c, fused in the recipe and rounded twice in the textbook form;
+ * OVER(x, d, id) is x/d, computed as x times the stored reciprocal id = 1/d
+ * in the recipe. */
+#ifdef ORACLE_PLAIN
+#define MULADD(a, b, c) ((a) * (b) + (c))
+#define OVER(x, d, id) ((x) / (d))
+#else
+#define MULADD(a, b, c) fma((a), (b), (c))
+#define OVER(x, d, id) ((x) * (id))
+#endif
+
 /* ------------------------------------------------- discrete operators (Sec. 2.2) */
 
+#ifndef ORACLE_PLAIN
 /* 5-point finite-volume Laplacian sum_nb a_nb (x_nb - x_P) as an fma chain
  * in the order E, W, N, S; a missing neighbour (outside the node range)
  * enters with value 0 and, except at an inflow face, a zero coefficient. */
@@ -357,6 +380,53 @@ static double lap_p_at(const or_sim* S, const double* f, int i, int j) {
   double xS = j > 0 ? f[PI_(i, j - 1)] : 0.0;
   return lap5(S->pE[i], S->pW[i], S->pN[j], S->pS[j], xE, xW, xN, xS, c);
 }
+#else
+/* Textbook flux form of the same three Laplacians: the face gradients
+ * (neighbour difference over the distance between the nodes) differenced
+ * across the control volume and divided by its width. */
+
+/* u grid: control volume [xc[i-1], xc[i]] x [yf[j], yf[j+1]]; free-slip walls
+ * pass no flux through y0 and y1; the faces i = 0 and i = nx hold Dirichlet
+ * values.  Unknown nodes i = 1..nx-1. */
+static double lap_u_at(const or_sim* S, const double* u, int i, int j) {
+  int nx = S->nx, ny = S->ny;
+  double c = u[UI(i, j)];
+  double fe = (u[UI(i + 1, j)] - c) / S->dx[i];
+  double fw = (c - u[UI(i - 1, j)]) / S->dx[i - 1];
+  double fn = (j < ny - 1) ? (u[UI(i, j + 1)] - c) / S->dyc[j + 1] : 0.0;
+  double fs = (j > 0) ? (c - u[UI(i, j - 1)]) / S->dyc[j] : 0.0;
+  return (fe - fw) / S->dxc[i] + (fn - fs) / S->dy[j];
+}
+
+/* v grid: control volume [xf[i], xf[i+1]] x [yc[j-1], yc[j]]; the walls y0,
+ * y1 hold v = 0.  At x0 the inflow (bc 0) holds v = 0 on the boundary, half a
+ * cell from the node; the free-slip box (bc 1) passes no flux.  At x1 no
+ * flux. */
+static double lap_v_at(const or_sim* S, const double* v, int i, int j) {
+  int nx = S->nx;
+  double c = v[VI(i, j)];
+  double fe = (i < nx - 1) ? (v[VI(i + 1, j)] - c) / S->dxc[i + 1] : 0.0;
+  double fw;
+  if (i > 0)
+    fw = (c - v[VI(i - 1, j)]) / S->dxc[i];
+  else
+    fw = (S->P.bc == 0) ? (c - 0.0) / (0.5 * S->dx[0]) : 0.0;
+  double fn = (v[VI(i, j + 1)] - c) / S->dy[j];
+  double fs = (c - v[VI(i, j - 1)]) / S->dy[j - 1];
+  return (fe - fw) / S->dx[i] + (fn - fs) / S->dyc[j];
+}
+
+/* Pressure Laplacian L_p = D G with homogeneous Neumann boundaries. */
+static double lap_p_at(const or_sim* S, const double* f, int i, int j) {
+  int nx = S->nx, ny = S->ny;
+  double c = f[PI_(i, j)];
+  double fe = (i < nx - 1) ? (f[PI_(i + 1, j)] - c) / S->dxc[i + 1] : 0.0;
+  double fw = (i > 0) ? (c - f[PI_(i - 1, j)]) / S->dxc[i] : 0.0;
+  double fn = (j < ny - 1) ? (f[PI_(i, j + 1)] - c) / S->dyc[j + 1] : 0.0;
+  double fs = (j > 0) ? (c - f[PI_(i, j - 1)]) / S->dyc[j] : 0.0;
+  return (fe - fw) / S->dx[i] + (fn - fs) / S->dy[j];
+}
+#endif
 
 /* Convective flux divergence H = div(u u), second-order central finite volume,
  * linear interpolation in the coordinate to the corners (Sec. 2.2). */
@@ -376,7 +446,7 @@ static double conv_u_at(const or_sim* S, const double* u, const double* v, int i
     double us = (1.0 - S->wy[j]) * u[UI(i, j - 1)] + S->wy[j] * u[UI(i, j)];
     fs = vs * us;
   }
-  return (ue * ue - uw * uw) * S->idxc[i] + (fn - fs) * S->idy[j];
+  return OVER(ue * ue - uw * uw, S->dxc[i], S->idxc[i]) + OVER(fn - fs, S->dy[j], S->idy[j]);
 }
 static double conv_v_at(const or_sim* S, const double* u, const double* v, int i, int j) {
   int nx = S->nx;
@@ -392,7 +462,7 @@ static double conv_v_at(const or_sim* S, const double* u, const double* v, int i
     vw = (1.0 - S->wx[i]) * v[VI(i - 1, j)] + S->wx[i] * v[VI(i, j)];
   else
     vw = (S->P.bc == 0) ? 0.0 : v[VI(i, j)];
-  return (ue * ve - uw * vw) * S->idx[i] + (vn * vn - vs * vs) * S->idyc[j];
+  return OVER(ue * ve - uw * vw, S->dx[i], S->idx[i]) + OVER(vn * vn - vs * vs, S->dyc[j], S->idyc[j]);
 }
 
 /* exported operator wrappers (canonical layouts; entries that are not
@@ -429,16 +499,17 @@ void or_grad(const or_sim* S, const double* f, double* gu, double* gv) {
   memset(gu, 0, sizeof(double) * (nx + 1) * ny);
   memset(gv, 0, sizeof(double) * nx * (ny + 1));
   for (int j = 0; j < ny; ++j)
-    for (int i = 1; i < nx; ++i) gu[UI(i, j)] = (f[PI_(i, j)] - f[PI_(i - 1, j)]) * S->idxc[i];
+    for (int i = 1; i < nx; ++i) gu[UI(i, j)] = OVER(f[PI_(i, j)] - f[PI_(i - 1, j)], S->dxc[i], S->idxc[i]);
   for (int j = 1; j < ny; ++j)
-    for (int i = 0; i < nx; ++i) gv[VI(i, j)] = (f[PI_(i, j)] - f[PI_(i, j - 1)]) * S->idyc[j];
+    for (int i = 0; i < nx; ++i) gv[VI(i, j)] = OVER(f[PI_(i, j)] - f[PI_(i, j - 1)], S->dyc[j], S->idyc[j]);
 }
 /* divergence of a face field, per cell */
 void or_div(const or_sim* S, const double* u, const double* v, double* out) {
   int nx = S->nx, ny = S->ny;
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i)
-      out[PI_(i, j)] = (u[UI(i + 1, j)] - u[UI(i, j)]) * S->idx[i] + (v[VI(i, j + 1)] - v[VI(i, j)]) * S->idy[j];
+      out[PI_(i, j)] = OVER(u[UI(i + 1, j)] - u[UI(i, j)], S->dx[i], S->idx[i]) +
+                       OVER(v[VI(i, j + 1)] - v[VI(i, j)], S->dy[j], S->idy[j]);
 }
 
 /* ------------------------------------------ classification (Sec. 2.2, "flagging") */
@@ -599,7 +670,7 @@ static double forcing_value(const or_sim* S, int grid, const double* x, int i, i
     int oi = i + (d == 0) - (d == 1), oj = j + (d == 2) - (d == 3);
     xo = x[grid == 0 ? UI(oi, oj) : VI(oi, oj)];
   }
-  return fma(al, xo - Ub, Ub);
+  return MULADD(al, xo - Ub, Ub);
 }
 
 /* Row residual of (I - beta L) x = R on fluid rows, of the interpolation
@@ -612,7 +683,7 @@ static double helm_row_res(const or_sim* S, int grid, const double* x, const dou
   if (fl == FL_SOLID) return Ub - x[id];
   if (fl == FL_FORCE) return forcing_value(S, grid, x, i, j, Ub) - x[id];
   double L = grid == 0 ? lap_u_at(S, x, i, j) : lap_v_at(S, x, i, j);
-  return R[id] - fma(-beta, L, x[id]);
+  return R[id] - MULADD(-beta, L, x[id]);
 }
 
 static double helm_res_inf(const or_sim* S, int grid, const double* x, const double* R, double beta,
@@ -672,12 +743,25 @@ static int helm_solve(or_sim* S, int grid, double* x, const double* R, double be
           }
           double xE, xW, xN, xS;
           helm_nb(S, grid, x, i, j, &xE, &xW, &xN, &xS);
+#ifndef ORACLE_PLAIN
           double sum = cE[i] * xE;
           sum = fma(cW[i], xW, sum);
           sum = fma(cN[j], xN, sum);
           sum = fma(cS[j], xS, sum);
           double gs = fma(beta, sum, R[id]) * inv[id];
           x[id] = fma(om, gs - x[id], x[id]);
+#else
+          /* (1 + beta sum a_nb) x_P = R + beta sum a_nb x_nb */
+          double offsum = 0.0;
+          offsum += cE[i] * xE;
+          offsum += cW[i] * xW;
+          offsum += cN[j] * xN;
+          offsum += cS[j] * xS;
+          double diag = cE[i] + cW[i] + cN[j] + cS[j];
+          double gs = (R[id] + beta * offsum) / (1.0 + beta * diag);
+          x[id] = (1.0 - om) * x[id] + om * gs;
+          (void)inv;
+#endif
         }
     }
     ++s;
@@ -743,12 +827,22 @@ int or_poisson(or_sim* S, const double* b, double* phi, double omega, double tol
           double xW = i > 0 ? phi[PI_(i - 1, j)] : 0.0;
           double xN = j < ny - 1 ? phi[PI_(i, j + 1)] : 0.0;
           double xS = j > 0 ? phi[PI_(i, j - 1)] : 0.0;
+#ifndef ORACLE_PLAIN
           double sum = S->pE[i] * xE;
           sum = fma(S->pW[i], xW, sum);
           sum = fma(S->pN[j], xN, sum);
           sum = fma(S->pS[j], xS, sum);
           double gs = (sum - b[id]) * S->ipd[id];
           phi[id] = fma(omega, gs - phi[id], phi[id]);
+#else
+          double sum = 0.0;
+          sum += S->pE[i] * xE;
+          sum += S->pW[i] * xW;
+          sum += S->pN[j] * xN;
+          sum += S->pS[j] * xS;
+          double gs = (sum - b[id]) / (S->pE[i] + S->pW[i] + S->pN[j] + S->pS[j]);
+          phi[id] = (1.0 - omega) * phi[id] + omega * gs;
+#endif
         }
     }
     ++s;
@@ -813,13 +907,13 @@ static int one_step(or_sim* S) {
   for (int j = 0; j < ny; ++j)
     for (int i = 1; i < nx; ++i) {
       size_t id = UI(i, j);
-      double gp = (S->p[PI_(i, j)] - S->p[PI_(i - 1, j)]) * S->idxc[i];
+      double gp = OVER(S->p[PI_(i, j)] - S->p[PI_(i - 1, j)], S->dxc[i], S->idxc[i]);
       S->Ru[id] = S->u[id] + dt * (-1.5 * S->Hu[id] + 0.5 * S->Huo[id] - gp) + beta * lap_u_at(S, S->u, i, j);
     }
   for (int j = 1; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       size_t id = VI(i, j);
-      double gp = (S->p[PI_(i, j)] - S->p[PI_(i, j - 1)]) * S->idyc[j];
+      double gp = OVER(S->p[PI_(i, j)] - S->p[PI_(i, j - 1)], S->dyc[j], S->idyc[j]);
       S->Rv[id] = S->v[id] + dt * (-1.5 * S->Hv[id] + 0.5 * S->Hvo[id] - gp) + beta * lap_v_at(S, S->v, i, j);
     }
   /* boundary values of the intermediate velocity at t^{n+1} */
@@ -836,8 +930,9 @@ static int one_step(or_sim* S) {
     for (int j = 0; j < ny; ++j) {
       S->uh[UI(0, j)] = P->u_in;
       double ub = S->u[UI(nx, j)];
-      S->uh[UI(nx, j)] = ub - dt * P->u_in * (ub - S->u[UI(nx - 1, j)]) * S->idx[nx - 1];
+      S->uh[UI(nx, j)] = ub - OVER(dt * P->u_in * (ub - S->u[UI(nx - 1, j)]), S->dx[nx - 1], S->idx[nx - 1]);
     }
+#ifndef ORACLE_PLAIN
     /* fluxes: in row order within chunks of 32 rows, then the chunk sums in order */
     for (int j0 = 0; j0 < ny; j0 += 32) {
       double a = 0.0, b = 0.0, c = 0.0;
@@ -850,6 +945,13 @@ static int one_step(or_sim* S) {
       qout += b;
       ly += c;
     }
+#else
+    for (int j = 0; j < ny; ++j) {
+      qin += S->uh[UI(0, j)] * S->dy[j];
+      qout += S->uh[UI(nx, j)] * S->dy[j];
+      ly += S->dy[j];
+    }
+#endif
     double corr = (qin - qout) / ly;
     for (int j = 0; j < ny; ++j) S->uh[UI(nx, j)] += corr;
   } else {
@@ -881,8 +983,9 @@ static int one_step(or_sim* S) {
    * so the faces a moving body pushes through still drive the pressure.
    * b = (D(uhat) - q)/dt. */
   or_div(S, S->uh, S->vh, S->D);
-  /* sums over body cells: along each row in order, then the row sums in order */
   double sdv = 0.0, sv = 0.0;
+#ifndef ORACLE_PLAIN
+  /* sums over body cells: along each row in order, then the row sums in order */
   for (int j = 0; j < ny; ++j) {
     double a = 0.0, b = 0.0;
     for (int i = 0; i < nx; ++i)
@@ -894,6 +997,15 @@ static int one_step(or_sim* S) {
     sdv += a;
     sv += b;
   }
+#else
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      if (S->cut[PI_(i, j)]) {
+        double V = S->dx[i] * S->dy[j];
+        sdv += S->D[PI_(i, j)] * V;
+        sv += V;
+      }
+#endif
   double cbar = sv > 0.0 ? sdv / sv : 0.0;
   double sq = 0.0;
   for (int j = 0; j < ny; ++j)
@@ -946,7 +1058,7 @@ static int one_step(or_sim* S) {
       if (i == 0 || i == nx)
         S->u[id] = S->uh[id];
       else
-        S->u[id] = S->uh[id] - dt * ((S->phi[PI_(i, j)] - S->phi[PI_(i - 1, j)]) * S->idxc[i]);
+        S->u[id] = S->uh[id] - dt * OVER(S->phi[PI_(i, j)] - S->phi[PI_(i - 1, j)], S->dxc[i], S->idxc[i]);
     }
   for (int j = 0; j <= ny; ++j)
     for (int i = 0; i < nx; ++i) {
@@ -954,7 +1066,7 @@ static int one_step(or_sim* S) {
       if (j == 0 || j == ny)
         S->v[id] = S->vh[id];
       else
-        S->v[id] = S->vh[id] - dt * ((S->phi[PI_(i, j)] - S->phi[PI_(i, j - 1)]) * S->idyc[j]);
+        S->v[id] = S->vh[id] - dt * OVER(S->phi[PI_(i, j)] - S->phi[PI_(i, j - 1)], S->dyc[j], S->idyc[j]);
     }
   for (size_t id = 0; id < (size_t)nx * ny; ++id) S->p[id] += S->phi[id];
   /* H^n becomes H^{n-1} */
@@ -965,7 +1077,8 @@ static int one_step(or_sim* S) {
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       if (S->cut[PI_(i, j)]) continue;
-      double d = (S->u[UI(i + 1, j)] - S->u[UI(i, j)]) * S->idx[i] + (S->v[VI(i, j + 1)] - S->v[VI(i, j)]) * S->idy[j];
+      double d = OVER(S->u[UI(i + 1, j)] - S->u[UI(i, j)], S->dx[i], S->idx[i]) +
+                 OVER(S->v[VI(i, j + 1)] - S->v[VI(i, j)], S->dy[j], S->idy[j]);
       if (fabs(d) > dm) dm = fabs(d);
     }
   st.div_max = dm;
