@@ -57,6 +57,12 @@ SOR32_TRAFFIC = {
     ("plunge_4096x2048", (32, 8, 8, 7)): 117.465e6,
     ("plunge_4096x2048", (64, 16, 16, 7)): 115.556e6,
 }
+# warp instructions issued per launch of the FP32 sweep kernel (ncu smsp__inst_executed.sum of one
+# launch, profiles/k_sor32_rb_*.md), by workload and tile shape: the issue roofline of a kernel that is
+# bound by latency and issue, not by DRAM (its working set fits in L2 on 2048x1024)
+SOR32_INST = {
+    ("plunge_2048x1024", (80, 16, 16, 7)): 15.768846e6,
+}
 WORKLOADS = ("plunge_2048x1024", "plunge_4096x2048", "unet_1024x512", "batch64")
 METRIC = "cell-steps/s at div<1e-8: learned warm-start+mixed vs plain FP64, one GB300"
 
@@ -216,9 +222,43 @@ def oracle_sim(cfg, threads):
     return oracle.Sim(**kw, threads=threads), kw["omega_p"]
 
 
+def host_info():
+    """The host's core count and CPU description (nproc, lscpu), for the
+    CPU-baseline record."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Architecture", "Model name", "CPU(s)", "Thread(s) per core", "Core(s) per socket",
+                             "Socket(s)", "NUMA node(s)"):
+                info[k.strip()] = v.strip()
+    except (OSError, subprocess.SubprocessError):
+        info["lscpu"] = "unavailable"
+    return info
+
+
+def oracle_sweep_seconds(o, cfg, threads, sweeps=128):
+    """Seconds per pressure SOR sweep of the oracle on this grid at the given
+    thread count (a fixed number of sweeps on a seeded compatible right-hand
+    side, no stopping test)."""
+    import numpy as np
+    from paper_2402_17337_gb300 import workloads as W
+    o._L.or_set_threads(o._h, threads)
+    b = W.random_field(o.shape("p"), seed=3)
+    b -= b.mean()
+    t0 = time.perf_counter()
+    o.poisson(b, tol=0.0, check=sweeps, maxs=sweeps)
+    return (time.perf_counter() - t0) / sweeps
+
+
 def cpu_oracle_sample(cfg, state=None, max_seconds=60.0):
-    """Times the FP64 oracle on one full step of the workload (all host
-    cores), optionally started from a given (u, v, p, phi) state."""
+    """Times the FP64 oracle on one full step of the workload on all host
+    cores, optionally started from a given (u, v, p, phi) state, and
+    estimates the same step on one core: the oracle threads only its
+    pressure solve, so the one-thread step is the all-core step with its
+    sweeps re-timed at the one-thread rate measured on 128 sweeps of the same
+    grid."""
     threads = os.cpu_count() or 1
     o, w = oracle_sim(cfg, threads)
     o.set_body(cfg.chord, cfg.tc, cfg.h, cfg.k, cfg.xc, cfg.yc)
@@ -228,8 +268,12 @@ def cpu_oracle_sample(cfg, state=None, max_seconds=60.0):
     t0 = time.perf_counter()
     rc, st = o.step(1)
     t = time.perf_counter() - t0
+    sw_all = oracle_sweep_seconds(o, cfg, threads)
+    sw_one = oracle_sweep_seconds(o, cfg, 1)
+    t_one = t + st["sweeps_p"] * (sw_one - sw_all)
     return {"seconds": t, "rc": rc, "sweeps_p": st["sweeps_p"], "threads": threads,
-            "div_max": st["div_max"], "omega": w}
+            "div_max": st["div_max"], "omega": w, "seconds_1thread": t_one,
+            "sweep_ms_all": 1e3 * sw_all, "sweep_ms_1thread": 1e3 * sw_one, "host": host_info()}
 
 
 def run_reference(args, cfg):
@@ -266,7 +310,9 @@ def run_reference(args, cfg):
                    "poisson_sweeps_per_step": statistics.mean(sweeps), "omega_p": w},
         "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": threads, "kind": "oracle",
                          "sample": f"{args.warmup} untimed + {args.steps} timed full steps of {cfg.name} "
-                                   f"from the uniform free stream, FP64 oracle, {threads} OpenMP threads in the pressure solve"},
+                                   f"from the uniform free stream, FP64 oracle, {threads} OpenMP threads in the "
+                                   f"pressure solve (all host cores)",
+                         "host": host_info()},
         "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -407,7 +453,12 @@ def run_batch(args):
                "sample": f"one full step of {cfgs[0].name} ({cfgs[0].nx}x{cfgs[0].ny}) from the GPU run's state at "
                          f"the start of the timed window, {r['sweeps_p']} pressure sweeps at the oracle's own "
                          f"relaxation factor {r['omega']:.6f}, {r['seconds']:.1f} s, FP64 oracle, "
-                         f"{r['threads']} OpenMP threads in the pressure solve"}
+                         f"{r['threads']} OpenMP threads in the pressure solve (all host cores)",
+               "one_core": {"value": cfgs[0].cells / r["seconds_1thread"] if r["rc"] == 0 else None,
+                            "unit": "cell-steps/s", "cores": 1,
+                            "sample": f"the same step with its sweeps at the one-thread rate "
+                                      f"({r['sweep_ms_1thread']:.1f} ms per sweep against {r['sweep_ms_all']:.1f} ms)"},
+               "host": r["host"]}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world,
@@ -603,16 +654,26 @@ def main():
             rows, half, nyt = prof["sor_shape"]
             sweeps_per_launch = half / 2
             traffic = SOR32_TRAFFIC.get((cfg.name, (rows, half, nyt, prof["sor_form"])))
+            inst = SOR32_INST.get((cfg.name, (rows, half, nyt, prof["sor_form"])))
+            clk_mhz = (clk or {}).get("sm_mhz") or sm_mhz
+            issue = None
+            if inst:
+                peak_issue = n_sm * 4 * clk_mhz * 1e6  # one warp instruction per clock per SM sub-partition
+                issue = {"inst_per_launch": inst, "achieved_inst_per_s": inst / t_launch,
+                         "peak_inst_per_s": peak_issue, "frac": inst / t_launch / peak_issue,
+                         "note": f"warp instructions of one launch (ncu) over the live launch time, against "
+                                 f"{n_sm} SMs x 4 issue slots per clock at {clk_mhz:.0f} MHz (sampled median)"}
             roof = {"bound": "hbm", "kernel": f"k_sor32_rb (FP32 red-black SOR, tile {rows} rows x 128 cells, "
                                               f"{half} half-sweeps per launch, chosen by the autotuner)",
                     "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "launch_us": t_launch * 1e6,
                     "shape": [rows, half, nyt, prof["sor_form"]], "shape_index": prof["sor_index"],
                     "fp32_tflops": SOR_FLOPS_PER_UPDATE * cfg.cells * sweeps_per_launch / t_launch / 1e12,
-                    "fp32_peak_tflops": fp32_peak,
-                    "peak_note": f"HBM {peaks['hbm_gbs']} GB/s ({peak_src}); algorithmic bytes: read e and r, "
-                                 f"write e once per launch ({SOR32_BYTES_PER_CELL_LAUNCH} B/cell); FP32 working set "
-                                 f"{cfg.cells * 16 / 1e6:.0f} MB against 129 MB of L2"}
+                    "fp32_peak_tflops": fp32_peak, "issue": issue,
+                    "peak_note": f"HBM {peaks['hbm_gbs']} GB/s ({peak_src}); algorithmic bytes "
+                                 f"{SOR32_BYTES_PER_CELL_LAUNCH} B/cell per launch (e and r read, e written, once "
+                                 f"per launch of {half} half-sweeps; the kernel also reads the FP32 reciprocal "
+                                 f"diagonal); FP32 working set {cfg.cells * 16 / 1e6:.0f} MB against 129 MB of L2"}
 
     # ------------------------------------------------------------- end to end
     # A second context runs the same warm-up and the same window of steps
@@ -662,7 +723,14 @@ def main():
                "sample": f"one full step of {cfg.name} started from the GPU run's state at the start of the "
                          f"timed window (AB2 history restarted), {r['sweeps_p']} pressure sweeps at the oracle's "
                          f"own relaxation factor {r['omega']:.6f}, {r['seconds']:.1f} s, FP64 oracle, "
-                         f"{r['threads']} OpenMP threads in the pressure solve"}
+                         f"{r['threads']} OpenMP threads in the pressure solve (all host cores)",
+               "one_core": {"value": cfg.cells / r["seconds_1thread"] if r["rc"] == 0 else None,
+                            "unit": "cell-steps/s", "cores": 1,
+                            "sample": f"the same step with its {r['sweeps_p']} sweeps at the one-thread rate "
+                                      f"({r['sweep_ms_1thread']:.1f} ms per sweep against "
+                                      f"{r['sweep_ms_all']:.1f} ms on {r['threads']} threads, 128 sweeps each); "
+                                      f"the rest of the oracle's step is single-threaded in both"},
+               "host": r["host"]}
 
     if rank == 0:
         sweeps = [st["sweeps_p"] for st in stats]

@@ -192,7 +192,9 @@ int ibm_poisson_solve(ibm_ctx* ctx, const double* b_dev, double* phi_dev, double
  * with factor omega, checking ||b - L_p phi||_inf <= tol every check_every
  * sweeps (<= 0: 8), at most max_sweeps sweeps (<= 0: 1e6), then shifts phi
  * so that cell (nx-1, 0) is zero; the iterates equal those of
- * ibm_poisson_solve on the same grid.  b_dev and phi_dev are device pointers
+ * ibm_poisson_solve on an FP64 (precision 0) context of the same grid (the
+ * mixed and multigrid contexts iterate differently).  xf and yf must
+ * increase strictly (IBM_E_INVAL otherwise).  b_dev and phi_dev are device pointers
  * to nx*ny doubles in the compact layout; phi_dev holds the initial guess
  * and receives the result.  stream is a cudaStream_t (NULL: the default
  * stream); the call returns after the stream has finished its work.

@@ -124,8 +124,11 @@ def forward(params, w, feat, bf16=False):
     return out[..., 0], cache
 
 
-def loss_and_grad(params, w, feat, target, bf16=False):
-    """Mean squared error of output channel 0 and its gradient (flat)."""
+def loss_and_grad(params, w, feat, target, bf16=False, trace=None):
+    """Mean squared error of output channel 0 and its gradient (flat).  With
+    a dict `trace`, trace[k] receives (input, output gradient after the ReLU
+    mask, weights as used) of convolution k: the operands of its weight and
+    bias gradients."""
     R = bf16_round if bf16 else (lambda a: a)
     P = unpack(params, w)
     out, cache = forward(params, w, feat, bf16)
@@ -139,6 +142,8 @@ def loss_and_grad(params, w, feat, target, bf16=False):
         Wk, bk, relu = P[k]
         if relu:
             gy = gy * (ys[k] > 0)
+        if trace is not None:
+            trace[k] = (xs[k], gy, R(Wk))
         gx, gW, gb = conv_backward(xs[k], R(Wk), gy)
         grads[k] = (gW, gb)
         return R(gx)

@@ -1117,6 +1117,7 @@ int step_pre(ibm_ctx* c, ibm_step_stats* st, double* thr) {
   if (rc) return rc;
   // a1: kinematics at t^{n+1} (Eqs. 1-2)
   if (c->has_body) {
+    NvtxRange r("a1-a3 kinematics and classification");
     yb = c->yb0 + c->h * std::sin(c->k * t1);
     vb = c->k * c->h * std::cos(c->k * t1);
     // a2/a3: classification and forcing data
@@ -1130,15 +1131,20 @@ int step_pre(ibm_ctx* c, ibm_step_stats* st, double* thr) {
     c->prof.launches += 1;
   }
   // a4: explicit predictor and initial guess
+  NvtxRange r4("a4 explicit predictor");
   launch_predict(c->stream, g, c->u, c->v, c->p, c->Hu, c->Hv, c->Huo, c->Hvo, c->Ru, c->Rv, c->uh, c->vh,
                  c->band, c->fu, c->fv, dt, beta, vb, c->n == 0 ? 1 : 0);
   c->prof.launches += 2;
   // a5: implicit velocity solves
-  rc = solve_helm(c, 0, beta, 0.0, &st->sweeps_u, &st->res_u);
-  if (rc) return rc;
-  rc = solve_helm(c, 1, beta, vb, &st->sweeps_v, &st->res_v);
-  if (rc) return rc;
+  {
+    NvtxRange r("a5 velocity solves");
+    rc = solve_helm(c, 0, beta, 0.0, &st->sweeps_u, &st->res_u);
+    if (rc) return rc;
+    rc = solve_helm(c, 1, beta, vb, &st->sweeps_v, &st->res_v);
+    if (rc) return rc;
+  }
   // a6: right-hand side with the mass source on body cells
+  NvtxRange r6("a6 right-hand side and mass source");
   launch_rhs(c->stream, g, c->uh, c->vh, c->b, dt);
   c->prof.launches += 1;
   if (c->has_body) {
@@ -1148,6 +1154,7 @@ int step_pre(ibm_ctx* c, ibm_step_stats* st, double* thr) {
   // a7: warm start.  The solve starts from the previous increment, or from
   // its linear extrapolation in time; the learned form adds the U-Net's
   // prediction of the remaining change.
+  NvtxRange r7("a7 warm start");
   if (c->ws_base == 1) {
     launch_extrapolate(c->stream, g, c->phi, c->phi_prev);
     c->prof.launches += 1;
@@ -1201,6 +1208,7 @@ int step_post(ibm_ctx* c, ibm_step_stats* st) {
   const Geo& g = c->geo;
   const ibm_grid_params& P = c->P;
   const double dt = P.dt, beta = dt / (2.0 * P.Re);
+  NvtxRange r("a9-a11 forces, projection and divergence");
   if (c->ws_mode == 2) {
     launch_phi_ref(c->stream, g, c->phi, c->sc);
     launch_ws_target(c->stream, g, c->Hc, c->Wc, c->phi, c->phi_old, c->sc, c->ws_cT, c->ws_max, c->ws_target);
@@ -1245,17 +1253,21 @@ int step_post(ibm_ctx* c, ibm_step_stats* st) {
 }
 
 int one_step(ibm_ctx* c) {
+  NvtxRange step("ibm_step");
   ibm_step_stats st;
   double thr;
   int rc = step_pre(c, &st, &thr);
   if (rc) return rc;
-  if (c->P.precision == 2)
-    rc = solve_poisson_mg(c, thr, c->P.max_sweeps, &st.sweeps_p, &st.res_p);
-  else if (c->P.precision == 1)
-    rc = solve_poisson_mixed(c, thr, c->P.max_sweeps, &st.sweeps_p, &st.res_p);
-  else
-    rc = solve_poisson(c, c->P.poisson_tol, c->P.poisson_rtol, c->P.check_every_p, c->P.max_sweeps, &st.sweeps_p,
-                       &st.res_p);
+  {
+    NvtxRange r("a8 pressure solve");
+    if (c->P.precision == 2)
+      rc = solve_poisson_mg(c, thr, c->P.max_sweeps, &st.sweeps_p, &st.res_p);
+    else if (c->P.precision == 1)
+      rc = solve_poisson_mixed(c, thr, c->P.max_sweeps, &st.sweeps_p, &st.res_p);
+    else
+      rc = solve_poisson(c, c->P.poisson_tol, c->P.poisson_rtol, c->P.check_every_p, c->P.max_sweeps,
+                         &st.sweeps_p, &st.res_p);
+  }
   if (rc) return rc;
   return step_post(c, &st);
 }
@@ -1538,7 +1550,11 @@ int batch_one_step(ibm_batch* B) {
     int rc = step_pre(B->cs[i], &st[i], &thr[i]);
     if (rc) return rc;
   }
-  int rc = batch_solve(B, thr, st);
+  int rc;
+  {
+    NvtxRange r("a8 pressure solves of the batch");
+    rc = batch_solve(B, thr, st);
+  }
   if (rc) return rc;
   for (int i = 0; i < n; ++i) {
     rc = step_post(B->cs[i], &st[i]);

@@ -2,10 +2,21 @@
 // Not part of the public C ABI (include/ibm.h).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
 
 namespace ibm {
+
+// Named NVTX range over a scope (host side: it spans the enqueueing of the
+// phase's kernels and any host waits inside it; a profiler attached to the
+// process shows the phases of a step, nothing is recorded otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Every staggered field (u, v, p-type) uses one storage geometry: rows
 // j = -1 .. ny+1 and columns i = -XOFF .. pitch-XOFF-1, element (i, j) at

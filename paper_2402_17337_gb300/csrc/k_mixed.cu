@@ -436,14 +436,21 @@ __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __res
     cW[m][0] = ok ? g.cW0[k] : 0.f;
     cW[m][1] = ok ? g.cW1[k] : 0.f;
   }
-  // Under a programmatic dependent launch a CTA waits for the previous
-  // kernel (griddep_wait) before it releases the next launch
-  // (griddep_release), so a launch starts only when every CTA of the launch
-  // before it is past its wait: a launch that follows a sweep launch
-  // (zero_init = 0) can load 1/d and r, which only kernels before the
-  // previous launch wrote, while the previous launch is still running.  The
-  // loads go to L2 (ld.global.cg): no line an earlier kernel left in this
-  // SM's L1 can answer them.  The first launch of a run follows the kernel
+  // Early loads of r and 1/d.  The PTX ISA defines griddepcontrol.wait to
+  // block until every prerequisite grid has completed and its memory
+  // operations are performed and visible to the waiting grid, and
+  // griddepcontrol.launch_dependents to let the dependent grid be scheduled
+  // once every CTA of the issuing grid has executed it (or exited).  Every
+  // CTA here executes the wait before the release.  So when a launch L2 that
+  // follows a sweep launch L1 (zero_init = 0) starts, every CTA of L1 has
+  // returned from its wait: the kernel before L1, which wrote r (1/d is
+  // written at set-up), has completed and its writes are performed.  L1
+  // itself writes only e.  L2 may therefore load r and 1/d before its own
+  // wait, while L1 still runs, provided the loads read the device-coherent
+  // L2 cache (ld.global.cg) and not this SM's L1, which is not coherent with
+  // writes made on other SMs and may still hold lines of an earlier kernel
+  // for a grid that starts this early (plain loads here gave wrong
+  // iterates).  The first launch of a run (zero_init = 1) follows the kernel
   // that wrote r and waits first.
   if (zero_init) {
     griddep_wait();

@@ -10,9 +10,10 @@
 // own input and output buffers.  Every GPU that loads the library holds this
 // array (256 KB) until the process exits.
 //
-// The iterates are those of ibm_poisson_solve on the same grid: same sweep
-// order, same fma chains, same reciprocal diagonal (1/(aE+aW+aN+aS),
-// computed here on the device with the same IEEE operations).
+// The iterates are those of ibm_poisson_solve on an FP64 (precision 0)
+// context of the same grid: same sweep order, same fma chains, same
+// reciprocal diagonal (1/(aE+aW+aN+aS), computed here on the device with the
+// same IEEE operations).
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -130,6 +131,21 @@ void axis_coefficients(const double* f, int n, double* aPlus, double* aMinus) {
 // from pageable memory has consumed the buffer when cudaMemcpyAsync returns)
 double g_coef[COEF];
 
+// sets the thread's error message for a failed CUDA call and returns IBM_E_CUDA
+int cuda_fail(const char* what, cudaError_t e) {
+  char msg[200];
+  snprintf(msg, sizeof msg, "ibm_poisson_solve_noalloc: %s failed: %s", what, cudaGetErrorString(e));
+  ibm::set_last_error(msg);
+  return IBM_E_CUDA;
+}
+
+// index of the first face that does not exceed its predecessor, or -1
+int first_non_increasing(const double* f, int n) {
+  for (int m = 0; m < n; ++m)
+    if (!(f[m + 1] > f[m])) return m + 1;
+  return -1;
+}
+
 }  // namespace
 
 extern "C" int ibm_poisson_solve_noalloc(int nx, int ny, const double* xf, const double* yf, const double* b_dev,
@@ -146,6 +162,15 @@ extern "C" int ibm_poisson_solve_noalloc(int nx, int ny, const double* xf, const
     ibm::set_last_error("ibm_poisson_solve_noalloc: invalid argument");
     return IBM_E_INVAL;
   }
+  for (int a = 0; a < 2; ++a) {
+    const int bad = first_non_increasing(a ? yf : xf, a ? ny : nx);
+    if (bad >= 0) {
+      snprintf(msg, sizeof msg, "ibm_poisson_solve_noalloc: %s[%d] does not exceed %s[%d] (faces must increase)",
+               a ? "yf" : "xf", bad, a ? "yf" : "xf", bad - 1);
+      ibm::set_last_error(msg);
+      return IBM_E_INVAL;
+    }
+  }
   cudaStream_t s = (cudaStream_t)stream;
   double* scratch = nullptr;
   int rc = scratch_address(&scratch);
@@ -154,11 +179,16 @@ extern "C" int ibm_poisson_solve_noalloc(int nx, int ny, const double* xf, const
     return rc;
   }
   {
+    // only the segments this grid uses: nx values of pE and pW, ny of pN and pS
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
     axis_coefficients(xf, nx, g_coef, g_coef + NOALLOC_MAX_N);
     axis_coefficients(yf, ny, g_coef + 2 * NOALLOC_MAX_N, g_coef + 3 * NOALLOC_MAX_N);
-    if (cudaMemcpyAsync(scratch, g_coef, sizeof(double) * COEF, cudaMemcpyHostToDevice, s) != cudaSuccess)
-      return IBM_E_CUDA;
+    for (int seg = 0; seg < 4; ++seg) {
+      const size_t off = (size_t)seg * NOALLOC_MAX_N, len = seg < 2 ? nx : ny;
+      const cudaError_t e =
+          cudaMemcpyAsync(scratch + off, g_coef + off, sizeof(double) * len, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync of the coefficients", e);
+    }
   }
   NoAllocGrid g{nx, ny, scratch, scratch + NOALLOC_MAX_N, scratch + 2 * NOALLOC_MAX_N, scratch + 3 * NOALLOC_MAX_N};
   unsigned long long* norm = (unsigned long long*)(scratch + COEF);
@@ -169,11 +199,13 @@ extern "C" int ibm_poisson_solve_noalloc(int nx, int ny, const double* xf, const
   for (int it = 0;; ++it) {
     if (it % m == 0) {
       unsigned long long bits = 0;
-      if (cudaMemsetAsync(norm, 0, sizeof(unsigned long long), s) != cudaSuccess) return IBM_E_CUDA;
+      cudaError_t e = cudaMemsetAsync(norm, 0, sizeof(unsigned long long), s);
+      if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync of the norm", e);
       k_na_res<<<grd_res, blk, 0, s>>>(g, phi_dev, b_dev, norm);
-      if (cudaMemcpyAsync(&bits, norm, sizeof bits, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess)
-        return IBM_E_CUDA;
+      e = cudaMemcpyAsync(&bits, norm, sizeof bits, cudaMemcpyDeviceToHost, s);
+      if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync of the norm", e);
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail("the residual check (cudaStreamSynchronize)", e);
       double r;
       std::memcpy(&r, &bits, sizeof r);
       if (sweeps) *sweeps = it;
@@ -194,6 +226,9 @@ extern "C" int ibm_poisson_solve_noalloc(int nx, int ny, const double* xf, const
   const size_t n = (size_t)nx * ny;
   k_na_ref<<<1, 32, 0, s>>>(phi_dev, nx, ref);
   k_na_shift<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(phi_dev, n, ref);
-  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return IBM_E_CUDA;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail("a kernel launch", e);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail("the final cudaStreamSynchronize", e);
   return IBM_OK;
 }

@@ -29,8 +29,11 @@ DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "unet_plunge_2048x1024.npz")
 
 
 def weights_for(workload):
-    """Path of the package's trained weights for a workload (may not exist)."""
-    return os.path.join(HERE, "weights", f"unet_{workload}.npz")
+    """Path of the package's trained weights for a workload (may not exist):
+    weights/unet_<workload>.npz, without doubling a workload name that
+    already starts with unet_."""
+    stem = workload if workload.startswith("unet_") else f"unet_{workload}"
+    return os.path.join(HERE, "weights", f"{stem}.npz")
 
 
 @dataclasses.dataclass

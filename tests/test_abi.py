@@ -133,3 +133,31 @@ def test_entry_points_reject_null_handles_before_touching_the_device():
     assert L.ibm_batch_stream(None) is None
     L.ibm_destroy(None)
     L.ibm_batch_destroy(None)
+
+
+def test_noalloc_solve_rejects_non_increasing_faces_before_touching_the_device():
+    """ibm_poisson_solve_noalloc checks its face coordinates on the host: a
+    repeated or reversed face would give infinite or negative coefficients,
+    so it returns IBM_E_INVAL and names the first bad index (dummy device
+    pointers: no CUDA call is made before the check)."""
+    import ctypes as C
+
+    import numpy as np
+
+    from paper_2402_17337_gb300 import build
+    build.build()
+    import paper_2402_17337_gb300 as ibm
+    fn = ibm.lib().ibm_poisson_solve_noalloc
+    D = C.POINTER(C.c_double)
+    fn.argtypes = [C.c_int, C.c_int, D, D, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int,
+                   C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    fn.restype = C.c_int
+    xf = np.linspace(0.0, 1.0, 11)
+    yf = np.linspace(0.0, 1.0, 9)
+    for axis, k in (("xf", 4), ("yf", 7)):
+        x, y = xf.copy(), yf.copy()
+        (x if axis == "xf" else y)[k] = (x if axis == "xf" else y)[k - 1]
+        rc = fn(10, 8, x.ctypes.data_as(D), y.ctypes.data_as(D), C.c_void_p(16), C.c_void_p(16), 1.5, 1e-8, 8, 10,
+                None, None, None)
+        assert rc == ibm.IBM_E_INVAL
+        assert f"{axis}[{k}]".encode() in ibm.lib().ibm_last_error()

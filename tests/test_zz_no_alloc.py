@@ -39,8 +39,9 @@ def test_noalloc_solve_matches_context_solve_on_two_calls():
     build.build()
     fn = _noalloc()
     nx, ny = 133, 67
+    # an FP64 (precision 0) context: the allocation-free solve repeats its iterates
     ctx = ibm.Solver(x0=-7.5, x1=24.0, y0=-12.5, y1=12.5, nx=nx, ny=ny, hmin=0.09, ubox=(-1.0, 2.0, -0.8, 0.8),
-                     dt=1.0)
+                     dt=1.0, precision=0)
     xf, yf = ctx.grid()
     V = np.outer(np.diff(yf), np.diff(xf))
     omega = ctx.P.omega_p
@@ -56,13 +57,49 @@ def test_noalloc_solve_matches_context_solve_on_two_calls():
         rc, s_ctx, r_ctx = ctx.poisson_solve(bd.data_ptr(), p_ctx.data_ptr(), 1e-9, 8)
         assert rc == 0
         s_na, r_na = C.c_int(-1), C.c_double(-1.0)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         rc = fn(nx, ny, xf.ctypes.data_as(D), yf.ctypes.data_as(D), bd.data_ptr(), p_na.data_ptr(), omega, 1e-9,
                 8, 0, None, C.byref(s_na), C.byref(r_na))
         assert rc == 0, ibm.lib().ibm_last_error()
+        if call == 1:  # after the first call's one-time set-up, a call takes no device memory
+            assert torch.cuda.mem_get_info()[0] == free0
         assert s_na.value == s_ctx and r_na.value <= 1e-9
         a, ref = p_na.cpu().numpy(), p_ctx.cpu().numpy()
         assert np.abs(a - ref).max() <= TOL * np.abs(ref).max()
         assert a[0, nx - 1] == 0.0
+
+
+def test_noalloc_on_a_side_stream():
+    """The call on a caller's non-default stream gives the same result."""
+    import torch
+
+    import paper_2402_17337_gb300 as ibm
+    from paper_2402_17337_gb300 import build
+    build.build()
+    fn = _noalloc()
+    nx, ny = 96, 61
+    ctx = ibm.Solver(x0=-7.5, x1=24.0, y0=-12.5, y1=12.5, nx=nx, ny=ny, hmin=0.12, ubox=(-1.0, 2.0, -0.8, 0.8),
+                     dt=1.0, precision=0)
+    xf, yf = ctx.grid()
+    V = np.outer(np.diff(yf), np.diff(xf))
+    b = W.random_field((ny, nx), seed=300)
+    b -= np.sum(b * V) / np.sum(V)
+    D = C.POINTER(C.c_double)
+    bd = torch.tensor(b, dtype=torch.float64, device="cuda")
+    p_ctx = torch.zeros((ny, nx), dtype=torch.float64, device="cuda")
+    p_na = torch.zeros((ny, nx), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    rc, s_ctx, _ = ctx.poisson_solve(bd.data_ptr(), p_ctx.data_ptr(), 1e-9, 8)
+    assert rc == 0
+    side = torch.cuda.Stream()
+    s_na, r_na = C.c_int(-1), C.c_double(-1.0)
+    rc = fn(nx, ny, xf.ctypes.data_as(D), yf.ctypes.data_as(D), bd.data_ptr(), p_na.data_ptr(), ctx.P.omega_p,
+            1e-9, 8, 0, C.c_void_p(side.cuda_stream), C.byref(s_na), C.byref(r_na))
+    assert rc == 0, ibm.lib().ibm_last_error()
+    assert s_na.value == s_ctx
+    a, ref = p_na.cpu().numpy(), p_ctx.cpu().numpy()
+    assert np.abs(a - ref).max() <= TOL * np.abs(ref).max()
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
