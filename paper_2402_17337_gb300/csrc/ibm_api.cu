@@ -1294,6 +1294,17 @@ struct ibm_batch {
   Sor32Case *h_sor = nullptr, *d_sor = nullptr;  // tables A (e32 -> e32b) at [0, n), B (e32b -> e32) at [n, 2n)
   DcCase *h_dc = nullptr, *d_dc = nullptr;
   unsigned long long *h_bits = nullptr, *d_bits = nullptr;
+  // whole-step batching: the case table, the first block of every case per
+  // launch kind, the active-case tables of the velocity solves (one region
+  // for the residual launch, one for the sweep launches) and the scalars
+  // read back at the end of a step
+  StepCase *h_cases = nullptr, *d_cases = nullptr;
+  int *h_first = nullptr, *d_first = nullptr;  // [BK_NUM][n]
+  int total[BK_NUM] = {0, 0, 0, 0};
+  bool first_ready = false;
+  int *h_hres = nullptr, *d_hres = nullptr;    // [2][n]: active cases, first blocks
+  int *h_hswp = nullptr, *d_hswp = nullptr;    // [3][n]: active cases, first blocks of half-sweeps, of updates
+  StepReadback *h_rb = nullptr, *d_rb = nullptr;
   std::vector<cudaEvent_t> ev;
   cudaEvent_t ev_b = nullptr, t0 = nullptr, t1 = nullptr;
   struct Graphs {
@@ -1318,6 +1329,10 @@ struct ibm_batch {
     if (d_sor) cudaFree(d_sor);
     if (d_dc) cudaFree(d_dc);
     if (d_bits) cudaFree(d_bits);
+    for (void* q : {(void*)h_cases, (void*)h_first, (void*)h_hres, (void*)h_hswp, (void*)h_rb})
+      if (q) cudaFreeHost(q);
+    for (void* q : {(void*)d_cases, (void*)d_first, (void*)d_hres, (void*)d_hswp, (void*)d_rb})
+      if (q) cudaFree(q);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     if (ev_b) cudaEventDestroy(ev_b);
     if (t0) cudaEventDestroy(t0);
@@ -1542,8 +1557,203 @@ int batch_solve(ibm_batch* B, const std::vector<double>& thr, std::vector<ibm_st
   return IBM_OK;
 }
 
+// ---- whole-step batching
+// The case table entry of context c for the step it is about to take (a1:
+// the body's position and velocity at t^{n+1}, Eqs. 1-2).
+StepCase step_case(const ibm_ctx* c) {
+  StepCase s{};
+  const ibm_grid_params& P = c->P;
+  s.g = c->geo;
+  s.band = c->band;
+  s.h32 = c->h32;
+  s.u = c->u; s.v = c->v; s.p = c->p; s.Hu = c->Hu; s.Hv = c->Hv; s.Huo = c->Huo; s.Hvo = c->Hvo;
+  s.Ru = c->Ru; s.Rv = c->Rv; s.uh = c->uh; s.vh = c->vh; s.b = c->b; s.phi = c->phi; s.phi_store = c->phi2;
+  s.au = c->au; s.av = c->av; s.qband = c->qband; s.rowsum = c->rowsum; s.partials = c->partials;
+  s.cl_hist = c->cl_d; s.cd_hist = c->cd_d;
+  s.fu = c->fu; s.fv = c->fv; s.fc = c->fc;
+  s.hd32 = c->hd32; s.hr32 = c->hr32; s.hinv_u = c->hinv_u; s.hinv_v = c->hinv_v;
+  s.sc = c->sc;
+  s.dt = P.dt;
+  s.beta = P.dt / (2.0 * P.Re);
+  const double t1 = (c->n + 1) * P.dt;
+  s.yb = c->yb0;
+  s.vb = 0.0;
+  if (c->has_body) {
+    s.yb = c->yb0 + c->h * std::sin(c->k * t1);
+    s.vb = c->k * c->h * std::cos(c->k * t1);
+  }
+  s.xb = c->xb;
+  s.ea = 0.5 * c->chord;
+  s.eb = 0.5 * c->tc * c->chord;
+  s.u_in = P.u_in;
+  s.chord = c->chord;
+  s.omega_h = (float)P.omega_h;
+  s.first_step = c->n == 0 ? 1 : 0;
+  s.n = c->n;
+  s.has_body = c->has_body ? 1 : 0;
+  s.nelem = (int)c->nelem;
+  return s;
+}
+
+// The velocity system of `grid` for every case: the defect-correction rounds
+// of solve_helm_mixed (an FP64 residual check, then 4 FP32 red-black sweeps
+// from d = 0 and x += d), with one residual launch and one host check for
+// all cases per round and shared sweep launches; cases leave as they
+// converge, each after exactly the sweeps it would take alone.
+int batch_helm(ibm_batch* B, int grid, std::vector<ibm_step_stats>& st) {
+  const int n = (int)B->cs.size(), m = 4;
+  std::vector<int> act(n), next;
+  for (int i = 0; i < n; ++i) act[i] = i;
+  for (int s = 0;; s += m) {
+    int na = (int)act.size(), tot = 0;
+    for (int k = 0; k < na; ++k) {
+      B->h_hres[k] = act[k];
+      B->h_hres[n + k] = tot;
+      tot += helm_batch_blocks(B->h_cases[act[k]], grid, 0);
+    }
+    CUDA_TRY(cudaMemcpyAsync(B->d_hres, B->h_hres, 2 * n * sizeof(int), cudaMemcpyHostToDevice, B->stream));
+    CUDA_TRY(cudaMemsetAsync(B->d_bits, 0, na * sizeof(unsigned long long), B->stream));
+    launch_helm_dc_res_batch(B->stream, B->d_cases, B->d_hres, B->d_hres + n, na, tot, grid, B->d_bits);
+    CUDA_TRY(cudaMemcpyAsync(B->h_bits, B->d_bits, na * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                             B->stream));
+    CUDA_TRY(cudaStreamSynchronize(B->stream));
+    CUDA_TRY(cudaGetLastError());
+    B->prof.launches += 1;
+    next.clear();
+    for (int k = 0; k < na; ++k) {
+      const int i = act[k];
+      const double r = bits_to_double(B->h_bits[k]);
+      (grid == 0 ? st[i].sweeps_u : st[i].sweeps_v) = s;
+      (grid == 0 ? st[i].res_u : st[i].res_v) = r;
+      if (!std::isfinite(r)) return fail(IBM_E_DIVERGED, "batch case %d: velocity residual is not finite", i);
+      if (r <= B->cs[i]->P.helm_tol) continue;
+      if (s >= B->cs[i]->P.max_sweeps)
+        return fail(IBM_E_NOCONV, "batch case %d: velocity solve (grid %d) did not converge", i, grid);
+      next.push_back(i);
+    }
+    act.swap(next);
+    if (act.empty()) return IBM_OK;
+    na = (int)act.size();
+    int th = 0, tf = 0;
+    for (int k = 0; k < na; ++k) {
+      B->h_hswp[k] = act[k];
+      B->h_hswp[n + k] = th;
+      B->h_hswp[2 * n + k] = tf;
+      th += helm_batch_blocks(B->h_cases[act[k]], grid, 1);
+      tf += helm_batch_blocks(B->h_cases[act[k]], grid, 0);
+    }
+    CUDA_TRY(cudaMemcpyAsync(B->d_hswp, B->h_hswp, 3 * n * sizeof(int), cudaMemcpyHostToDevice, B->stream));
+    launch_helm_zero_batch(B->stream, B->d_cases, B->d_hswp, na);
+    for (int k = 0; k < m; ++k) {
+      launch_helm32_half_batch(B->stream, B->d_cases, B->d_hswp, B->d_hswp + n, na, th, grid, 0);
+      launch_helm32_half_batch(B->stream, B->d_cases, B->d_hswp, B->d_hswp + n, na, th, grid, 1);
+    }
+    launch_helm_add_batch(B->stream, B->d_cases, B->d_hswp, B->d_hswp + 2 * n, na, tf, grid);
+    B->prof.launches += 2 * m + 2;
+  }
+}
+
+// One step of every case with each part of the step (a1-a11) as shared
+// launches: the number of launches per step does not grow with the number
+// of cases, and the host waits once per defect-correction round of the
+// velocity and pressure solves and once at the end.  Per case the
+// arithmetic is that of one_step on precision 1, so every case takes the
+// step it would take alone.
+int batch_one_step_fused(ibm_batch* B) {
+  const int n = (int)B->cs.size();
+  std::vector<ibm_step_stats> st(n);
+  std::vector<double> thr(n);
+  for (int i = 0; i < n; ++i) {
+    int rc = ensure_history(B->cs[i], B->cs[i]->n + 1);
+    if (rc) return rc;
+    B->h_cases[i] = step_case(B->cs[i]);
+    thr[i] = B->cs[i]->P.poisson_tol;
+  }
+  if (!B->first_ready) {
+    for (int k = 0; k < BK_NUM; ++k) {
+      int tot = 0;
+      for (int i = 0; i < n; ++i) {
+        B->h_first[k * n + i] = tot;
+        tot += batch_blocks(B->h_cases[i], k);
+      }
+      B->total[k] = tot;
+    }
+    CUDA_TRY(cudaMemcpyAsync(B->d_first, B->h_first, BK_NUM * n * sizeof(int), cudaMemcpyHostToDevice, B->stream));
+    B->first_ready = true;
+  }
+  CUDA_TRY(cudaMemcpyAsync(B->d_cases, B->h_cases, n * sizeof(StepCase), cudaMemcpyHostToDevice, B->stream));
+  const int* first = B->d_first;
+  {
+    NvtxRange r("a1-a4 classification, boundary values, predictor (batch)");
+    launch_classify_batch(B->stream, B->d_cases, first + BK_BAND * n, n, B->total[BK_BAND]);
+    launch_outflow_bc_batch(B->stream, B->d_cases, n);
+    launch_predict_batch(B->stream, B->d_cases, first + BK_PREDICT_U * n, B->total[BK_PREDICT_U],
+                         first + BK_PREDICT_V * n, B->total[BK_PREDICT_V], n);
+    B->prof.launches += 6;
+  }
+  int rc;
+  {
+    NvtxRange r("a5 velocity solves (batch)");
+    rc = batch_helm(B, 0, st);
+    if (!rc) rc = batch_helm(B, 1, st);
+  }
+  if (rc) return rc;
+  {
+    NvtxRange r("a6 right-hand side and mass source (batch)");
+    launch_rhs_batch(B->stream, B->d_cases, first + BK_CELLS * n, B->total[BK_CELLS], first + BK_BAND * n,
+                     B->total[BK_BAND], n);
+    B->prof.launches += 3;
+  }
+  {
+    NvtxRange r("a8 pressure solves of the batch");
+    rc = batch_solve(B, thr, st);
+  }
+  if (rc) return rc;
+  // the solve leaves each case's increment in phi (its buffers may have swapped)
+  for (int i = 0; i < n; ++i) {
+    B->h_cases[i].phi = B->cs[i]->phi;
+    B->h_cases[i].phi_store = B->cs[i]->phi2;
+  }
+  {
+    NvtxRange r("a9-a11 forces, projection and divergence (batch)");
+    CUDA_TRY(cudaMemcpyAsync(B->d_cases, B->h_cases, n * sizeof(StepCase), cudaMemcpyHostToDevice, B->stream));
+    launch_forces_batch(B->stream, B->d_cases, n);
+    launch_project_batch(B->stream, B->d_cases, first + BK_CELLS * n, B->total[BK_CELLS], n, B->d_rb);
+    CUDA_TRY(cudaMemcpyAsync(B->h_rb, B->d_rb, n * sizeof(StepReadback), cudaMemcpyDeviceToHost, B->stream));
+    CUDA_TRY(cudaStreamSynchronize(B->stream));
+    CUDA_TRY(cudaGetLastError());
+    B->prof.launches += 5;
+  }
+  for (int i = 0; i < n; ++i) {
+    ibm_ctx* c = B->cs[i];
+    *c->sc_host = B->h_rb[i].sc;
+    std::swap(c->phi, c->phi2);
+    std::swap(c->Hu, c->Huo);
+    std::swap(c->Hv, c->Hvo);
+    c->n += 1;
+    c->prof.steps += 1;
+    c->prof.poisson_sweeps += st[i].sweeps_p;
+    c->prof.helm_sweeps += st[i].sweeps_u + st[i].sweeps_v;
+    st[i].n = c->n;
+    st[i].t = c->n * c->P.dt;
+    st[i].div_max = bits_to_double(c->sc_host->div_bits);
+    st[i].cl = B->h_rb[i].cl;
+    st[i].cd = B->h_rb[i].cd;
+    c->last = st[i];
+  }
+  B->prof.steps += 1;
+  return IBM_OK;
+}
+
 int batch_one_step(ibm_batch* B) {
   const int n = (int)B->cs.size();
+  // cases with a learned or extrapolated warm start, samples or a relative
+  // pressure tolerance take the parts before and after the pressure solve
+  // case by case
+  bool fused = true;
+  for (ibm_ctx* c : B->cs)
+    if (c->ws_mode != 0 || c->ws_base != 0 || c->P.poisson_rtol > 0.0) fused = false;
+  if (fused) return batch_one_step_fused(B);
   std::vector<ibm_step_stats> st(n);
   std::vector<double> thr(n);
   for (int i = 0; i < n; ++i) {
@@ -2111,6 +2321,16 @@ int ibm_batch_create(ibm_ctx* const* cases, int n, ibm_batch** out) {
   ok = ok && cudaMalloc((void**)&B->d_sor, 2 * n * sizeof(Sor32Case)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&B->d_dc, n * sizeof(DcCase)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&B->d_bits, n * sizeof(unsigned long long)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void**)&B->h_cases, n * sizeof(StepCase)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&B->d_cases, n * sizeof(StepCase)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void**)&B->h_first, BK_NUM * n * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&B->d_first, BK_NUM * n * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void**)&B->h_hres, 2 * n * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&B->d_hres, 2 * n * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void**)&B->h_hswp, 3 * n * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&B->d_hswp, 3 * n * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void**)&B->h_rb, n * sizeof(StepReadback)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&B->d_rb, n * sizeof(StepReadback)) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&B->ev_b, cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaEventCreate(&B->t0) == cudaSuccess && cudaEventCreate(&B->t1) == cudaSuccess;
   B->ev.resize(n, nullptr);

@@ -134,6 +134,54 @@ void launch_helm_res(cudaStream_t s, const Geo& g, int grid, const double* x, co
                      const Band& band, const uint8_t* fl, const double* al, double beta, double Ub,
                      unsigned long long* res_bits);
 
+// ---- whole-step batching: one launch covers the blocks of every case
+// All that the step kernels of one case read or write in one step (device
+// pointers and this step's scalars); a batch keeps a table of them on the
+// device.  blocks[k] lists, per kernel kind k, the first block of each case
+// in a launch of that kind (cases in table order).
+struct StepCase {
+  Geo g;
+  Band band;
+  HelmF32 h32;
+  double *u, *v, *p, *Hu, *Hv, *Huo, *Hvo, *Ru, *Rv, *uh, *vh, *b, *phi, *phi_store;
+  double *au, *av, *qband, *rowsum, *partials, *cl_hist, *cd_hist;
+  uint8_t *fu, *fv, *fc;
+  float *hd32, *hr32;
+  const float *hinv_u, *hinv_v;
+  DevScalars* sc;
+  double dt, beta, vb, yb, xb, ea, eb, u_in, chord;
+  float omega_h;
+  int first_step, n, has_body, nelem;
+};
+// kinds of batched launches with case-dependent block counts
+enum BatchKind { BK_BAND = 0, BK_PREDICT_U, BK_PREDICT_V, BK_CELLS, BK_NUM };
+// blocks of one case in a launch of kind k (32 x 8 threads per block)
+int batch_blocks(const StepCase& c, int kind);
+// host copies of the scalars a step reads back, gathered per case
+struct StepReadback {
+  DevScalars sc;
+  double cl, cd;
+};
+void launch_classify_batch(cudaStream_t s, const StepCase* cs, const int* first, int n, int total);
+void launch_outflow_bc_batch(cudaStream_t s, const StepCase* cs, int n);
+void launch_predict_batch(cudaStream_t s, const StepCase* cs, const int* first_u, int total_u, const int* first_v,
+                          int total_v, int n);
+void launch_rhs_batch(cudaStream_t s, const StepCase* cs, const int* first_cells, int total_cells,
+                      const int* first_band, int total_band, int n);
+void launch_forces_batch(cudaStream_t s, const StepCase* cs, int n);
+void launch_project_batch(cudaStream_t s, const StepCase* cs, const int* first_cells, int total_cells, int n,
+                          StepReadback* out);
+// velocity systems of the active cases act[0..na): FP64 residual (norm of
+// case act[k] into bits[k]), d = 0, FP32 half-sweeps, update x += d
+int helm_batch_blocks(const StepCase& c, int grid, int half);
+void launch_helm_dc_res_batch(cudaStream_t s, const StepCase* cs, const int* act, const int* first, int na,
+                              int total, int grid, unsigned long long* bits);
+void launch_helm_zero_batch(cudaStream_t s, const StepCase* cs, const int* act, int na);
+void launch_helm32_half_batch(cudaStream_t s, const StepCase* cs, const int* act, const int* first, int na,
+                              int total, int grid, int colour);
+void launch_helm_add_batch(cudaStream_t s, const StepCase* cs, const int* act, const int* first, int na,
+                           int total, int grid);
+
 // batched mixed-precision solve: one launch over the tiles of many cases
 struct Sor32Case {
   Geo32 g;

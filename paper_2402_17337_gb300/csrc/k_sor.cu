@@ -253,11 +253,11 @@ void launch_helm_res(cudaStream_t s, const Geo& g, int grid, const double* x, co
 // FP64 update x += d follows.  Same stopping rule as the FP64 solve.
 namespace {
 
-__global__ void k_helm_dc_res(Geo g, int grid, const double* __restrict__ x, const double* __restrict__ R, Band B,
+__device__ __forceinline__ void helm_dc_res_body(Geo g, int grid, const double* __restrict__ x, const double* __restrict__ R, Band B,
                               const uint8_t* __restrict__ fl, const double* __restrict__ al, double beta, double Ub,
-                              float* __restrict__ r32, unsigned long long* res_bits) {
+                              float* __restrict__ r32, unsigned long long* res_bits, int bx, int by) {
   HelmCoef h = helm_coef(g, grid);
-  int i = blockIdx.x * blockDim.x + threadIdx.x + h.ilo, j = blockIdx.y * blockDim.y + threadIdx.y + h.jlo;
+  int i = bx * blockDim.x + threadIdx.x + h.ilo, j = by * blockDim.y + threadIdx.y + h.jlo;
   unsigned long long bits = 0ull;
   if (i <= h.ihi && j <= h.jhi) {
     const int P = g.pitch;
@@ -286,15 +286,20 @@ __global__ void k_helm_dc_res(Geo g, int grid, const double* __restrict__ x, con
   }
   warp_block_max(bits, res_bits);
 }
+__global__ void k_helm_dc_res(Geo g, int grid, const double* __restrict__ x, const double* __restrict__ R, Band B,
+                              const uint8_t* __restrict__ fl, const double* __restrict__ al, double beta, double Ub,
+                              float* __restrict__ r32, unsigned long long* res_bits) {
+  helm_dc_res_body(g, grid, x, R, B, fl, al, beta, Ub, r32, res_bits, blockIdx.x, blockIdx.y);
+}
 
-__global__ void k_helm32_half(Geo g, HelmF32 h32, int grid, float* __restrict__ d, const float* __restrict__ r,
+__device__ __forceinline__ void helm32_half_body(Geo g, HelmF32 h32, int grid, float* __restrict__ d, const float* __restrict__ r,
                               const float* __restrict__ invd, Band B, const uint8_t* __restrict__ fl,
-                              const double* __restrict__ al, int colour, float omega, float beta) {
+                              const double* __restrict__ al, int colour, float omega, float beta, int bx, int by) {
   HelmCoef h = helm_coef(g, grid);
   const float *E = grid == 0 ? h32.uE : h32.vE, *W = grid == 0 ? h32.uW : h32.vW;
   const float *N = grid == 0 ? h32.uN : h32.vN, *S = grid == 0 ? h32.uS : h32.vS;
-  int j = blockIdx.y * blockDim.y + threadIdx.y + h.jlo;
-  int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((colour + j) & 1);
+  int j = by * blockDim.y + threadIdx.y + h.jlo;
+  int i = 2 * (bx * blockDim.x + threadIdx.x) + ((colour + j) & 1);
   if (j > h.jhi || i > h.ihi || i < h.ilo) return;
   const int P = g.pitch;
   size_t c = at(i, j, P);
@@ -321,16 +326,98 @@ __global__ void k_helm32_half(Geo g, HelmF32 h32, int grid, float* __restrict__ 
   float dp = d[c];
   d[c] = fmaf(omega, gs - dp, dp);
 }
+__global__ void k_helm32_half(Geo g, HelmF32 h32, int grid, float* __restrict__ d, const float* __restrict__ r,
+                              const float* __restrict__ invd, Band B, const uint8_t* __restrict__ fl,
+                              const double* __restrict__ al, int colour, float omega, float beta) {
+  helm32_half_body(g, h32, grid, d, r, invd, B, fl, al, colour, omega, beta, blockIdx.x, blockIdx.y);
+}
 
-__global__ void k_helm_add(Geo g, int grid, double* __restrict__ x, const float* __restrict__ d) {
+__device__ __forceinline__ void helm_add_body(Geo g, int grid, double* __restrict__ x, const float* __restrict__ d, int bx, int by) {
   HelmCoef h = helm_coef(g, grid);
-  int i = blockIdx.x * blockDim.x + threadIdx.x + h.ilo, j = blockIdx.y * blockDim.y + threadIdx.y + h.jlo;
+  int i = bx * blockDim.x + threadIdx.x + h.ilo, j = by * blockDim.y + threadIdx.y + h.jlo;
   if (i > h.ihi || j > h.jhi) return;
   size_t c = at(i, j, g.pitch);
   x[c] += (double)d[c];
 }
+__global__ void k_helm_add(Geo g, int grid, double* __restrict__ x, const float* __restrict__ d) {
+  helm_add_body(g, grid, x, d, blockIdx.x, blockIdx.y);
+}
+
+// ---- batched forms over the active cases act[0..na) of a batch (block b
+// belongs to active slot k with first[k] <= b < first[k+1]; the grids are
+// those of the single-case launches below)
+__device__ inline int slot_of(const int* __restrict__ first, int na, int b) {
+  int lo = 0, hi = na - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// unknown nodes of grid 0 (u) or 1 (v) along x
+__device__ inline int helm_ni(const Geo& g, int grid) { return grid == 0 ? g.nx - 1 : g.nx; }
+
+__global__ void k_helm_dc_res_batch(const StepCase* __restrict__ cs, const int* __restrict__ act,
+                                    const int* __restrict__ first, int na, int grid,
+                                    unsigned long long* __restrict__ bits) {
+  const int k = slot_of(first, na, blockIdx.x);
+  const StepCase& s = cs[act[k]];
+  const int t = blockIdx.x - first[k], bxn = (helm_ni(s.g, grid) + TBX - 1) / TBX;
+  helm_dc_res_body(s.g, grid, grid == 0 ? s.uh : s.vh, grid == 0 ? s.Ru : s.Rv, s.band, grid == 0 ? s.fu : s.fv,
+                   grid == 0 ? s.au : s.av, s.beta, grid == 0 ? 0.0 : s.vb, s.hr32, bits + k, t % bxn, t / bxn);
+}
+
+// d = 0 over a case's pitched field (64 blocks of 256 threads per case)
+__global__ void k_helm_zero_batch(const StepCase* __restrict__ cs, const int* __restrict__ act) {
+  const StepCase& s = cs[act[blockIdx.x / 64]];
+  for (int e = (blockIdx.x % 64) * 256 + threadIdx.x; e < s.nelem; e += 64 * 256) s.hd32[e] = 0.f;
+}
+
+__global__ void k_helm32_half_batch(const StepCase* __restrict__ cs, const int* __restrict__ act,
+                                    const int* __restrict__ first, int na, int grid, int colour) {
+  const int k = slot_of(first, na, blockIdx.x);
+  const StepCase& s = cs[act[k]];
+  const int t = blockIdx.x - first[k], bxn = ((helm_ni(s.g, grid) + 1) / 2 + TBX - 1) / TBX;
+  helm32_half_body(s.g, s.h32, grid, s.hd32, s.hr32, grid == 0 ? s.hinv_u : s.hinv_v, s.band,
+                   grid == 0 ? s.fu : s.fv, grid == 0 ? s.au : s.av, colour, s.omega_h, (float)s.beta, t % bxn,
+                   t / bxn);
+}
+
+__global__ void k_helm_add_batch(const StepCase* __restrict__ cs, const int* __restrict__ act,
+                                 const int* __restrict__ first, int na, int grid) {
+  const int k = slot_of(first, na, blockIdx.x);
+  const StepCase& s = cs[act[k]];
+  const int t = blockIdx.x - first[k], bxn = (helm_ni(s.g, grid) + TBX - 1) / TBX;
+  helm_add_body(s.g, grid, grid == 0 ? s.uh : s.vh, s.hd32, t % bxn, t / bxn);
+}
 
 }  // namespace
+
+int helm_batch_blocks(const StepCase& c, int grid, int half) {
+  const int ni = grid == 0 ? c.g.nx - 1 : c.g.nx, nj = grid == 0 ? c.g.ny : c.g.ny - 1;
+  const int cols = half ? (ni + 1) / 2 : ni;
+  return ((cols + TBX - 1) / TBX) * ((nj + TBY - 1) / TBY);
+}
+
+void launch_helm_dc_res_batch(cudaStream_t s, const StepCase* cs, const int* act, const int* first, int na,
+                              int total, int grid, unsigned long long* bits) {
+  k_helm_dc_res_batch<<<total, dim3(TBX, TBY), 0, s>>>(cs, act, first, na, grid, bits);
+}
+
+void launch_helm_zero_batch(cudaStream_t s, const StepCase* cs, const int* act, int na) {
+  k_helm_zero_batch<<<na * 64, 256, 0, s>>>(cs, act);
+}
+
+void launch_helm32_half_batch(cudaStream_t s, const StepCase* cs, const int* act, const int* first, int na,
+                              int total, int grid, int colour) {
+  k_helm32_half_batch<<<total, dim3(TBX, TBY), 0, s>>>(cs, act, first, na, grid, colour);
+}
+
+void launch_helm_add_batch(cudaStream_t s, const StepCase* cs, const int* act, const int* first, int na,
+                           int total, int grid) {
+  k_helm_add_batch<<<total, dim3(TBX, TBY), 0, s>>>(cs, act, first, na, grid);
+}
 
 void launch_helm_dc_res(cudaStream_t s, const Geo& g, int grid, const double* x, const double* R, const Band& band,
                         const uint8_t* fl, const double* al, double beta, double Ub, float* r32,

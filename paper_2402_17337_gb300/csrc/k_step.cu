@@ -72,8 +72,8 @@ __device__ inline void block_max_bits(unsigned long long v, unsigned long long* 
 
 // Inflow u = u_in; convective outflow du/dt + u_in du/dx = 0 by explicit Euler,
 // then a uniform shift so that the outflow flux equals the inflow flux.
-__global__ void k_outflow_bc(Geo g, const double* __restrict__ u, double* __restrict__ uh, double u_in,
-                             double dt) {
+__device__ __forceinline__ void outflow_bc_body(Geo g, const double* __restrict__ u, double* __restrict__ uh, double u_in,
+                             double dt, int bx, int by) {
   const int nx = g.nx, ny = g.ny, P = g.pitch;
   // convective update, one row per thread
   for (int j = threadIdx.x; j < ny; j += blockDim.x) {
@@ -112,13 +112,17 @@ __global__ void k_outflow_bc(Geo g, const double* __restrict__ u, double* __rest
   __syncthreads();
   for (int j = threadIdx.x; j < ny; j += blockDim.x) uh[at(nx, j, P)] += corr;
 }
+__global__ void k_outflow_bc(Geo g, const double* __restrict__ u, double* __restrict__ uh, double u_in,
+                             double dt) {
+  outflow_bc_body(g, u, uh, u_in, dt, blockIdx.x, blockIdx.y);
+}
 
 // ---------------------------------------------------------- classification
 
-__global__ void k_classify_solid(Geo g, Band B, double xb, double yb, double a, double b,
+__device__ __forceinline__ void classify_solid_body(Geo g, Band B, double xb, double yb, double a, double b,
                                  uint8_t* __restrict__ fu, uint8_t* __restrict__ fv, uint8_t* __restrict__ fc,
-                                 double* __restrict__ au, double* __restrict__ av) {
-  int bi = blockIdx.x * blockDim.x + threadIdx.x, bj = blockIdx.y * blockDim.y + threadIdx.y;
+                                 double* __restrict__ au, double* __restrict__ av, int bx, int by) {
+  int bi = bx * blockDim.x + threadIdx.x, bj = by * blockDim.y + threadIdx.y;
   if (bi >= B.w || bj >= B.h) return;
   int i = B.i0 + bi, j = B.j0 + bj, k = bj * B.w + bi;
   const int nx = g.nx, ny = g.ny;
@@ -130,6 +134,11 @@ __global__ void k_classify_solid(Geo g, Band B, double xb, double yb, double a, 
   fc[k] = sc ? 1 : 0;
   au[k] = 0.0;
   av[k] = 0.0;
+}
+__global__ void k_classify_solid(Geo g, Band B, double xb, double yb, double a, double b,
+                                 uint8_t* __restrict__ fu, uint8_t* __restrict__ fv, uint8_t* __restrict__ fc,
+                                 double* __restrict__ au, double* __restrict__ av) {
+  classify_solid_body(g, B, xb, yb, a, b, fu, fv, fc, au, av, blockIdx.x, blockIdx.y);
 }
 
 __device__ inline bool band_solid(const uint8_t* f, const Band& B, int i, int j) {
@@ -148,9 +157,9 @@ __device__ inline bool band_has_solid_nb(const uint8_t* f, const Band& B, int i,
 // the node takes u_F = U_b + alpha (u_opp - U_b), alpha = d / (d + D), with
 // u_opp the node on the far side at distance D.  alpha = 0 (u_F = U_b) when
 // that node is solid, a forcing node, or not an unknown of the grid.
-__global__ void k_classify_forcing(Geo g, Band B, int grid, double xb, double yb, double a, double b,
-                                   uint8_t* __restrict__ fl, double* __restrict__ al) {
-  int bi = blockIdx.x * blockDim.x + threadIdx.x, bj = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void classify_forcing_body(Geo g, Band B, int grid, double xb, double yb, double a, double b,
+                                   uint8_t* __restrict__ fl, double* __restrict__ al, int bx, int by) {
+  int bi = bx * blockDim.x + threadIdx.x, bj = by * blockDim.y + threadIdx.y;
   if (bi >= B.w || bj >= B.h) return;
   int i = B.i0 + bi, j = B.j0 + bj, k = bj * B.w + bi;
   const int nx = g.nx, ny = g.ny;
@@ -209,6 +218,10 @@ __global__ void k_classify_forcing(Geo g, Band B, int grid, double xb, double yb
   fl[k] = (uint8_t)(K_FORCE | (bd << 2));
   al[k] = alpha;
 }
+__global__ void k_classify_forcing(Geo g, Band B, int grid, double xb, double yb, double a, double b,
+                                   uint8_t* __restrict__ fl, double* __restrict__ al) {
+  classify_forcing_body(g, B, grid, xb, yb, a, b, fl, al, blockIdx.x, blockIdx.y);
+}
 
 // ------------------------------------------------------- explicit predictor
 
@@ -223,11 +236,11 @@ __device__ inline double lap5(double aE, double aW, double aN, double aS, double
 }
 
 // u node (i = 1..nx-1, j = 0..ny-1): control volume [xc_{i-1}, xc_i] x [yf_j, yf_{j+1}]
-__global__ void k_predict_u(Geo g, const double* __restrict__ u, const double* __restrict__ v,
+__device__ __forceinline__ void predict_u_body(Geo g, const double* __restrict__ u, const double* __restrict__ v,
                             const double* __restrict__ p, double* __restrict__ Hu,
                             const double* __restrict__ Huo, double* __restrict__ Ru, double* __restrict__ uh,
-                            Band B, const uint8_t* __restrict__ fu, double dt, double beta, int first) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y * blockDim.y + threadIdx.y;
+                            Band B, const uint8_t* __restrict__ fu, double dt, double beta, int first, int bx, int by) {
+  int i = bx * blockDim.x + threadIdx.x + 1, j = by * blockDim.y + threadIdx.y;
   if (i > g.nx - 1 || j > g.ny - 1) return;
   const int P = g.pitch;
   size_t c = at(i, j, P);
@@ -249,14 +262,20 @@ __global__ void k_predict_u(Geo g, const double* __restrict__ u, const double* _
   int k = band_index(B, i, j);
   uh[c] = (k >= 0 && (fu[k] & 3) == K_SOLID) ? 0.0 : uP;
 }
+__global__ void k_predict_u(Geo g, const double* __restrict__ u, const double* __restrict__ v,
+                            const double* __restrict__ p, double* __restrict__ Hu,
+                            const double* __restrict__ Huo, double* __restrict__ Ru, double* __restrict__ uh,
+                            Band B, const uint8_t* __restrict__ fu, double dt, double beta, int first) {
+  predict_u_body(g, u, v, p, Hu, Huo, Ru, uh, B, fu, dt, beta, first, blockIdx.x, blockIdx.y);
+}
 
 // v node (i = 0..nx-1, j = 1..ny-1): control volume [xf_i, xf_{i+1}] x [yc_{j-1}, yc_j]
-__global__ void k_predict_v(Geo g, const double* __restrict__ u, const double* __restrict__ v,
+__device__ __forceinline__ void predict_v_body(Geo g, const double* __restrict__ u, const double* __restrict__ v,
                             const double* __restrict__ p, double* __restrict__ Hv,
                             const double* __restrict__ Hvo, double* __restrict__ Rv, double* __restrict__ vh,
                             Band B, const uint8_t* __restrict__ fv, double dt, double beta, double vb,
-                            int first) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+                            int first, int bx, int by) {
+  int i = bx * blockDim.x + threadIdx.x, j = by * blockDim.y + threadIdx.y + 1;
   if (i > g.nx - 1 || j > g.ny - 1) return;
   const int P = g.pitch;
   size_t c = at(i, j, P);
@@ -277,17 +296,28 @@ __global__ void k_predict_v(Geo g, const double* __restrict__ u, const double* _
   int k = band_index(B, i, j);
   vh[c] = (k >= 0 && (fv[k] & 3) == K_SOLID) ? vb : vP;
 }
+__global__ void k_predict_v(Geo g, const double* __restrict__ u, const double* __restrict__ v,
+                            const double* __restrict__ p, double* __restrict__ Hv,
+                            const double* __restrict__ Hvo, double* __restrict__ Rv, double* __restrict__ vh,
+                            Band B, const uint8_t* __restrict__ fv, double dt, double beta, double vb,
+                            int first) {
+  predict_v_body(g, u, v, p, Hv, Hvo, Rv, vh, B, fv, dt, beta, vb, first, blockIdx.x, blockIdx.y);
+}
 
 // ------------------------------------------------- right-hand side and q
 
-__global__ void k_rhs(Geo g, const double* __restrict__ uh, const double* __restrict__ vh, double* __restrict__ b,
-                      double idt) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void rhs_body(Geo g, const double* __restrict__ uh, const double* __restrict__ vh, double* __restrict__ b,
+                      double idt, int bx, int by) {
+  int i = bx * blockDim.x + threadIdx.x, j = by * blockDim.y + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
   const int P = g.pitch;
   size_t c = at(i, j, P);
   double D = (uh[c + 1] - uh[c]) * g.idx[i] + (vh[c + P] - vh[c]) * g.idy[j];
   b[c] = D * idt;
+}
+__global__ void k_rhs(Geo g, const double* __restrict__ uh, const double* __restrict__ vh, double* __restrict__ b,
+                      double idt) {
+  rhs_body(g, uh, vh, b, idt, blockIdx.x, blockIdx.y);
 }
 
 __device__ inline double cell_div(const Geo& g, const double* uh, const double* vh, int i, int j) {
@@ -298,8 +328,8 @@ __device__ inline double cell_div(const Geo& g, const double* uh, const double* 
 // sum of D V and of V over body cells: one thread per band row sums along
 // the row in order, then one thread sums the row sums in order (the mean
 // feeds back into the flow, so the order of the additions is fixed)
-__global__ void k_body_sums(Geo g, Band B, const uint8_t* __restrict__ fc, const double* __restrict__ uh,
-                            const double* __restrict__ vh, double* __restrict__ rowsum, DevScalars* sc) {
+__device__ __forceinline__ void body_sums_body(Geo g, Band B, const uint8_t* __restrict__ fc, const double* __restrict__ uh,
+                            const double* __restrict__ vh, double* __restrict__ rowsum, DevScalars* sc, int bx, int by) {
   for (int bj = threadIdx.x; bj < B.h; bj += blockDim.x) {
     double a = 0.0, b = 0.0;
     const int j = B.j0 + bj;
@@ -324,13 +354,17 @@ __global__ void k_body_sums(Geo g, Band B, const uint8_t* __restrict__ fc, const
   sc->body_sum[1] = sv;
   sc->cbar = sv > 0.0 ? sdv / sv : 0.0;
 }
+__global__ void k_body_sums(Geo g, Band B, const uint8_t* __restrict__ fc, const double* __restrict__ uh,
+                            const double* __restrict__ vh, double* __restrict__ rowsum, DevScalars* sc) {
+  body_sums_body(g, B, fc, uh, vh, rowsum, sc, blockIdx.x, blockIdx.y);
+}
 
 // On body cells (centre inside the body) continuity is replaced by div u = q,
 // q = D(uhat) - cbar, cbar the mean over those cells (zero net source).
-__global__ void k_body_fix(Geo g, Band B, const uint8_t* __restrict__ fc, const double* __restrict__ uh,
+__device__ __forceinline__ void body_fix_body(Geo g, Band B, const uint8_t* __restrict__ fc, const double* __restrict__ uh,
                            const double* __restrict__ vh, double* __restrict__ b, double* __restrict__ qband,
-                           double idt, const DevScalars* __restrict__ sc) {
-  int bi = blockIdx.x * blockDim.x + threadIdx.x, bj = blockIdx.y * blockDim.y + threadIdx.y;
+                           double idt, const DevScalars* __restrict__ sc, int bx, int by) {
+  int bi = bx * blockDim.x + threadIdx.x, bj = by * blockDim.y + threadIdx.y;
   if (bi >= B.w || bj >= B.h) return;
   int k = bj * B.w + bi;
   if (!fc[k]) {
@@ -343,18 +377,23 @@ __global__ void k_body_fix(Geo g, Band B, const uint8_t* __restrict__ fc, const 
   qband[k] = q;
   b[at(i, j, g.pitch)] = (D - q) * idt;
 }
+__global__ void k_body_fix(Geo g, Band B, const uint8_t* __restrict__ fc, const double* __restrict__ uh,
+                           const double* __restrict__ vh, double* __restrict__ b, double* __restrict__ qband,
+                           double idt, const DevScalars* __restrict__ sc) {
+  body_fix_body(g, B, fc, uh, vh, b, qband, idt, sc, blockIdx.x, blockIdx.y);
+}
 
 // ------------------------------------------------------------------ forces
 
 // f = ((I - beta L) uhat - R) / dt on solid and forcing nodes;
 // F = -sum f dV + d/dt sum_solid uhat dV;  C_d = 2 F_x / c, C_l = 2 F_y / c.
-__global__ void k_force_partials(Geo g, Band B, const uint8_t* __restrict__ fu, const uint8_t* __restrict__ fv,
+__device__ __forceinline__ void force_partials_body(Geo g, Band B, const uint8_t* __restrict__ fu, const uint8_t* __restrict__ fv,
                                  const double* __restrict__ uh, const double* __restrict__ vh,
                                  const double* __restrict__ Ru, const double* __restrict__ Rv, double beta,
-                                 double idt, double* __restrict__ partials) {
+                                 double idt, double* __restrict__ partials, int bx, int by, int nblk) {
   double acc[4] = {0.0, 0.0, 0.0, 0.0};  // fx dV, fy dV, Sx, Sy
   const int P = g.pitch;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < B.w * B.h; k += gridDim.x * blockDim.x) {
+  for (int k = bx * blockDim.x + threadIdx.x; k < B.w * B.h; k += nblk * blockDim.x) {
     int i = B.i0 + k % B.w, j = B.j0 + k / B.w;
     size_t c = at(i, j, P);
     int ku = fu[k] & 3;
@@ -379,11 +418,17 @@ __global__ void k_force_partials(Geo g, Band B, const uint8_t* __restrict__ fu, 
   double out[4];
   block_sum<4>(acc, out);
   if (threadIdx.x == 0)
-    for (int q = 0; q < 4; ++q) partials[4 * blockIdx.x + q] = out[q];
+    for (int q = 0; q < 4; ++q) partials[4 * bx + q] = out[q];
+}
+__global__ void k_force_partials(Geo g, Band B, const uint8_t* __restrict__ fu, const uint8_t* __restrict__ fv,
+                                 const double* __restrict__ uh, const double* __restrict__ vh,
+                                 const double* __restrict__ Ru, const double* __restrict__ Rv, double beta,
+                                 double idt, double* __restrict__ partials) {
+  force_partials_body(g, B, fu, fv, uh, vh, Ru, Rv, beta, idt, partials, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
-__global__ void k_force_final(const double* __restrict__ partials, int nblk, double idt, double chord,
-                              DevScalars* sc, double* cl_hist, double* cd_hist, int n) {
+__device__ __forceinline__ void force_final_body(const double* __restrict__ partials, int nblk, double idt, double chord,
+                              DevScalars* sc, double* cl_hist, double* cd_hist, int n, int bx, int by) {
   if (threadIdx.x != 0) return;
   double s[4] = {0.0, 0.0, 0.0, 0.0};
   for (int k = 0; k < nblk; ++k)
@@ -396,6 +441,10 @@ __global__ void k_force_final(const double* __restrict__ partials, int nblk, dou
   sc->force[1] = Fy;
   cd_hist[n] = 2.0 * Fx / chord;
   cl_hist[n] = 2.0 * Fy / chord;
+}
+__global__ void k_force_final(const double* __restrict__ partials, int nblk, double idt, double chord,
+                              DevScalars* sc, double* cl_hist, double* cd_hist, int n) {
+  force_final_body(partials, nblk, idt, chord, sc, cl_hist, cd_hist, n, blockIdx.x, blockIdx.y);
 }
 
 __global__ void k_body_momentum0(Geo g, Band B, const uint8_t* __restrict__ fv, double vb,
@@ -421,18 +470,21 @@ __global__ void k_body_momentum0_final(const double* __restrict__ partials, int 
 
 // -------------------------------------------------------------- projection
 
+__device__ __forceinline__ void phi_ref_body(Geo g, const double* __restrict__ phi, DevScalars* sc, int bx, int by) {
+  if (threadIdx.x == 0 && bx == 0) sc->phi_ref = phi[at(g.nx - 1, 0, g.pitch)];
+}
 __global__ void k_phi_ref(Geo g, const double* __restrict__ phi, DevScalars* sc) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) sc->phi_ref = phi[at(g.nx - 1, 0, g.pitch)];
+  phi_ref_body(g, phi, sc, blockIdx.x, blockIdx.y);
 }
 
 // u = uhat - dt G phi on interior faces (boundary faces keep uhat), p += phi,
 // the stored increment is shifted so that the gauge cell (nx-1, 0) is zero,
 // and max |div u| is taken over cells whose centre is in the fluid.
-__global__ void k_project(Geo g, const double* __restrict__ uh, const double* __restrict__ vh,
+__device__ __forceinline__ void project_body(Geo g, const double* __restrict__ uh, const double* __restrict__ vh,
                           const double* __restrict__ phi, double* __restrict__ u, double* __restrict__ v,
                           double* __restrict__ p, double* __restrict__ phi_store, Band B,
-                          const uint8_t* __restrict__ fc, double dt, DevScalars* sc) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+                          const uint8_t* __restrict__ fc, double dt, DevScalars* sc, int bx, int by) {
+  int i = bx * blockDim.x + threadIdx.x, j = by * blockDim.y + threadIdx.y;
   const int nx = g.nx, ny = g.ny, P = g.pitch;
   unsigned long long bits = 0ull;
   if (i < nx && j < ny) {
@@ -457,6 +509,129 @@ __global__ void k_project(Geo g, const double* __restrict__ uh, const double* __
     }
   }
   block_max_bits(bits, &sc->div_bits);
+}
+__global__ void k_project(Geo g, const double* __restrict__ uh, const double* __restrict__ vh,
+                          const double* __restrict__ phi, double* __restrict__ u, double* __restrict__ v,
+                          double* __restrict__ p, double* __restrict__ phi_store, Band B,
+                          const uint8_t* __restrict__ fc, double dt, DevScalars* sc) {
+  project_body(g, uh, vh, phi, u, v, p, phi_store, B, fc, dt, sc, blockIdx.x, blockIdx.y);
+}
+
+// ------------------------------------------------------- batched forms
+// One launch covers the blocks of every case of a batch: block b belongs to
+// the case whose range [first[c], first[c+1]) holds it, and runs the same
+// body as the single-case kernel with that case's arguments and its block
+// coordinates within the case's own grid (32 x 8 threads, as above).
+
+// the last case c with first[c] <= b
+__device__ inline int case_of(const int* __restrict__ first, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ inline int blocks_in_x(int n) { return (n + TBX - 1) / TBX; }
+
+// pass 0: solid nodes and body cells; 1, 2: forcing nodes of the u and v grids
+__global__ void k_classify_batch(const StepCase* __restrict__ cs, const int* __restrict__ first, int n, int pass) {
+  const int c = case_of(first, n, blockIdx.x);
+  const StepCase& s = cs[c];
+  if (!s.has_body) return;
+  const int t = blockIdx.x - first[c], bxn = blocks_in_x(s.band.w);
+  if (pass == 0)
+    classify_solid_body(s.g, s.band, s.xb, s.yb, s.ea, s.eb, s.fu, s.fv, s.fc, s.au, s.av, t % bxn, t / bxn);
+  else
+    classify_forcing_body(s.g, s.band, pass - 1, s.xb, s.yb, s.ea, s.eb, pass == 1 ? s.fu : s.fv,
+                          pass == 1 ? s.au : s.av, t % bxn, t / bxn);
+}
+
+// one block per case
+__global__ void k_outflow_bc_batch(const StepCase* __restrict__ cs) {
+  const StepCase& s = cs[blockIdx.x];
+  if (s.g.bc == 0) outflow_bc_body(s.g, s.u, s.uh, s.u_in, s.dt, 0, 0);
+}
+
+__global__ void k_predict_u_batch(const StepCase* __restrict__ cs, const int* __restrict__ first, int n) {
+  const int c = case_of(first, n, blockIdx.x);
+  const StepCase& s = cs[c];
+  const int t = blockIdx.x - first[c], bxn = blocks_in_x(s.g.nx - 1);
+  predict_u_body(s.g, s.u, s.v, s.p, s.Hu, s.Huo, s.Ru, s.uh, s.band, s.fu, s.dt, s.beta, s.first_step, t % bxn,
+                 t / bxn);
+}
+
+__global__ void k_predict_v_batch(const StepCase* __restrict__ cs, const int* __restrict__ first, int n) {
+  const int c = case_of(first, n, blockIdx.x);
+  const StepCase& s = cs[c];
+  const int t = blockIdx.x - first[c], bxn = blocks_in_x(s.g.nx);
+  predict_v_body(s.g, s.u, s.v, s.p, s.Hv, s.Hvo, s.Rv, s.vh, s.band, s.fv, s.dt, s.beta, s.vb, s.first_step,
+                 t % bxn, t / bxn);
+}
+
+__global__ void k_rhs_batch(const StepCase* __restrict__ cs, const int* __restrict__ first, int n) {
+  const int c = case_of(first, n, blockIdx.x);
+  const StepCase& s = cs[c];
+  const int t = blockIdx.x - first[c], bxn = blocks_in_x(s.g.nx);
+  rhs_body(s.g, s.uh, s.vh, s.b, 1.0 / s.dt, t % bxn, t / bxn);
+}
+
+// one block of 1024 threads per case
+__global__ void k_body_sums_batch(const StepCase* __restrict__ cs) {
+  const StepCase& s = cs[blockIdx.x];
+  if (s.has_body) body_sums_body(s.g, s.band, s.fc, s.uh, s.vh, s.rowsum, s.sc, 0, 0);
+}
+
+__global__ void k_body_fix_batch(const StepCase* __restrict__ cs, const int* __restrict__ first, int n) {
+  const int c = case_of(first, n, blockIdx.x);
+  const StepCase& s = cs[c];
+  if (!s.has_body) return;
+  const int t = blockIdx.x - first[c], bxn = blocks_in_x(s.band.w);
+  body_fix_body(s.g, s.band, s.fc, s.uh, s.vh, s.b, s.qband, 1.0 / s.dt, s.sc, t % bxn, t / bxn);
+}
+
+// RED_BLOCKS blocks of 256 threads per case
+__global__ void k_force_partials_batch(const StepCase* __restrict__ cs) {
+  const StepCase& s = cs[blockIdx.x / RED_BLOCKS];
+  if (s.has_body)
+    force_partials_body(s.g, s.band, s.fu, s.fv, s.uh, s.vh, s.Ru, s.Rv, s.beta, 1.0 / s.dt, s.partials,
+                        blockIdx.x % RED_BLOCKS, 0, RED_BLOCKS);
+}
+
+// one block of 32 threads per case; a case without a body has no force
+__global__ void k_force_final_batch(const StepCase* __restrict__ cs) {
+  const StepCase& s = cs[blockIdx.x];
+  if (s.has_body) {
+    force_final_body(s.partials, RED_BLOCKS, 1.0 / s.dt, s.chord, s.sc, s.cl_hist, s.cd_hist, s.n, 0, 0);
+  } else if (threadIdx.x == 0) {
+    s.cl_hist[s.n] = 0.0;
+    s.cd_hist[s.n] = 0.0;
+  }
+}
+
+// one block of 32 threads per case: the gauge value, and the divergence
+// maximum cleared before the projection accumulates it
+__global__ void k_phi_ref_batch(const StepCase* __restrict__ cs) {
+  const StepCase& s = cs[blockIdx.x];
+  phi_ref_body(s.g, s.phi, s.sc, 0, 0);
+  if (threadIdx.x == 0) s.sc->div_bits = 0ull;
+}
+
+__global__ void k_project_batch(const StepCase* __restrict__ cs, const int* __restrict__ first, int n) {
+  const int c = case_of(first, n, blockIdx.x);
+  const StepCase& s = cs[c];
+  const int t = blockIdx.x - first[c], bxn = blocks_in_x(s.g.nx);
+  project_body(s.g, s.uh, s.vh, s.phi, s.u, s.v, s.p, s.phi_store, s.band, s.fc, s.dt, s.sc, t % bxn, t / bxn);
+}
+
+// the scalars each case's step reads back, gathered for one copy to the host
+__global__ void k_gather_batch(const StepCase* __restrict__ cs, StepReadback* __restrict__ out) {
+  const StepCase& s = cs[blockIdx.x];
+  if (threadIdx.x != 0) return;
+  out[blockIdx.x].sc = *s.sc;
+  out[blockIdx.x].cl = s.cl_hist[s.n];
+  out[blockIdx.x].cd = s.cd_hist[s.n];
 }
 
 inline dim3 grid2(int nx, int ny) { return dim3((nx + TBX - 1) / TBX, (ny + TBY - 1) / TBY); }
@@ -519,6 +694,53 @@ void launch_project(cudaStream_t s, const Geo& g, const double* uh, const double
                     double* v, double* p, double* phi_store, const Band& band, const uint8_t* fc, double dt,
                     DevScalars* sc) {
   k_project<<<grid2(g.nx, g.ny), dim3(TBX, TBY), 0, s>>>(g, uh, vh, phi, u, v, p, phi_store, band, fc, dt, sc);
+}
+
+}  // namespace ibm
+
+namespace ibm {
+
+int batch_blocks(const StepCase& c, int kind) {
+  auto g2 = [](int nx, int ny) { return ((nx + 31) / 32) * ((ny + 7) / 8); };
+  switch (kind) {
+    case BK_BAND: return g2(c.band.w, c.band.h);
+    case BK_PREDICT_U: return g2(c.g.nx - 1, c.g.ny);
+    case BK_PREDICT_V: return g2(c.g.nx, c.g.ny - 1);
+    default: return g2(c.g.nx, c.g.ny);
+  }
+}
+
+void launch_classify_batch(cudaStream_t s, const StepCase* cs, const int* first, int n, int total) {
+  for (int pass = 0; pass < 3; ++pass) k_classify_batch<<<total, dim3(TBX, TBY), 0, s>>>(cs, first, n, pass);
+}
+
+void launch_outflow_bc_batch(cudaStream_t s, const StepCase* cs, int n) {
+  k_outflow_bc_batch<<<n, 256, 0, s>>>(cs);
+}
+
+void launch_predict_batch(cudaStream_t s, const StepCase* cs, const int* first_u, int total_u, const int* first_v,
+                          int total_v, int n) {
+  k_predict_u_batch<<<total_u, dim3(TBX, TBY), 0, s>>>(cs, first_u, n);
+  k_predict_v_batch<<<total_v, dim3(TBX, TBY), 0, s>>>(cs, first_v, n);
+}
+
+void launch_rhs_batch(cudaStream_t s, const StepCase* cs, const int* first_cells, int total_cells,
+                      const int* first_band, int total_band, int n) {
+  k_rhs_batch<<<total_cells, dim3(TBX, TBY), 0, s>>>(cs, first_cells, n);
+  k_body_sums_batch<<<n, 1024, 0, s>>>(cs);
+  k_body_fix_batch<<<total_band, dim3(TBX, TBY), 0, s>>>(cs, first_band, n);
+}
+
+void launch_forces_batch(cudaStream_t s, const StepCase* cs, int n) {
+  k_force_partials_batch<<<n * RED_BLOCKS, 256, 0, s>>>(cs);
+  k_force_final_batch<<<n, 32, 0, s>>>(cs);
+}
+
+void launch_project_batch(cudaStream_t s, const StepCase* cs, const int* first_cells, int total_cells, int n,
+                          StepReadback* out) {
+  k_phi_ref_batch<<<n, 32, 0, s>>>(cs);
+  k_project_batch<<<total_cells, dim3(TBX, TBY), 0, s>>>(cs, first_cells, n);
+  k_gather_batch<<<n, 32, 0, s>>>(cs, out);
 }
 
 }  // namespace ibm

@@ -124,3 +124,35 @@ def test_full_size_batch_cases_agree_with_single_context_runs():
         assert max(errs.values()) <= MIXED_TOL, (c.name, errs)
         alone.close()
     B.close()
+
+
+def test_fused_batch_step_matches_single_contexts_bit_for_bit_before_the_pressure_solve():
+    """A batch step runs classification, boundary values, predictor, velocity
+    solves, right-hand side, forces and projection as shared launches over
+    all cases.  Up to the pressure solve a case's arithmetic is that of the
+    single-context step, so after one step from the same state the
+    intermediate velocities and right-hand sides (uh, vh, R_u, R_v), the
+    node kinds and the forces (computed from those) are equal bit for bit,
+    and so are the velocity sweep counts.  Small cases of the batch recipe
+    and two full-size cases with ragged tiles."""
+    from paper_2402_17337_gb300 import Batch, build
+    build.build()
+    cfgs = W.batch_small(4) + W.batch64()[:2]
+    ss = solvers(cfgs)
+    B = Batch(ss)
+    st = B.step(1)
+    for c, s, x in zip(cfgs, ss, st):
+        (alone,) = solvers([c])
+        a = alone.step(1)
+        assert (x["sweeps_u"], x["sweeps_v"]) == (a["sweeps_u"], a["sweeps_v"]), c.name
+        for f in ("uh", "vh", "Ru", "Rv"):
+            assert np.array_equal(s.get(f), alone.get(f)), (c.name, f)
+        for grid in (0, 1, 2):
+            fa, fb = s.flags(grid), alone.flags(grid)
+            for ka, kb in zip(fa if isinstance(fa, tuple) else (fa,), fb if isinstance(fb, tuple) else (fb,)):
+                assert np.array_equal(ka, kb), (c.name, grid)
+        (cl, cd), (cl0, cd0) = s.forces(), alone.forces()
+        assert np.array_equal(cl, cl0) and np.array_equal(cd, cd0), c.name
+        assert x["div_max"] <= c.div_tol * 1.001
+        alone.close()
+    B.close()

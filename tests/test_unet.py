@@ -191,17 +191,20 @@ def test_gpu_unet_matches_oracle_bit_for_bit_in_the_exact_regime(case):
 # ------------------------------------------------------------ realistic weights
 #
 # He-initialised weights and random features at the sizes the warm start
-# uses.  Here storing activations and gradients in BF16 rounds them (unit
-# roundoff 2^-8), and the GPU's FP32 sums round in another order than the
-# oracle's FP64 ones, so single roundings flip between the two and each
-# result carries the perturbations of the stored operands it sums.  Element by
-# element the difference is bounded by a few BF16 units of the sum of the
-# magnitudes of the terms that make the element (the head convolution's terms
-# for the output; x * g over all pixels for a weight gradient, g for a bias
-# gradient), which the oracle computes from the operands it used:
-#     |gpu - oracle| <= C 2^-8 sum |terms|,  C = 16
-# (16 BF16 units: the operands of the deepest layer have passed about that
-# many BF16 stores).
+# uses.  Storing activations and gradients in BF16 rounds them (unit roundoff
+# 2^-8), and the GPU's FP32 sums round in another order than the oracle's FP64
+# ones, so single roundings flip between the two.  The output is within a few
+# BF16 units of the magnitudes of the head convolution's terms, element by
+# element:  |out - out_oracle| <= C 2^-8 sum |terms|, C = 16 (measured <= 0.64).
+# The gradients are not bounded that way element by element: where a stored
+# activation lies within a rounding of zero, its ReLU mask differs between
+# the two, and the whole gradient through that element changes.  Such entries
+# are few and they average out over a layer, so for gradients the test is
+# statistical: per layer the relative L2 difference is at most 0.1 (measured
+# <= 0.052), and at least 90 % of the entries lie within C 2^-8 of the sum of
+# the magnitudes of their terms (x * g over all pixels for a weight, g for a
+# bias; measured >= 95.8 %).  Errors of logic (an index, a tap, a slice) are
+# caught element by element by the exact regime above.
 
 C_BF16 = 16.0
 
@@ -250,10 +253,14 @@ def test_gpu_unet_forward_and_gradients_match_oracle(w, H, W):
         _, SW, Sb = U.conv_backward(np.abs(x), np.abs(Wk_), np.abs(gy))
         Sk = np.concatenate([SW.ravel(), Sb])
         a, b = g[off:off + m], gref[off:off + m]
-        assert np.all((Sk > 0) | (a == b)), k  # an entry with no terms is zero on both sides
-        r = np.abs(a - b)[Sk > 0] / (2.0 ** -8 * Sk[Sk > 0])
-        print(f"layer {k}: max |g - g_oracle| / (2^-8 sum|terms|) = {r.max():.3g}")
-        assert r.max() <= C_BF16, (k, r.max())
+        # an entry whose oracle terms all vanish (a mask that flipped) but differs counts as outside
+        r = np.where(Sk > 0, np.abs(a - b) / (2.0 ** -8 * np.where(Sk > 0, Sk, 1.0)),
+                     np.where(a == b, 0.0, np.inf))
+        frac_out = float(np.mean(r > C_BF16))
+        l2 = np.linalg.norm(a - b) / np.linalg.norm(b)
+        print(f"layer {k}: fraction above {C_BF16:g}: {frac_out:.2e}, relative L2 {l2:.3g}")
+        assert l2 <= 0.1, (k, l2)
+        assert frac_out <= 0.1, (k, frac_out)
         off += m
 
 
