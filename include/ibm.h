@@ -366,9 +366,14 @@ int ibm_get_sample(const ibm_ctx* ctx, float* feat, float* target, int* Hc, int*
  * after the pressure solve run case by case, and the pressure solves of
  * all cases run as one defect-correction loop whose FP32 sweep launches and
  * FP64 residual launches each cover every case that has not converged yet
- * (cases leave the launches as they reach their tolerance).  The tile
- * shape is chosen for the whole batch by the autotuner on the first step;
- * sweep launches are replayed from CUDA graphs (ibm_batch_set_graphs).
+ * (cases leave the launches as they reach their tolerance).  The parts
+ * before and after the pressure solve (classification, predictor, velocity
+ * solves, right-hand side, forces, projection) run as shared launches over
+ * all cases too, so the launches of a step do not grow with the number of
+ * cases (cases with a learned or extrapolated warm start or a relative
+ * pressure tolerance take those parts case by case).  The tile shape is
+ * chosen for the whole batch by the autotuner on the first step; see
+ * ibm_batch_set_budgets for the rounds of the pressure loop.
  *
  * The contexts are borrowed: they must outlive the batch and must not be
  * used by other calls while ibm_batch_step runs.  The batch owns a stream
@@ -393,7 +398,18 @@ void* ibm_batch_stream(const ibm_batch* batch);
  * ibm_set_sor_shape; -1: tuned over the batch on the next step). */
 int ibm_batch_set_sor_shape(ibm_batch* batch, int index);
 
-/* CUDA-graph replay of the sweep launches: on (1, the default) or off (0). */
+/* Sweep budgets of the batched pressure solve: on (1, the default), each
+ * round of the defect-correction loop gives every active case the FP32
+ * sweeps it predicts for itself (its CTAs skip the launches beyond them),
+ * so the loop takes as many rounds as its slowest case, in direct
+ * (programmatic dependent) launches; off (0), every active case takes the
+ * shortest prediction of the round, and the sweep launches are replayed
+ * from CUDA graphs (ibm_batch_set_graphs).  Either way each case stops at
+ * its own tolerance; the iterates differ only in where the checks fall. */
+int ibm_batch_set_budgets(ibm_batch* batch, int on);
+
+/* CUDA-graph replay of the sweep launches when budgets are off: on (1, the
+ * default) or off (0, direct launches of the same sweeps). */
 int ibm_batch_set_graphs(ibm_batch* batch, int on);
 
 /* Profiling of the batch (event timing of its sweep runs; counters of the

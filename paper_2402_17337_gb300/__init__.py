@@ -113,6 +113,7 @@ def lib():
             L.ibm_batch_create.argtypes = [C.POINTER(_VP), C.c_int, C.POINTER(_VP)]
             L.ibm_batch_step.argtypes = [_VP, C.c_int, C.POINTER(StepStats)]
             L.ibm_batch_set_graphs.argtypes = [_VP, C.c_int]
+            L.ibm_batch_set_budgets.argtypes = [_VP, C.c_int]
             L.ibm_batch_set_sor_shape.argtypes = [_VP, C.c_int]
             L.ibm_batch_stream.argtypes = [_VP]
             L.ibm_batch_stream.restype = _VP
@@ -334,7 +335,13 @@ class Batch:
         return [x.as_dict() for x in st]
 
     def set_graphs(self, on=True):
+        """CUDA-graph replay of the sweeps when budgets are off."""
         _check(lib().ibm_batch_set_graphs(self._h, 1 if on else 0))
+
+    def set_budgets(self, on=True):
+        """Each case its own sweeps per round of the pressure loop (default) or
+        the shortest prediction of the round for all (graph-replayable)."""
+        _check(lib().ibm_batch_set_budgets(self._h, 1 if on else 0))
 
     def set_sor_shape(self, index):
         """Fixes the FP32 sweep tile shape of the batch (-1: tune over the batch)."""

@@ -1,6 +1,7 @@
 // Host side of libibm: the C ABI declared in include/ibm.h, grid
 // construction (Sec. 2.3), device memory of a context and the fractional-step
 // driver (Sec. 2.2).
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1290,6 +1291,7 @@ struct ibm_batch {
   int cfg = -1;
   double sor_us = 0.0;
   bool use_graphs = true;
+  bool budgets = true;  // each case its own sweeps per round (direct launches); off: shared rounds
   bool profiling = false;
   Sor32Case *h_sor = nullptr, *d_sor = nullptr;  // tables A (e32 -> e32b) at [0, n), B (e32b -> e32) at [n, 2n)
   DcCase *h_dc = nullptr, *d_dc = nullptr;
@@ -1346,8 +1348,10 @@ namespace {
 constexpr int kPairsPerGraph = 8;
 
 // Sweep tables of the cases act[0..na) for tile shape cfg; *tiles receives
-// the CTAs of one launch.  Copied to the device on the batch's stream.
-int batch_sor_tables(ibm_batch* B, int cfg, const std::vector<int>& act, int* tiles) {
+// the CTAs of one launch; pairs (may be NULL: no limit) the launch pairs of
+// the round per active case.  Copied to the device on the batch's stream.
+int batch_sor_tables(ibm_batch* B, int cfg, const std::vector<int>& act, int* tiles,
+                     const std::vector<int>* pairs = nullptr) {
   const int n = (int)B->cs.size(), na = (int)act.size();
   int first = 0;
   for (int k = 0; k < na; ++k) {
@@ -1355,8 +1359,9 @@ int batch_sor_tables(ibm_batch* B, int cfg, const std::vector<int>& act, int* ti
     int tx = 0, ty = 0;
     sor32_tiles(cfg, c->geo32, &tx, &ty);
     const float om = (float)c->P.omega_p;
-    B->h_sor[k] = Sor32Case{c->geo32, c->e32, c->e32b, c->r32, c->invd32, om, first, tx};
-    B->h_sor[n + k] = Sor32Case{c->geo32, c->e32b, c->e32, c->r32, c->invd32, om, first, tx};
+    const int np = pairs ? (*pairs)[k] : INT_MAX;
+    B->h_sor[k] = Sor32Case{c->geo32, c->e32, c->e32b, c->r32, c->invd32, om, first, tx, np};
+    B->h_sor[n + k] = Sor32Case{c->geo32, c->e32b, c->e32, c->r32, c->invd32, om, first, tx, np};
     first += tx * ty;
   }
   *tiles = first;
@@ -1533,24 +1538,44 @@ int batch_solve(ibm_batch* B, const std::vector<double>& thr, std::vector<ibm_st
     }
     act.swap(next);
     if (act.empty()) break;
-    // FP32 sweeps of every active case
+    // FP32 sweeps of every active case: with budgets each case takes the
+    // sweeps it asked for (its CTAs skip the launch pairs beyond them) and
+    // the round lasts as long as the largest request; otherwise every case
+    // takes the shortest request
+    std::vector<int> pairs(act.size());
+    int round_pairs = 0;
+    for (size_t k = 0; k < act.size(); ++k) {
+      pairs[k] = (B->budgets ? want[act[k]] : round) / pair_sweeps;
+      round_pairs = std::max(round_pairs, pairs[k]);
+    }
     int tiles = 0;
-    int rc = batch_sor_tables(B, B->cfg, act, &tiles);
+    int rc = batch_sor_tables(B, B->cfg, act, &tiles, B->budgets ? &pairs : nullptr);
     if (rc) return rc;
     if (B->profiling) {
       CUDA_TRY(cudaEventRecord(B->t0, B->stream));
       timing = true;
       long long cells = 0;
-      for (int i : act) cells += (long long)B->cs[i]->nx * B->cs[i]->ny;
-      B->prof.sweep_launches += 2 * (round / pair_sweeps);
-      B->prof.sweep_cells += cells * 2 * (round / pair_sweeps);
+      for (size_t k = 0; k < act.size(); ++k) cells += (long long)B->cs[act[k]]->nx * B->cs[act[k]]->ny * pairs[k];
+      B->prof.sweep_launches += 2 * round_pairs;
+      B->prof.sweep_cells += cells * 2;
     }
-    rc = batch_sweeps(B, (int)act.size(), tiles, round / pair_sweeps);
-    if (rc) return rc;
-    for (int i : act) {
-      S[i].s += round;
+    if (B->budgets) {
+      // direct launches (programmatic dependents): the pair index varies per launch
+      B->prof.launches += 2 * round_pairs;
+      for (int q = 0; q < round_pairs; ++q) {
+        launch_sor32_batch(B->stream, B->cfg, B->d_sor, (int)act.size(), tiles, q == 0, 1, q);
+        launch_sor32_batch(B->stream, B->cfg, B->d_sor + n, (int)act.size(), tiles, 0, 1, q);
+      }
+      CUDA_TRY(cudaGetLastError());
+    } else {
+      rc = batch_sweeps(B, (int)act.size(), tiles, round_pairs);
+      if (rc) return rc;
+    }
+    for (size_t k = 0; k < act.size(); ++k) {
+      const int i = act[k];
+      S[i].s += pairs[k] * pair_sweeps;
       S[i].add = 1;
-      S[i].inner = round;
+      S[i].inner = pairs[k] * pair_sweeps;
     }
   }
   for (int i = 0; i < n; ++i) B->prof.poisson_sweeps += st[i].sweeps_p;
@@ -2389,6 +2414,12 @@ void* ibm_batch_stream(const ibm_batch* B) { return B ? (void*)B->stream : nullp
 int ibm_batch_set_graphs(ibm_batch* B, int on) {
   if (!B) return fail(IBM_E_INVAL, "null batch");
   B->use_graphs = on != 0;
+  return IBM_OK;
+}
+
+int ibm_batch_set_budgets(ibm_batch* B, int on) {
+  if (!B) return fail(IBM_E_INVAL, "null batch");
+  B->budgets = on != 0;
   return IBM_OK;
 }
 

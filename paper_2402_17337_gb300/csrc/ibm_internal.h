@@ -191,6 +191,7 @@ struct Sor32Case {
   const float* invd;
   float omega;
   int first, tiles_x;  // first CTA of this case, tiles per row
+  int pairs;           // launch pairs of this round for this case (a launch with pair index >= pairs skips it)
 };
 struct DcCase {
   Geo g;
@@ -206,8 +207,9 @@ void sor32_tiles(int cfg, const Geo32& g, int* tiles_x, int* tiles_y);
 cudaError_t sor32_batch_prepare(int cfg);
 // pdl: launch as a programmatic dependent of the previous kernel on the
 // stream (direct launches; the kernel waits for it before its first load)
+// q: index of the launch pair within the round (cases with pairs <= q skip it)
 void launch_sor32_batch(cudaStream_t s, int cfg, const Sor32Case* cases_dev, int ncases, int total_tiles,
-                        int zero_init, int pdl = 0);
+                        int zero_init, int pdl = 0, int q = 0);
 void launch_dc_residual_batch(cudaStream_t s, const DcCase* cases_dev, int ncases, int total_blocks);
 
 // geometric multigrid on the FP32 correction equation (k_mg.cu)

@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(32 * C::NY, C::MINB)
 // CTA b belongs to the case whose tile range [first, first + count) holds b.
 template <class C>
 __global__ void __launch_bounds__(32 * C::NY, C::MINB)
-    k_sor32_rb_batch(const Sor32Case* __restrict__ cases, int ncases, int zero_init) {
+    k_sor32_rb_batch(const Sor32Case* __restrict__ cases, int ncases, int zero_init, int q) {
   extern __shared__ float smem[];
   __shared__ Sor32Case c;  // the case's descriptor, read from shared memory where needed
   // programmatic dependent launch (a no-op unless the launch asks for it):
@@ -629,6 +629,7 @@ __global__ void __launch_bounds__(32 * C::NY, C::MINB)
     c = cases[lo];
   }
   __syncthreads();
+  if (q >= c.pairs) return;  // this case's sweeps of the round are done (uniform over the CTA)
   const int t = b - c.first;
   tile<C>(c.g, c.e_in, c.e_out, c.r, c.invd, c.omega, zero_init, t % c.tiles_x, t / c.tiles_x, smem);
 }
@@ -637,7 +638,7 @@ __global__ void __launch_bounds__(32 * C::NY, C::MINB)
 struct Sor32Config {
   int TY, K, NY, V;
   void (*launch)(cudaStream_t, const Geo32&, const float*, float*, const float*, const float*, float, int, int);
-  void (*launch_batch)(cudaStream_t, const Sor32Case*, int, int, int, int);
+  void (*launch_batch)(cudaStream_t, const Sor32Case*, int, int, int, int, int);
   cudaError_t (*prepare)();
   void (*tiles)(const Geo32&, int*, int*);
 };
@@ -680,10 +681,10 @@ void launch_shape(cudaStream_t s, const Geo32& g, const float* e_in, float* e_ou
 
 template <class C>
 void launch_shape_batch(cudaStream_t s, const Sor32Case* cases, int ncases, int total_tiles, int zero_init,
-                        int pdl) {
+                        int pdl, int q) {
   if (total_tiles <= 0) return;
   if (!pdl) {
-    k_sor32_rb_batch<C><<<total_tiles, dim3(32, C::NY), C::smem, s>>>(cases, ncases, zero_init);
+    k_sor32_rb_batch<C><<<total_tiles, dim3(32, C::NY), C::smem, s>>>(cases, ncases, zero_init, q);
     return;
   }
   cudaLaunchConfig_t lc{};
@@ -696,7 +697,7 @@ void launch_shape_batch(cudaStream_t s, const Sor32Case* cases, int ncases, int 
   at[0].val.programmaticStreamSerializationAllowed = 1;
   lc.attrs = at;
   lc.numAttrs = 1;
-  cudaLaunchKernelEx(&lc, k_sor32_rb_batch<C>, cases, ncases, zero_init);
+  cudaLaunchKernelEx(&lc, k_sor32_rb_batch<C>, cases, ncases, zero_init, q);
 }
 
 template <class C>
@@ -757,8 +758,8 @@ void sor32_tiles(int cfg, const Geo32& g, int* tiles_x, int* tiles_y) { kConfigs
 cudaError_t sor32_batch_prepare(int cfg) { return kConfigs[cfg].prepare(); }
 
 void launch_sor32_batch(cudaStream_t s, int cfg, const Sor32Case* cases_dev, int ncases, int total_tiles,
-                        int zero_init, int pdl) {
-  kConfigs[cfg].launch_batch(s, cases_dev, ncases, total_tiles, zero_init, pdl);
+                        int zero_init, int pdl, int q) {
+  kConfigs[cfg].launch_batch(s, cases_dev, ncases, total_tiles, zero_init, pdl, q);
 }
 
 void launch_dc_residual_batch(cudaStream_t s, const DcCase* cases_dev, int ncases, int total_blocks) {

@@ -114,6 +114,7 @@ def test_entry_points_reject_null_handles_before_touching_the_device():
         "ibm_batch_create": (None, 0, None),
         "ibm_batch_step": (None, 1, C.byref(stats)),
         "ibm_batch_set_graphs": (None, 1),
+        "ibm_batch_set_budgets": (None, 1),
         "ibm_batch_set_sor_shape": (None, 0),
         "ibm_batch_set_profiling": (None, 1),
         "ibm_batch_get_profile": (None, C.byref(prof)),
