@@ -56,12 +56,14 @@ SOR32_TRAFFIC = {
     ("plunge_2048x1024", (80, 16, 16, 7)): 25.221e6,
     ("plunge_4096x2048", (32, 8, 8, 7)): 117.465e6,
     ("plunge_4096x2048", (64, 16, 16, 7)): 115.556e6,
+    ("plunge_4096x2048", (80, 16, 16, 7)): 114.906e6,
 }
 # warp instructions issued per launch of the FP32 sweep kernel (ncu smsp__inst_executed.sum of one
 # launch, profiles/k_sor32_rb_*.md), by workload and tile shape: the issue roofline of a kernel that is
 # bound by latency and issue, not by DRAM (its working set fits in L2 on 2048x1024)
 SOR32_INST = {
     ("plunge_2048x1024", (80, 16, 16, 7)): 15.768846e6,
+    ("plunge_4096x2048", (80, 16, 16, 7)): 61.646262e6,
 }
 WORKLOADS = ("plunge_2048x1024", "plunge_4096x2048", "unet_1024x512", "batch64")
 METRIC = "cell-steps/s at div<1e-8: learned warm-start+mixed vs plain FP64, one GB300"

@@ -98,12 +98,14 @@ def evaluate(cfg, net, cT, steps, start, precision=1, stream=None):
             s.step(1)
         if mode == 1:
             s.set_warmstart(1, net, cT)
-        sw, t0 = [], time.perf_counter()
+        sw, kept, t0 = [], [], time.perf_counter()
         for _ in range(steps):
+            k0 = s.profile()["ws_kept"]
             st = s.step(1)
             sw.append(st["sweeps_p"])
+            kept.append(s.profile()["ws_kept"] - k0)
             assert st["div_max"] <= cfg.div_tol * 1.001
-        res["learned" if mode else "plain"] = {"sweeps": sw, "seconds": time.perf_counter() - t0}
+        res["learned" if mode else "plain"] = {"sweeps": sw, "kept": kept, "seconds": time.perf_counter() - t0}
         s.close()
     return res
 

@@ -111,6 +111,39 @@ def test_unet_two_level_preconditioner_meets_the_same_tolerance():
     net.close()
 
 
+def test_unet_preconditioner_with_pre_smoothing_never_returns_a_step_that_misses_the_tolerance():
+    """The configuration in which the real use fails: with pre-smoothing the
+    two-level cycle is no longer symmetric and the network's coarse correction
+    belongs to another residual, and FCG(1) stalls (near 1e-5 on this case
+    over two steps; every trained network stalled it on the bench grids).
+    Whatever the iteration does, a step either meets the residual and
+    divergence tolerances or ends with IBM_E_NOCONV at its iteration cap:
+    never fields that miss the tolerance."""
+    import dataclasses
+    from paper_2402_17337_gb300 import IBM_E_NOCONV, IbmError, Solver, UNet, build
+    build.build()
+    c = dataclasses.replace(W.plunge_192x128(), name="uniform_128x64", x0=-4.0, x1=8.0, y0=-3.0, y1=3.0, nx=128,
+                            ny=64, steps=2, div_tol=1e-8)
+    net = UNet((16, 16, 32, 32), seed=3)
+    g = Solver(**kwargs(c), precision=2, max_sweeps=1500)
+    g.set_body(c.chord, c.tc, c.h, c.k, c.xc, c.yc)
+    g.set("u", c.initial_u(g.shape("u")))
+    g.set_preconditioner(1, net, 1e-4, 1)
+    outcome = []
+    for _ in range(c.steps):
+        try:
+            st = g.step(1)
+        except IbmError as e:
+            assert e.code == IBM_E_NOCONV, e
+            outcome.append("NOCONV")
+            break
+        assert st["res_p"] <= c.ptol and st["div_max"] <= c.div_tol * 1.001, st
+        outcome.append(st["sweeps_p"])
+    print("two-level U-Net preconditioner with pre-smoothing:", outcome)
+    g.close()
+    net.close()
+
+
 def test_preconditioner_rejects_invalid_use():
     from paper_2402_17337_gb300 import IbmError, Solver, UNet, build
     build.build()
