@@ -405,7 +405,7 @@ __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wa
 // grid has released it
 __device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-template <int TY, int K, int NY, bool RDREG>
+template <int TY, int K, int NY, bool RDREG, bool SPLIT = false>
 __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __restrict__ e_in, float* __restrict__ e_out,
                                               const float* __restrict__ r, const float* __restrict__ invd,
                                               float omega, int zero_init, int bx, int by, float* smem) {
@@ -502,11 +502,18 @@ __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __res
       }
   }
   __syncthreads();
-  // one half-sweep of colour C whose first row has parity S0 (both compile-time)
-  auto half = [&](auto colour, auto start) {
+  // one half-sweep of colour C whose first row has parity S0 (all
+  // compile-time), over the rows selected by PART: 0 all rows, 1 the rows
+  // inside the thread's run, 2 its first and last row
+  auto half_rows = [&](auto colour, auto start, auto part) {
     constexpr int c = decltype(colour)::value, oc = c ^ 1, S0 = decltype(start)::value;
+    constexpr int PART = decltype(part)::value;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
+      if constexpr (PART != 0) {
+        const bool edge = q == 0 || q == RPT - 1;
+        if ((PART == 2) != edge) continue;
+      }
       const int s = S0 ^ (q & 1);
       const int ly = ly0 + q;
 #pragma unroll
@@ -536,7 +543,26 @@ __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __res
         se[c][ly + 1][kk + 1] = nxv;
       }
     }
-    __syncthreads();
+  };
+  // A half-sweep of a thread row (one warp) reads other threads' cells only
+  // in the last row of the thread row above and the first row of the one
+  // below; its other rows read the row's own cells (registers, and shared
+  // memory written by the same warp).  With SPLIT the barrier between
+  // half-sweeps comes after the rows inside each run and before its first
+  // and last rows: those read the neighbours' edge rows of the previous
+  // half-sweep (written before the barrier) and overwrite cells the
+  // neighbours last read before it, and the inside rows of the next
+  // half-sweep, which depend on no other warp, can interleave with them.
+  // The same updates, each from the same values: identical iterates.
+  auto half = [&](auto colour, auto start) {
+    if constexpr (SPLIT) {
+      half_rows(colour, start, std::integral_constant<int, 1>{});
+      __syncthreads();
+      half_rows(colour, start, std::integral_constant<int, 2>{});
+    } else {
+      half_rows(colour, start, std::integral_constant<int, 0>{});
+      __syncthreads();
+    }
   };
   const int p0 = (j0 + ly0) & 1;  // parity of this thread's first row
 #pragma unroll 1
@@ -568,14 +594,15 @@ __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __res
 
 // A tile shape: rows per tile, half-sweeps per launch, thread rows, form
 // (3: sor32_tile; 4: sor32_tile_v4 with r and 1/d in shared memory; 5: with
-// r and 1/d in registers; 6, 7: sor32_tile_v6 likewise) and minimum
-// resident CTAs per SM.
+// r and 1/d in registers; 6, 7: sor32_tile_v6 likewise; 8: as 7 with the
+// barrier between the inside rows of each thread's run and its edge rows)
+// and minimum resident CTAs per SM.
 template <int TY_, int K_, int NY_, int V_, int MINB_>
 struct Cfg {
   static constexpr int TY = TY_, K = K_, NY = NY_, V = V_, MINB = MINB_;
   static constexpr int HK = (K + 1) / 2, TK = 64 - 2 * HK;
   static constexpr size_t smem =
-      std::conditional_t<V == 3, Sor32Shape<TY, K, NY>, Sor32ShapeV4<TY, K, NY, V == 5 || V == 7>>::smem;
+      std::conditional_t<V == 3, Sor32Shape<TY, K, NY>, Sor32ShapeV4<TY, K, NY, V == 5 || V >= 7>>::smem;
 };
 
 template <class C>
@@ -586,7 +613,8 @@ __device__ __forceinline__ void tile(const Geo32& g, const float* e_in, float* e
   else if constexpr (C::V == 4 || C::V == 5)
     sor32_tile_v4<C::TY, C::K, C::NY, C::V == 5>(g, e_in, e_out, r, invd, omega, zero_init, bx, by, smem);
   else
-    sor32_tile_v6<C::TY, C::K, C::NY, C::V == 7>(g, e_in, e_out, r, invd, omega, zero_init, bx, by, smem);
+    sor32_tile_v6<C::TY, C::K, C::NY, C::V >= 7, C::V == 8>(g, e_in, e_out, r, invd, omega, zero_init, bx, by,
+                                                              smem);
 }
 
 template <class C>
@@ -722,6 +750,7 @@ const Sor32Config kConfigs[] = {
     shape<Cfg<48, 8, 16, 7, 1>>(),  shape<Cfg<24, 4, 8, 7, 2>>(),   shape<Cfg<48, 8, 8, 6, 2>>(),
     shape<Cfg<48, 8, 8, 7, 1>>(),   shape<Cfg<40, 12, 8, 6, 2>>(),  shape<Cfg<80, 16, 16, 6, 1>>(),
     shape<Cfg<96, 16, 16, 6, 1>>(), shape<Cfg<64, 16, 16, 7, 1>>(), shape<Cfg<80, 16, 16, 7, 1>>(),
+    shape<Cfg<64, 16, 16, 8, 1>>(), shape<Cfg<80, 16, 16, 8, 1>>(),
 };
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
