@@ -57,6 +57,8 @@ SOR32_TRAFFIC = {
     ("plunge_4096x2048", (32, 8, 8, 7)): 117.465e6,
     ("plunge_4096x2048", (64, 16, 16, 7)): 115.556e6,
     ("plunge_4096x2048", (80, 16, 16, 7)): 114.906e6,
+    ("plunge_2048x1024", (80, 16, 16, 8)): 25.230592e6,
+    ("plunge_4096x2048", (80, 16, 16, 8)): 115.323392e6,
 }
 # warp instructions issued per launch of the FP32 sweep kernel (ncu smsp__inst_executed.sum of one
 # launch, profiles/k_sor32_rb_*.md), by workload and tile shape: the issue roofline of a kernel that is
@@ -64,6 +66,8 @@ SOR32_TRAFFIC = {
 SOR32_INST = {
     ("plunge_2048x1024", (80, 16, 16, 7)): 15.768846e6,
     ("plunge_4096x2048", (80, 16, 16, 7)): 61.646262e6,
+    ("plunge_2048x1024", (80, 16, 16, 8)): 15.773422e6,
+    ("plunge_4096x2048", (80, 16, 16, 8)): 61.66415e6,
 }
 WORKLOADS = ("plunge_2048x1024", "plunge_4096x2048", "unet_1024x512", "batch64")
 METRIC = "cell-steps/s at div<1e-8: learned warm-start+mixed vs plain FP64, one GB300"
@@ -434,7 +438,7 @@ def run_batch(args):
             st = batch2.step(1)
             for s, pn in zip(ss2, pinned):
                 for n in names:
-                    pn[n][...] = s.get(n)
+                    s.get(n, out=pn[n])
             ok2 += sum(n for n, c, x in zip(cells, cfgs, st) if x["div_max"] < c.div_tol)
         barrier()
         e2e_value, _, _ = replica_throughput(ok2, 1e3 * (time.perf_counter() - t0), dist, "cuda")
@@ -703,7 +707,7 @@ def main():
                 s2.set(n, pinned[n])
             st = s2.step(1)
             for n in names:
-                pinned[n][...] = s2.get(n)
+                s2.get(n, out=pinned[n])
             ok_e2e += st["div_max"] < cfg.div_tol
         barrier()
         te = time.perf_counter() - t0
@@ -712,7 +716,7 @@ def main():
         e2e = {"value": e2e_value, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": h2d,
                "note": "same steps as the timed window on a second context; per step u, v, p, phi copied "
-                       "in from pinned host memory, step, copied back; host wall clock"}
+                       "in from pinned host memory, step, copied back into pinned host memory; host wall clock"}
 
     # ------------------------------------------------------------ CPU oracle
     cpu = None

@@ -221,8 +221,15 @@ class Solver:
         _check(lib().ibm_forces(self._h, _dp(cl), _dp(cd), n.value, C.byref(n)))
         return cl[:n.value], cd[:n.value]
 
-    def get(self, name):
-        out = np.zeros(self.shape(name))
+    def get(self, name, out=None):
+        """Field `name` in the compact row-major layout.  out: a C-contiguous
+        float64 array of the field's shape to copy into (e.g. pinned memory,
+        which the device writes directly); a new array otherwise."""
+        if out is None:
+            out = np.zeros(self.shape(name))
+        elif (out.dtype != np.float64 or out.shape != self.shape(name) or not out.flags["C_CONTIGUOUS"]
+              or not out.flags["WRITEABLE"]):
+            raise ValueError(f"out must be a writeable C-contiguous float64 array of shape {self.shape(name)}")
         _check(lib().ibm_get_field(self._h, FIELDS[name], _dp(out), out.size))
         return out
 
