@@ -2,6 +2,8 @@
 
     python -m paper_2402_17337_gb300.train_warmstart --workload plunge_2048x1024 \
         --runs 4 --steps 60 --epochs 20 --out weights.npz
+    python -m paper_2402_17337_gb300.train_warmstart --workload unet_1024x512 \
+        --samples 20000 --start 200 --every 1 --steps 700 --epochs 8 --out weights.npz
 
 Training runs use the workload's grid and time step with seeded foil
 parameters (h ~ U[0.1, 0.5], k ~ U[1, 4], Re ~ U[100, 1000]) and record one
@@ -49,6 +51,11 @@ def main(argv=None):
     ap.add_argument("--eval-steps", type=int, default=10)
     ap.add_argument("--widths", type=int, nargs=4, default=list(WIDTHS),
                     help="channels of the four levels (multiples of 16)")
+    ap.add_argument("--samples", type=int, default=0,
+                    help="train on this many snapshots held in device memory, taken every --every steps "
+                         "after --start steps of as many seeded runs as it takes (0: one per step of --runs runs)")
+    ap.add_argument("--start", type=int, default=200)
+    ap.add_argument("--every", type=int, default=1)
     ap.add_argument("--out", required=True)
     args = ap.parse_args(argv)
 
@@ -56,14 +63,31 @@ def main(argv=None):
     build.build()
     cfg = getattr(W, args.workload)()
     t0 = time.perf_counter()
-    samples = warmstart.Samples([], [], [])
-    for c in training_configs(cfg, args.runs, args.seed):
-        s = warmstart.capture(c, steps=args.steps, start=0, every=1)
-        samples.feat += s.feat
-        samples.target += s.target
-        samples.sweeps += s.sweeps
-        print(f"captured {len(s.feat)} samples of {c.name} (h={c.h:.3f} k={c.k:.3f} Re={c.Re:.0f}), "
-              f"{time.perf_counter() - t0:.0f} s", flush=True)
+    if args.samples > 0:
+        import torch
+        Hc, Wc = cfg.ny // 2, cfg.nx // 2
+        feats = torch.empty((args.samples, Hc, Wc, 4), dtype=torch.float32, device="cuda")
+        targs = torch.empty((args.samples, Hc, Wc), dtype=torch.float32, device="cuda")
+        pos, runs = 0, 0
+        while pos < args.samples:
+            (c,) = training_configs(cfg, runs + 1, args.seed)[runs:]
+            pos, sw = warmstart.capture_to_device(c, steps=args.steps, start=args.start, every=args.every,
+                                                  feats=feats, targs=targs, pos=pos)
+            runs += 1
+            print(f"run {runs}: {len(sw)} samples of {c.name} (h={c.h:.3f} k={c.k:.3f} Re={c.Re:.0f}), "
+                  f"{pos} in total, {time.perf_counter() - t0:.0f} s", flush=True)
+        samples = (feats, targs)
+        n_samples, args.runs = pos, runs
+    else:
+        samples = warmstart.Samples([], [], [])
+        for c in training_configs(cfg, args.runs, args.seed):
+            s = warmstart.capture(c, steps=args.steps, start=0, every=1)
+            samples.feat += s.feat
+            samples.target += s.target
+            samples.sweeps += s.sweeps
+            print(f"captured {len(s.feat)} samples of {c.name} (h={c.h:.3f} k={c.k:.3f} Re={c.Re:.0f}), "
+                  f"{time.perf_counter() - t0:.0f} s", flush=True)
+        n_samples = len(samples.feat)
     net = ibm.UNet(tuple(args.widths), seed=args.seed)
     t1 = time.perf_counter()
     cT, hist = warmstart.train(net, samples, epochs=args.epochs, lr=args.lr, seed=args.seed,
@@ -72,7 +96,8 @@ def main(argv=None):
     res = warmstart.evaluate(cfg, net, cT, steps=args.eval_steps, start=args.eval_start)
     plain, learned = sum(res["plain"]["sweeps"]), sum(res["learned"]["sweeps"])
     meta = {"workload": cfg.name, "widths": list(args.widths), "runs": args.runs, "steps_per_run": args.steps,
-            "samples": len(samples.feat), "epochs": args.epochs, "lr": args.lr, "seed": args.seed,
+            "samples": n_samples, "sample_start": args.start if args.samples else 0,
+            "sample_every": args.every if args.samples else 1, "epochs": args.epochs, "lr": args.lr, "seed": args.seed,
             "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "train_seconds": t_train,
             "eval": {"steps": [args.eval_start, args.eval_start + args.eval_steps],
                      "plain_sweeps": res["plain"]["sweeps"], "learned_sweeps": res["learned"]["sweeps"],

@@ -61,18 +61,54 @@ def capture(cfg, steps, start, every, precision=1, stream=None):
     return out
 
 
+def capture_to_device(cfg, steps, start, every, feats, targs, pos, precision=1, stream=None):
+    """As capture, but each sample goes straight into the preallocated device
+    tensors feats [N, Hc, Wc, 4] and targs [N, Hc, Wc] from index pos on (no
+    host list: a large training set lives in device memory).  Returns the
+    next free index and the pressure sweeps of the sampled steps."""
+    import torch
+    s = ibm.Solver.from_config(cfg, precision=precision, stream=stream)
+    s.set("u", cfg.initial_u(s.shape("u")))
+    s.set_warmstart(2, None, 1.0)
+    sweeps = []
+    for n in range(steps):
+        if pos >= feats.shape[0]:
+            break
+        st = s.step(1)
+        if n >= start and (n - start) % every == 0:
+            f, t = s.sample()
+            feats[pos].copy_(torch.from_numpy(f))
+            targs[pos].copy_(torch.from_numpy(t))
+            sweeps.append(st["sweeps_p"])
+            pos += 1
+    s.close()
+    return pos, sweeps
+
+
 def target_scale(samples):
     return float(np.sqrt(np.mean([np.mean(t.astype(np.float64) ** 2) for t in samples.target])))
 
 
 def train(net, samples, epochs, lr=1e-3, cT=None, seed=0, log=None):
-    """Adam on the mean squared error, one sample per step, shuffled epochs."""
+    """Adam on the mean squared error, one sample per step, shuffled epochs.
+    samples: a Samples of host arrays, or a pair (feats, targs) of device
+    tensors [N, Hc, Wc, 4] and [N, Hc, Wc] (capture_to_device)."""
     import torch
-    cT = cT or target_scale(samples)
-    feats = [torch.tensor(f, device="cuda") for f in samples.feat]
-    targs = [torch.tensor(t / cT, device="cuda") for t in samples.target]
+    if isinstance(samples, tuple):
+        fdev, tdev = samples
+        if not cT:
+            ss = sum(float(torch.sum(tdev[k:k + 256].double() ** 2)) for k in range(0, tdev.shape[0], 256))
+            cT = float(np.sqrt(ss / tdev.numel()))
+        tdev.div_(cT)
+        feats = [fdev[k] for k in range(fdev.shape[0])]
+        targs = [tdev[k] for k in range(tdev.shape[0])]
+        Hc, Wc = tdev.shape[1], tdev.shape[2]
+    else:
+        cT = cT or target_scale(samples)
+        feats = [torch.tensor(f, device="cuda") for f in samples.feat]
+        targs = [torch.tensor(t / cT, device="cuda") for t in samples.target]
+        Hc, Wc = samples.target[0].shape
     torch.cuda.synchronize()
-    Hc, Wc = samples.target[0].shape
     rng = np.random.default_rng(seed)
     hist = []
     for ep in range(epochs):
