@@ -13,7 +13,8 @@
 // full sweeps and the halo is recomputed by the neighbouring tiles.  The
 // FP32 arrays are stored split by colour (Geo32), so a half-sweep reads its
 // neighbours contiguously; each thread keeps its own cells' correction,
-// right-hand side and reciprocal diagonal in registers for the whole launch
+// update coefficients a = omega / d and b = -a r (formed from the
+// right-hand side and the reciprocal diagonal) in registers for the whole launch
 // and shared memory only carries the values the neighbours read.
 #include <type_traits>
 
@@ -124,6 +125,27 @@ __global__ void k_dc_residual_batch(const DcCase* __restrict__ cases, int ncases
   block_max_bits(bits, c.res_bits);
 }
 
+// One SOR update.  x <- x + omega (gs - x) with the Gauss-Seidel value
+// gs = (sum - r) / d is evaluated as x <- a sum + ((1 - omega) x + b), where
+// a = omega / d and b = -a r are formed once per cell and launch (sor_ab):
+// after the neighbour sum an update costs two FMAs, the first of which does
+// not wait for the sum.  The neighbour sum takes the N and S terms first and
+// the W/E term of the neighbour across the packed column (a shared-memory
+// read) last.  Every tile form below uses exactly these operations in this
+// order, so all give identical iterates.
+__device__ __forceinline__ void sor_ab(float omega, float rr, float dd, float& a, float& b) {
+  a = omega * dd;
+  b = -(a * rr);
+}
+__device__ __forceinline__ float sor_update(float cN, float xN, float cS, float xS, float cSelf, float xSelf,
+                                            float cOther, float xOther, float a, float b, float omc, float x) {
+  float sum = cN * xN;
+  sum = fmaf(cS, xS, sum);
+  sum = fmaf(cSelf, xSelf, sum);
+  sum = fmaf(cOther, xOther, sum);
+  return fmaf(a, sum, fmaf(omc, x, b));
+}
+
 // K half-sweeps (red first) of FP32 red-black SOR on L_p e = r, from e_in
 // into e_out.  The two buffers must differ: a tile's halo is read from cells
 // that neighbouring tiles write, and tiles of later waves would otherwise
@@ -134,7 +156,7 @@ __global__ void k_dc_residual_batch(const DcCase* __restrict__ cases, int ncases
 // by TK = LK - 2 HK colour columns, HK = ceil(K/2).  Thread (tx, ty) owns
 // colour columns tx and tx + 32 of rows ty, ty + NY, ... for both colours;
 // it keeps its cells' values in registers, and shared memory holds the
-// values, right-hand side and reciprocal diagonal of the whole region.
+// values and update coefficients a, b of the whole region.
 // Every half-sweep updates all cells that have their four neighbours in the
 // region; a value that is wrong because the region is finite moves inwards
 // by one cell per half-sweep, so after K half-sweeps the tile, at least K
@@ -155,12 +177,13 @@ __device__ __forceinline__ void sor32_tile(const Geo32& g, const float* __restri
   using S = Sor32Shape<TY, K, NY>;
   constexpr int LK = S::LK, HK = S::HK, TK = S::TK, LY = S::LY, RPT = S::RPT;
   float(*se)[LY][LK] = reinterpret_cast<float(*)[LY][LK]>(smem);                    // [2][LY][LK]
-  float(*sr)[LY][LK] = reinterpret_cast<float(*)[LY][LK]>(smem + 2 * LY * LK);      // [2][LY][LK]
-  float(*sd)[LY][LK] = reinterpret_cast<float(*)[LY][LK]>(smem + 4 * LY * LK);      // [2][LY][LK]
+  float(*sb)[LY][LK] = reinterpret_cast<float(*)[LY][LK]>(smem + 2 * LY * LK);      // [2][LY][LK]
+  float(*sa)[LY][LK] = reinterpret_cast<float(*)[LY][LK]>(smem + 4 * LY * LK);      // [2][LY][LK]
   const int nx = g.nx, ny = g.ny, pk = g.pk;
   const int k0 = bx * TK - HK, j0 = by * TY - K;
   const int tx = threadIdx.x, ty = threadIdx.y;
   float ev[2][RPT][2];
+  const float omc = 1.f - omega;
   float cE[2][2], cW[2][2], cN[RPT], cS[RPT];
   unsigned live = 0u, upd = 0u;  // bit (c, q, m): inside the domain / updated each half-sweep
 #pragma unroll
@@ -191,9 +214,11 @@ __device__ __forceinline__ void sor32_tile(const Geo32& g, const float* __restri
         if (in) live |= 1u << bit;
         if (in && ly >= 1 && ly <= LY - 2 && li >= 1 && li <= 2 * LK - 2) upd |= 1u << bit;
         if (ly < LY) {
+          float aa, bb;
+          sor_ab(omega, in ? r[o] : 0.f, in ? invd[o] : 0.f, aa, bb);
           se[c][ly][kk] = x;
-          sr[c][ly][kk] = in ? r[o] : 0.f;
-          sd[c][ly][kk] = in ? invd[o] : 0.f;
+          sb[c][ly][kk] = bb;
+          sa[c][ly][kk] = aa;
         }
       }
   }
@@ -210,17 +235,13 @@ __device__ __forceinline__ void sor32_tile(const Geo32& g, const float* __restri
       for (int m = 0; m < 2; ++m) {
         if (!(upd >> ((c * RPT + q) * 2 + m) & 1u)) continue;
         const int kk = tx + 32 * m;
-        // neighbours of the other colour: W and E in this row, N and S
-        const float xW = se[oc][ly][kk - 1 + s], xE = se[oc][ly][kk + s];
+        // neighbours of the other colour: N and S, the one in this packed
+        // column (W if s, else E) and the one across the next (E if s, else W)
+        const float xSelf = se[oc][ly][kk], xOther = se[oc][ly][kk + (s ? 1 : -1)];
         const float xN = se[oc][ly + 1][kk], xS = se[oc][ly - 1][kk];
-        const float ce = s ? cE[m][1] : cE[m][0], cw = s ? cW[m][1] : cW[m][0];
-        float sum = ce * xE;
-        sum = fmaf(cw, xW, sum);
-        sum = fmaf(cN[q], xN, sum);
-        sum = fmaf(cS[q], xS, sum);
-        const float gs = (sum - sr[c][ly][kk]) * sd[c][ly][kk];
-        const float x = ev[c][q][m];
-        const float nxv = fmaf(omega, gs - x, x);
+        const float cself = s ? cW[m][1] : cE[m][0], cother = s ? cE[m][1] : cW[m][0];
+        const float nxv = sor_update(cN[q], xN, cS[q], xS, cself, xSelf, cother, xOther, sa[c][ly][kk],
+                                     sb[c][ly][kk], omc, ev[c][q][m]);
         ev[c][q][m] = nxv;
         se[c][ly][kk] = nxv;
       }
@@ -251,7 +272,8 @@ __device__ __forceinline__ void sor32_tile(const Geo32& g, const float* __restri
 
 // Second form of the tile sweep (same iterates, fewer instructions per
 // update).  The region is stored with one zero row and column on each side
-// and cells outside the domain carry r = 0 and a zero reciprocal diagonal,
+// and cells outside the domain carry r = 0 and a zero reciprocal diagonal
+// (a = b = 0, so an update multiplies them by 1 - omega),
 // so every cell of the region is updated without a test: a cell outside the
 // domain stays exactly zero, and a cell on the region's edge takes wrong
 // values that, like any value spoiled by the region's finite size, move
@@ -261,8 +283,8 @@ __device__ __forceinline__ void sor32_tile(const Geo32& g, const float* __restri
 // thread and colour; of the W and E neighbours one is the thread's own cell
 // of the other colour (register) and the other is read from shared memory.
 // The arithmetic of an update is the same as in sor32_tile, in the same
-// order, so both forms give identical iterates.  With RDREG the right-hand
-// side and reciprocal diagonal of a thread's cells stay in registers.
+// order, so both forms give identical iterates.  With RDREG the update
+// coefficients a, b of a thread's cells stay in registers.
 template <int TY, int K, int NY, bool RDREG>
 struct Sor32ShapeV4 {
   static constexpr int LK = 64, HK = (K + 1) / 2, TK = LK - 2 * HK, LY = TY + 2 * K;
@@ -279,8 +301,8 @@ __device__ __forceinline__ void sor32_tile_v4(const Geo32& g, const float* __res
   using S = Sor32ShapeV4<TY, K, NY, RDREG>;
   constexpr int HK = S::HK, TK = S::TK, LY = S::LY, RPT = S::RPT, PY = S::PY, PK = S::PK;
   float(*se)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem);  // [2][PY][PK], cell (ly, kk) at [ly+1][kk+1]
-  float(*sr)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem + 2 * PY * PK);
-  float(*sd)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem + 4 * PY * PK);
+  float(*sb)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem + 2 * PY * PK);
+  float(*sa)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem + 4 * PY * PK);
   const int nx = g.nx, ny = g.ny, pk = g.pk;
   const int k0 = bx * TK - HK, j0 = by * TY - K;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -294,7 +316,8 @@ __device__ __forceinline__ void sor32_tile_v4(const Geo32& g, const float* __res
       se[c][1 + (u - 2 * PK) / 2][(u & 1) ? PK - 1 : 0] = 0.f;
   }
   float ev[2][RPT][2];
-  float rv[RDREG ? 2 : 1][RDREG ? RPT : 1][2], dv[RDREG ? 2 : 1][RDREG ? RPT : 1][2];
+  const float omc = 1.f - omega;
+  float bv[RDREG ? 2 : 1][RDREG ? RPT : 1][2], av[RDREG ? 2 : 1][RDREG ? RPT : 1][2];
   float ce[2][2], cw[2][2], cN[RPT], cS[RPT];
 #pragma unroll
   for (int m = 0; m < 2; ++m) {
@@ -320,15 +343,16 @@ __device__ __forceinline__ void sor32_tile_v4(const Geo32& g, const float* __res
         const bool in = rowok && k >= 0 && i < nx;
         const size_t o = (size_t)(c * ny + j) * pk + k;
         const float x = (in && !zero_init) ? e_in[o] : 0.f;
-        const float rr = in ? r[o] : 0.f, dd = in ? invd[o] : 0.f;
+        float aa, bb;  // a and b of the update
+        sor_ab(omega, in ? r[o] : 0.f, in ? invd[o] : 0.f, aa, bb);
         ev[c][q][m] = x;
         se[c][ly + 1][kk + 1] = x;
         if constexpr (RDREG) {
-          rv[c][q][m] = rr;
-          dv[c][q][m] = dd;
+          bv[c][q][m] = bb;
+          av[c][q][m] = aa;
         } else {
-          sr[c][ly + 1][kk + 1] = rr;
-          sd[c][ly + 1][kk + 1] = dd;
+          sb[c][ly + 1][kk + 1] = bb;
+          sa[c][ly + 1][kk + 1] = aa;
         }
       }
   }
@@ -346,22 +370,16 @@ __device__ __forceinline__ void sor32_tile_v4(const Geo32& g, const float* __res
         const float xSelf = ev[oc][q][m];                 // the other colour in this packed column
         const float xOther = se[oc][ly + 1][kk + off];    // the other colour one packed column away
         const float xN = se[oc][ly + 2][kk + 1], xS = se[oc][ly][kk + 1];
-        const float xE = s ? xOther : xSelf, xW = s ? xSelf : xOther;
-        float sum = ce[c][m] * xE;
-        sum = fmaf(cw[c][m], xW, sum);
-        sum = fmaf(cN[q], xN, sum);
-        sum = fmaf(cS[q], xS, sum);
-        float rr, dd;
+        float aa, bb;  // a and b of the update
         if constexpr (RDREG) {
-          rr = rv[c][q][m];
-          dd = dv[c][q][m];
+          bb = bv[c][q][m];
+          aa = av[c][q][m];
         } else {
-          rr = sr[c][ly + 1][kk + 1];
-          dd = sd[c][ly + 1][kk + 1];
+          bb = sb[c][ly + 1][kk + 1];
+          aa = sa[c][ly + 1][kk + 1];
         }
-        const float gs = (sum - rr) * dd;
-        const float x = ev[c][q][m];
-        const float nxv = fmaf(omega, gs - x, x);
+        const float nxv = sor_update(cN[q], xN, cS[q], xS, s ? cw[c][m] : ce[c][m], xSelf, s ? ce[c][m] : cw[c][m],
+                                     xOther, aa, bb, omc, ev[c][q][m]);
         ev[c][q][m] = nxv;
         se[c][ly + 1][kk + 1] = nxv;
       }
@@ -412,8 +430,8 @@ __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __res
   using S = Sor32ShapeV4<TY, K, NY, RDREG>;
   constexpr int HK = S::HK, TK = S::TK, LY = S::LY, RPT = S::RPT, PY = S::PY, PK = S::PK;
   float(*se)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem);  // [2][PY][PK], cell (ly, kk) at [ly+1][kk+1]
-  float(*sr)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem + 2 * PY * PK);
-  float(*sd)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem + 4 * PY * PK);
+  float(*sb)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem + 2 * PY * PK);
+  float(*sa)[PY][PK] = reinterpret_cast<float(*)[PY][PK]>(smem + 4 * PY * PK);
   const int nx = g.nx, ny = g.ny, pk = g.pk;
   const int k0 = bx * TK - HK, j0 = by * TY - K;
   const int tx = threadIdx.x, ty = threadIdx.y, ly0 = ty * RPT;
@@ -425,7 +443,8 @@ __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __res
       se[c][1 + (u - 2 * PK) / 2][(u & 1) ? PK - 1 : 0] = 0.f;
   }
   float ev[2][RPT][2];
-  float rv[RDREG ? 2 : 1][RDREG ? RPT : 1][2], dv[RDREG ? 2 : 1][RDREG ? RPT : 1][2];
+  const float omc = 1.f - omega;
+  float bv[RDREG ? 2 : 1][RDREG ? RPT : 1][2], av[RDREG ? 2 : 1][RDREG ? RPT : 1][2];
   float cE[2][2], cW[2][2], cN[RPT], cS[RPT];  // cE[m][s]: coefficient of the cell at i = 2k + s
 #pragma unroll
   for (int m = 0; m < 2; ++m) {
@@ -469,13 +488,14 @@ __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __res
         const int kk = tx + 32 * m, k = k0 + kk, i = 2 * k + ((c + j) & 1);
         const bool in = rowok && k >= 0 && i < nx;
         const size_t o = (size_t)(c * ny + j) * pk + k;
-        const float rr = in ? __ldcg(r + o) : 0.f, dd = in ? __ldcg(invd + o) : 0.f;
+        float aa, bb;  // a and b of the update
+        sor_ab(omega, in ? __ldcg(r + o) : 0.f, in ? __ldcg(invd + o) : 0.f, aa, bb);
         if constexpr (RDREG) {
-          rv[c][q][m] = rr;
-          dv[c][q][m] = dd;
+          bv[c][q][m] = bb;
+          av[c][q][m] = aa;
         } else {
-          sr[c][ly + 1][kk + 1] = rr;
-          sd[c][ly + 1][kk + 1] = dd;
+          sb[c][ly + 1][kk + 1] = bb;
+          sa[c][ly + 1][kk + 1] = aa;
         }
       }
   }
@@ -523,22 +543,16 @@ __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __res
         const float xOther = se[oc][ly + 1][kk + (s ? 2 : 0)];
         const float xN = q < RPT - 1 ? ev[oc][q < RPT - 1 ? q + 1 : q][m] : se[oc][ly + 2][kk + 1];
         const float xS = q > 0 ? ev[oc][q > 0 ? q - 1 : q][m] : se[oc][ly][kk + 1];
-        const float xE = s ? xOther : xSelf, xW = s ? xSelf : xOther;
-        float sum = (s ? cE[m][1] : cE[m][0]) * xE;
-        sum = fmaf(s ? cW[m][1] : cW[m][0], xW, sum);
-        sum = fmaf(cN[q], xN, sum);
-        sum = fmaf(cS[q], xS, sum);
-        float rr, dd;
+        float aa, bb;  // a and b of the update
         if constexpr (RDREG) {
-          rr = rv[c][q][m];
-          dd = dv[c][q][m];
+          bb = bv[c][q][m];
+          aa = av[c][q][m];
         } else {
-          rr = sr[c][ly + 1][kk + 1];
-          dd = sd[c][ly + 1][kk + 1];
+          bb = sb[c][ly + 1][kk + 1];
+          aa = sa[c][ly + 1][kk + 1];
         }
-        const float gs = (sum - rr) * dd;
-        const float x = ev[c][q][m];
-        const float nxv = fmaf(omega, gs - x, x);
+        const float nxv = sor_update(cN[q], xN, cS[q], xS, s ? cW[m][1] : cE[m][0], xSelf, s ? cE[m][1] : cW[m][0],
+                                     xOther, aa, bb, omc, ev[c][q][m]);
         ev[c][q][m] = nxv;
         se[c][ly + 1][kk + 1] = nxv;
       }
@@ -592,17 +606,200 @@ __device__ __forceinline__ void sor32_tile_v6(const Geo32& g, const float* __res
   }
 }
 
+// Fourth form (9, 10): as sor32_tile_v6 with the coefficients in registers,
+// but a thread owns the two adjacent packed columns 2 tx and 2 tx + 1 (not
+// tx and tx + 32).  Of a cell's W and E neighbours one is the thread's own
+// cell of the other colour in the same packed column and the other lies in
+// the next packed column, which is the thread's other column or, once per
+// row and half-sweep, the adjacent lane's (a shuffle): no shared memory is
+// read or written for W and E.  Shared memory carries only the first and
+// last row of each thread's run, which the thread rows above and below read
+// as N and S neighbours, stored as pairs.  At the region's left and right
+// edges the shuffle returns the lane's own value in place of the missing
+// neighbour; like any value spoiled by the region's finite size it moves
+// inwards by one cell per half-sweep and stays in the halo, and a cell
+// outside the domain (a = b = 0) stays zero whatever it reads.  The update
+// is sor_update with the same operands: identical iterates.  Form 10 puts
+// the barrier between the rows inside each run and its edge rows (as
+// form 8 does).
+template <int TY, int K, int NY>
+struct Sor32ShapeV9 {
+  static constexpr int LK = 64, HK = K / 2, TK = LK - 2 * HK, LY = TY + 2 * K;
+  static constexpr int RPT = LY / NY, PY = LY + 2;
+  static constexpr size_t smem = sizeof(float) * 2 * PY * LK;
+  static_assert(K % 4 == 0, "an even halo keeps a thread's column pair inside or outside the written tile");
+  static_assert(LY % NY == 0, "rows per thread must be whole");
+  static_assert(LY / NY >= 3, "a run needs a row between its first and last");
+};
+
+template <int TY, int K, int NY, bool SPLIT>
+__device__ __forceinline__ void sor32_tile_v9(const Geo32& g, const float* __restrict__ e_in, float* __restrict__ e_out,
+                                              const float* __restrict__ r, const float* __restrict__ invd,
+                                              float omega, int zero_init, int bx, int by, float* smem) {
+  using S = Sor32ShapeV9<TY, K, NY>;
+  constexpr int LK = S::LK, HK = S::HK, TK = S::TK, RPT = S::RPT, PY = S::PY;
+  constexpr unsigned FULL = 0xffffffffu;
+  float(*se)[PY][LK] = reinterpret_cast<float(*)[PY][LK]>(smem);  // [2][PY][LK], cell (ly, kk) at [ly + 1][kk]
+  const int nx = g.nx, ny = g.ny, pk = g.pk;
+  const int k0 = bx * TK - HK, j0 = by * TY - K;  // k0 is even, and so is every thread's first column
+  const int tx = threadIdx.x, ty = threadIdx.y, ly0 = ty * RPT, kk0 = 2 * tx;
+  for (int t = ty * 32 + tx; t < 2 * 2 * LK; t += 32 * NY) {  // zero rows above and below the region
+    const int c = t / (2 * LK), u = t % (2 * LK);
+    se[c][u < LK ? 0 : PY - 1][u % LK] = 0.f;
+  }
+  float ev[2][RPT][2], av[2][RPT][2], bv[2][RPT][2];
+  float cE[2][2], cW[2][2], cN[RPT], cS[RPT];  // cE[m][s]: coefficient of the cell at i = 2k + s
+  const float omc = 1.f - omega;
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const int k = k0 + kk0 + m;
+    const bool ok = k >= 0 && k < pk;
+    cE[m][0] = ok ? g.cE0[k] : 0.f;
+    cE[m][1] = ok ? g.cE1[k] : 0.f;
+    cW[m][0] = ok ? g.cW0[k] : 0.f;
+    cW[m][1] = ok ? g.cW1[k] : 0.f;
+  }
+  // early loads of r and 1/d, before the wait, on the argument given in
+  // sor32_tile_v6
+  if (zero_init) {
+    griddep_wait();
+    griddep_release();
+  }
+  const int kp = k0 + kk0;  // first packed column of the pair; rows hold pk (even) entries, so the pair is in one row
+  const bool pair_ok = kp >= 0 && kp < pk;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int ly = ly0 + q, j = j0 + ly;
+    const bool rowok = j >= 0 && j < ny;
+    cN[q] = rowok ? g.pN[j] : 0.f;
+    cS[q] = rowok ? g.pS[j] : 0.f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float2 rr = make_float2(0.f, 0.f), dd = make_float2(0.f, 0.f);
+      if (rowok && pair_ok) {
+        const size_t o = (size_t)(c * ny + j) * pk + kp;
+        rr = __ldcg(reinterpret_cast<const float2*>(r + o));
+        dd = __ldcg(reinterpret_cast<const float2*>(invd + o));
+      }
+      const int s = (c + j) & 1;
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const bool in = rowok && pair_ok && 2 * (kp + m) + s < nx;
+        sor_ab(omega, in ? (m ? rr.y : rr.x) : 0.f, in ? (m ? dd.y : dd.x) : 0.f, av[c][q][m], bv[c][q][m]);
+      }
+    }
+  }
+  if (!zero_init) {
+    griddep_wait();
+    griddep_release();
+  }
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int ly = ly0 + q, j = j0 + ly;
+    const bool rowok = j >= 0 && j < ny;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float2 x = make_float2(0.f, 0.f);
+      if (rowok && pair_ok && !zero_init)
+        x = __ldcg(reinterpret_cast<const float2*>(e_in + (size_t)(c * ny + j) * pk + kp));
+      const int s = (c + j) & 1;
+      ev[c][q][0] = (rowok && pair_ok && 2 * kp + s < nx) ? x.x : 0.f;
+      ev[c][q][1] = (rowok && pair_ok && 2 * (kp + 1) + s < nx) ? x.y : 0.f;
+      if (q == 0 || q == RPT - 1)
+        *reinterpret_cast<float2*>(&se[c][ly + 1][kk0]) = make_float2(ev[c][q][0], ev[c][q][1]);
+    }
+  }
+  __syncthreads();
+  // one half-sweep of colour C whose first row has parity S0, over the rows
+  // selected by PART (0 all, 1 inside the run, 2 its first and last row)
+  auto half_rows = [&](auto colour, auto start, auto part) {
+    constexpr int c = decltype(colour)::value, oc = c ^ 1, S0 = decltype(start)::value;
+    constexpr int PART = decltype(part)::value;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const bool edge = q == 0 || q == RPT - 1;
+      if constexpr (PART != 0) {
+        if ((PART == 2) != edge) continue;
+      }
+      const int s = S0 ^ (q & 1);
+      const int ly = ly0 + q;
+      // the neighbour across the packed column: W (column k - 1) if s = 0,
+      // else E (column k + 1)
+      float xo[2];
+      if (s) {
+        xo[0] = ev[oc][q][1];
+        xo[1] = __shfl_down_sync(FULL, ev[oc][q][0], 1);
+      } else {
+        xo[0] = __shfl_up_sync(FULL, ev[oc][q][1], 1);
+        xo[1] = ev[oc][q][0];
+      }
+      float2 nN = make_float2(0.f, 0.f), nS = make_float2(0.f, 0.f);
+      if (q == RPT - 1) nN = *reinterpret_cast<const float2*>(&se[oc][ly + 2][kk0]);
+      if (q == 0) nS = *reinterpret_cast<const float2*>(&se[oc][ly][kk0]);
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const float xN = q < RPT - 1 ? ev[oc][q < RPT - 1 ? q + 1 : q][m] : (m ? nN.y : nN.x);
+        const float xS = q > 0 ? ev[oc][q > 0 ? q - 1 : q][m] : (m ? nS.y : nS.x);
+        ev[c][q][m] = sor_update(cN[q], xN, cS[q], xS, s ? cW[m][1] : cE[m][0], ev[oc][q][m],
+                                 s ? cE[m][1] : cW[m][0], xo[m], av[c][q][m], bv[c][q][m], omc, ev[c][q][m]);
+      }
+      if (edge) *reinterpret_cast<float2*>(&se[c][ly + 1][kk0]) = make_float2(ev[c][q][0], ev[c][q][1]);
+    }
+  };
+  auto half = [&](auto colour, auto start) {
+    if constexpr (SPLIT) {
+      half_rows(colour, start, std::integral_constant<int, 1>{});
+      __syncthreads();
+      half_rows(colour, start, std::integral_constant<int, 2>{});
+    } else {
+      half_rows(colour, start, std::integral_constant<int, 0>{});
+      __syncthreads();
+    }
+  };
+  const int p0 = (j0 + ly0) & 1;  // parity of this thread's first row
+#pragma unroll 1
+  for (int h = 0; h < K; h += 2) {
+    if (p0) {
+      half(std::integral_constant<int, 0>{}, std::integral_constant<int, 1>{});
+      half(std::integral_constant<int, 1>{}, std::integral_constant<int, 0>{});
+    } else {
+      half(std::integral_constant<int, 0>{}, std::integral_constant<int, 0>{});
+      half(std::integral_constant<int, 1>{}, std::integral_constant<int, 1>{});
+    }
+  }
+  if (kk0 < HK || kk0 >= HK + TK || !pair_ok) return;  // the pair lies in the halo or outside the rows
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int ly = ly0 + q;
+    if (ly < K || ly >= K + TY) continue;
+    const int j = j0 + ly;
+    if (j < 0 || j >= ny) continue;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int s = (c + j) & 1;
+      float* dst = e_out + (size_t)(c * ny + j) * pk + kp;
+      if (2 * (kp + 1) + s < nx)
+        *reinterpret_cast<float2*>(dst) = make_float2(ev[c][q][0], ev[c][q][1]);
+      else if (2 * kp + s < nx)
+        dst[0] = ev[c][q][0];
+    }
+  }
+}
+
 // A tile shape: rows per tile, half-sweeps per launch, thread rows, form
-// (3: sor32_tile; 4: sor32_tile_v4 with r and 1/d in shared memory; 5: with
-// r and 1/d in registers; 6, 7: sor32_tile_v6 likewise; 8: as 7 with the
-// barrier between the inside rows of each thread's run and its edge rows)
+// (3: sor32_tile; 4: sor32_tile_v4 with a and b in shared memory; 5: with
+// a and b in registers; 6, 7: sor32_tile_v6 likewise; 8: as 7 with the
+// barrier between the inside rows of each thread's run and its edge rows;
+// 9, 10: sor32_tile_v9, without and with that split)
 // and minimum resident CTAs per SM.
 template <int TY_, int K_, int NY_, int V_, int MINB_>
 struct Cfg {
   static constexpr int TY = TY_, K = K_, NY = NY_, V = V_, MINB = MINB_;
   static constexpr int HK = (K + 1) / 2, TK = 64 - 2 * HK;
   static constexpr size_t smem =
-      std::conditional_t<V == 3, Sor32Shape<TY, K, NY>, Sor32ShapeV4<TY, K, NY, V == 5 || V >= 7>>::smem;
+      std::conditional_t<V == 3, Sor32Shape<TY, K, NY>,
+                         std::conditional_t<(V >= 9), Sor32ShapeV9<TY, K, NY>,
+                                            Sor32ShapeV4<TY, K, NY, V == 5 || V >= 7>>>::smem;
 };
 
 template <class C>
@@ -612,9 +809,11 @@ __device__ __forceinline__ void tile(const Geo32& g, const float* e_in, float* e
     sor32_tile<C::TY, C::K, C::NY>(g, e_in, e_out, r, invd, omega, zero_init, bx, by, smem);
   else if constexpr (C::V == 4 || C::V == 5)
     sor32_tile_v4<C::TY, C::K, C::NY, C::V == 5>(g, e_in, e_out, r, invd, omega, zero_init, bx, by, smem);
-  else
+  else if constexpr (C::V <= 8)
     sor32_tile_v6<C::TY, C::K, C::NY, C::V >= 7, C::V == 8>(g, e_in, e_out, r, invd, omega, zero_init, bx, by,
                                                               smem);
+  else
+    sor32_tile_v9<C::TY, C::K, C::NY, C::V == 10>(g, e_in, e_out, r, invd, omega, zero_init, bx, by, smem);
 }
 
 template <class C>
@@ -750,7 +949,9 @@ const Sor32Config kConfigs[] = {
     shape<Cfg<48, 8, 16, 7, 1>>(),  shape<Cfg<24, 4, 8, 7, 2>>(),   shape<Cfg<48, 8, 8, 6, 2>>(),
     shape<Cfg<48, 8, 8, 7, 1>>(),   shape<Cfg<40, 12, 8, 6, 2>>(),  shape<Cfg<80, 16, 16, 6, 1>>(),
     shape<Cfg<96, 16, 16, 6, 1>>(), shape<Cfg<64, 16, 16, 7, 1>>(), shape<Cfg<80, 16, 16, 7, 1>>(),
-    shape<Cfg<64, 16, 16, 8, 1>>(), shape<Cfg<80, 16, 16, 8, 1>>(),
+    shape<Cfg<64, 16, 16, 8, 1>>(), shape<Cfg<80, 16, 16, 8, 1>>(), shape<Cfg<80, 16, 16, 9, 1>>(),
+    shape<Cfg<80, 16, 16, 10, 1>>(), shape<Cfg<64, 16, 16, 10, 1>>(), shape<Cfg<48, 8, 16, 10, 1>>(),
+    shape<Cfg<32, 8, 8, 10, 2>>(),
 };
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 

@@ -117,7 +117,7 @@ def test_fp32_sweeps_reproduce_sor_iterates(nx, ny, hmin):
 
 @pytest.mark.parametrize("nx,ny,hmin", [(517, 263, 0.05), (2001, 1201, 0.006)])
 def test_every_sweep_shape_gives_identical_iterates(nx, ny, hmin):
-    """All tile shapes of the FP32 sweep kernel (both forms, every temporal
+    """All tile shapes of the FP32 sweep kernel (every form, every temporal
     blocking depth) perform the same red-black SOR updates in the same
     arithmetic order: 48 sweeps from the same start (one run of FP32 sweeps,
     48 being a whole number of launches for every shape) give bit-identical
