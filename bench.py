@@ -144,11 +144,12 @@ def network_roofline(learned, cfg, stream, peaks, peak_src, reps=10, warm=3):
     flops = unet_forward_flops(learned["meta"].get("widths", net.widths), H, W)
     achieved = flops / (ms * 1e-3) / 1e12
     peak = peaks.get("bf16_tflops", 1900.0)
-    return {"kernel": "U-Net forward (k_conv3x3 BF16 mma.sync, pooling, upsampling)", "widths": list(net.widths),
+    return {"kernel": "U-Net forward (k_conv3x3_tc: BF16 tcgen05.mma, TMEM accumulators, TMA-staged operands; "
+                      "pooling, upsampling)", "widths": list(net.widths),
             "input": [H, W], "gflop": flops / 1e9, "ms": ms, "achieved_tflops": achieved,
             "peak_tflops": peak, "frac": achieved / peak,
-            "peak_note": f"BF16 dense tensor peak ({peak_src}, burst); small channel counts (4-128) leave the "
-                         f"convolutions bound by shared memory, not by the tensor pipe"}
+            "peak_note": f"BF16 dense tensor peak ({peak_src}, burst); the whole forward pass, whose layers have "
+                         f"16-128 channels"}
 
 
 def load_peaks():

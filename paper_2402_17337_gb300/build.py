@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libibm.so")
-SOURCES = ["ibm_api.cu", "k_step.cu", "k_sor.cu", "k_mixed.cu", "k_noalloc.cu", "k_mg.cu", "k_nn.cu", "unet.cu", "k_ws.cu"]
+SOURCES = ["ibm_api.cu", "k_step.cu", "k_sor.cu", "k_mixed.cu", "k_noalloc.cu", "k_mg.cu", "k_nn.cu", "k_conv_tc.cu",
+           "unet.cu", "k_ws.cu"]
 HEADERS = ["ibm_internal.h", "nn_internal.h", os.path.join("..", "..", "include", "ibm.h")]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1,0 +1,411 @@
+// 3x3 convolutions of the warm-start U-Net on the fifth-generation tensor
+// cores: tcgen05.mma with the accumulator in tensor memory, operands staged
+// in shared memory by the tensor memory accelerator.
+//
+// The convolution is an implicit GEMM.  One CTA computes a tile of M = 128
+// output pixels (R image rows of TW pixels, R TW = 128) times NT output
+// channels; K runs over the 9 taps and the input channels, 16 channels (one
+// K = 16 MMA) per tap and chunk.  Operands use the K-major layout without
+// swizzling, whose unit is the core matrix: 8 rows (pixels, or output
+// channels) of 16 bytes (8 channels) stored contiguously.
+//
+//   A (pixels x channels): the input halo tile is loaded by TMA from a 3-D
+//   tensor map over the activation view (channels, x, y), one box of 8
+//   channels per channel group, so shared memory holds [row][pixel][8 ch],
+//   16 bytes per pixel.  A tap's operand is a window of that tile: with one
+//   image row per tile (R = 1) the box spans TW + 2 pixels and a tap's
+//   shift (dy, dx) moves the descriptor's start by dy rows and dx pixels
+//   (16 bytes each); with R > 1 rows a pixel shift would wrap between rows,
+//   so three boxes are loaded, each already shifted by its dx, and a tap
+//   moves the start by dy rows only.  Out-of-image pixels are zero-filled by
+//   the TMA unit, which is the convolution's zero padding.
+//   B (output channels x channels): weights pre-packed (k_pack_conv_weights)
+//   into the exact shared-memory image of a chunk, copied by one bulk copy.
+//
+// One thread issues the TMA loads and the MMAs (two-stage pipeline on
+// mbarriers: full = data landed, empty = the MMAs reading a stage are done,
+// signalled by tcgen05.commit); the four warps then read the accumulator
+// from tensor memory (warp w owns lanes 32 w .. 32 w + 31, i.e. pixels) and
+// apply bias and ReLU.  Every wait is bounded: a wait that gives up sets a
+// flag in mapped host memory and the CTA skips the rest of its work.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "ibm_internal.h"
+#include "nn_internal.h"
+
+namespace ibm {
+namespace nn {
+
+namespace {
+
+constexpr int TC_M = 128;
+constexpr int TC_STAGES = 2;
+constexpr int TC_SMEM = 200 * 1024;  // dynamic shared memory of every launch
+constexpr long long TC_WAIT_CYCLES = 4000000000ll;  // about 2 s at the SM clock
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// waits for the phase with the given parity to complete; false if it has
+// not completed within TC_WAIT_CYCLES
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity))
+    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor, K-major without swizzling: start address,
+// leading byte offset (between the two core matrices of a K = 16 slice),
+// stride byte offset (between 8-row groups), descriptor version 1
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = n, M = 128
+__device__ __forceinline__ uint32_t instr_desc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// 16 consecutive FP32 columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Geometry of one launch (host-computed).
+struct TcGeom {
+  int TW, R;           // pixels per tile row, rows per tile (TW R = 128)
+  int copies, boxw;    // A boxes per channel group (1 or 3), pixels per box row
+  int a_region;        // bytes of one A box in shared memory (padded to 128)
+  int a_bytes, b_bytes, stage_bytes, tx_bytes;
+  int NT, tmem_cols, nchunks;
+};
+
+// Y[.., co] = act(sum over taps and channels + bias), the tile of CTA
+// (blockIdx.x: TW-pixel column, blockIdx.y: R-row band, blockIdx.z: NT
+// output channels).  wpk: this convolution's packed weights.
+template <bool RELU>
+__global__ void __launch_bounds__(128, 1)
+    k_conv3x3_tc(const __grid_constant__ CUtensorMap tmX, const bf16* __restrict__ wpk, const float* __restrict__ bias,
+                 bf16* __restrict__ Y, int ldy, int offy, float* __restrict__ yf, int H, int W, int Cout, TcGeom G,
+                 unsigned int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bar_full[TC_STAGES], bar_empty[TC_STAGES], bar_acc;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int failed;
+  const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int x0 = blockIdx.x * G.TW, y0 = blockIdx.y * G.R, n0 = blockIdx.z * G.NT;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(G.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 32) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bar_acc), 1);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = instr_desc(G.NT);
+    const size_t wchunk = (size_t)2 * 9 * G.NT * 8;  // bf16 elements of one chunk's weights
+    const bf16* wtile = wpk + (size_t)blockIdx.z * G.nchunks * wchunk;
+    auto load = [&](int ch, int s) {
+      const uint32_t st = sbase + s * G.stage_bytes, bar = smem_u32(&bar_full[s]);
+      mbar_expect_tx(bar, G.tx_bytes);
+      for (int cp = 0; cp < G.copies; ++cp)
+        for (int g = 0; g < 2; ++g)
+          tma_load_3d(st + (cp * 2 + g) * G.a_region, &tmX, ch * 16 + g * 8, G.copies == 1 ? x0 - 1 : x0 + cp - 1,
+                      y0 - 1, bar);
+      bulk_load(st + G.a_bytes, wtile + ch * wchunk, G.b_bytes, bar);
+    };
+    const int npre = G.nchunks < TC_STAGES ? G.nchunks : TC_STAGES;
+    for (int s = 0; s < npre; ++s) load(s, s);
+    int issued = npre;  // chunks whose loads were issued
+    bool ok = true;
+    for (int ch = 0; ch < G.nchunks; ++ch) {
+      const int s = ch % TC_STAGES;
+      const uint32_t par = (uint32_t)(ch / TC_STAGES) & 1u;
+      if (!mbar_wait(smem_u32(&bar_full[s]), par)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t st = sbase + s * G.stage_bytes;
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;
+        const uint32_t a = G.copies == 1 ? st + (dy * G.boxw + dx) * 16 : st + dx * 2 * G.a_region + dy * G.TW * 16;
+        // B: [tap][8-row group of output channels][channel group][8 rows][16 bytes]
+        const uint32_t b = st + G.a_bytes + tap * G.NT * 32;
+        tc_mma(tmem, smem_desc(a, G.a_region, 128), smem_desc(b, 128, 256), idesc, (ch | tap) != 0);
+      }
+      tc_commit(smem_u32(&bar_empty[s]));
+      if (ch + TC_STAGES < G.nchunks) {
+        if (!mbar_wait(smem_u32(&bar_empty[s]), par)) {
+          ok = false;
+          break;
+        }
+        load(ch + TC_STAGES, s);
+        ++issued;
+      }
+    }
+    tc_commit(smem_u32(&bar_acc));
+    if (!ok) {
+      // wait (bounded) for every load still in flight before giving up
+      failed = 1;
+      for (int ch = 0; ch < issued; ++ch) mbar_wait(smem_u32(&bar_full[ch % TC_STAGES]), (ch / TC_STAGES) & 1u);
+    }
+  }
+  __syncwarp();
+  const bool acc_ok = mbar_wait(smem_u32(&bar_acc), 0);
+  tc_fence_after();
+  __syncthreads();  // 'failed' is read below
+  const bool good = acc_ok && !failed;
+  if (!good && threadIdx.x == 0) atomicOr_system(err, 1u);
+
+  const int m = warp * 32 + lane;
+  const int y = y0 + m / G.TW, x = x0 + m % G.TW;
+  const bool valid = good && x < W && y < H;
+  const size_t p = (size_t)y * W + x;
+  for (int c0 = 0; c0 < G.NT; c0 += 16) {
+    float v[16];
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    const int co = n0 + c0;
+    if (!valid || co >= Cout) continue;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      float t = v[j] + (bias ? bias[co + j] : 0.f);
+      v[j] = RELU ? fmaxf(t, 0.f) : t;
+    }
+    uint4 o[2];
+    uint32_t* ow = reinterpret_cast<uint32_t*>(o);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      ow[j] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(Y + p * ldy + offy + co);
+    dst[0] = o[0];
+    dst[1] = o[1];
+    if (yf) {
+      float4* f = reinterpret_cast<float4*>(yf + p * Cout + co);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) f[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G.tmem_cols) : "memory");
+  }
+}
+
+// Packed weights of a convolution with Cin input and Cout output channels:
+// for output-channel tile t (NT channels) and input-channel chunk ch (16
+// channels), the chunk's shared-memory image
+//   [tap 9][8-row group NT/8][channel group 2][row 8][8 channels]
+// of W'[co][tap][ci], zero for co >= Cout.  W' is the layer's weights
+// w[Cout][9][Cin]; with flip it is the data-gradient operator of a layer
+// whose weights are w[Cin][9][Cout]: W'[co][tap][ci] = w[ci][8 - tap][co].
+__global__ void k_pack_conv_weights(int Cin, int Cout, int NT, int ntiles, const bf16* __restrict__ w,
+                                    bf16* __restrict__ wpk, int flip) {
+  const int nchunks = Cin / 16;
+  const long n = (long)ntiles * nchunks * 9 * NT * 16;
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    const int e = (int)(k & 7), row = (int)((k >> 3) & 7), g = (int)((k >> 6) & 1);
+    long r = k >> 7;
+    const int ngrp = (int)(r % (NT / 8));
+    r /= NT / 8;
+    const int tap = (int)(r % 9);
+    r /= 9;
+    const int ch = (int)(r % nchunks), t = (int)(r / nchunks);
+    const int co = t * NT + ngrp * 8 + row, ci = ch * 16 + g * 8 + e;
+    bf16 v = __float2bfloat16_rn(0.f);
+    if (co < Cout) v = flip ? w[((size_t)ci * 9 + (8 - tap)) * Cout + co] : w[((size_t)co * 9 + tap) * Cin + ci];
+    wpk[k] = v;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// a flag the kernels set (system-scope atomic) when a wait gives up; mapped
+// host memory, so the host reads it without a device synchronisation
+unsigned int* error_flag(unsigned int** dev) {
+  static unsigned int* host = nullptr;
+  static unsigned int* devp = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* h = nullptr;
+    if (cudaHostAlloc(&h, sizeof(unsigned int), cudaHostAllocMapped) == cudaSuccess) {
+      host = static_cast<unsigned int*>(h);
+      *host = 0u;
+      void* d = nullptr;
+      if (cudaHostGetDevicePointer(&d, h, 0) == cudaSuccess) devp = static_cast<unsigned int*>(d);
+    }
+  });
+  *dev = devp;
+  return host;
+}
+
+int pow2_at_least(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+int conv_tile_channels(int Cout) { return Cout <= 128 ? Cout : 128; }
+
+size_t packed_conv_weights(int Cin, int Cout) {
+  const int NT = conv_tile_channels(Cout), ntiles = (Cout + NT - 1) / NT;
+  return (size_t)ntiles * NT * 9 * Cin;
+}
+
+void pack_conv_weights(cudaStream_t s, int Cin, int Cout, const bf16* w, bf16* wpk, bool flip) {
+  const int NT = conv_tile_channels(Cout), ntiles = (Cout + NT - 1) / NT;
+  const long n = (long)packed_conv_weights(Cin, Cout);
+  long b = (n + 255) / 256;
+  k_pack_conv_weights<<<(int)(b > 4096 ? 4096 : b), 256, 0, s>>>(Cin, Cout, NT, ntiles, w, wpk, flip ? 1 : 0);
+}
+
+bool conv_tc_failed() {
+  unsigned int* dev = nullptr;
+  unsigned int* host = error_flag(&dev);
+  return host && *reinterpret_cast<volatile unsigned int*>(host) != 0u;
+}
+
+int conv3x3(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* X, int ldx, int offx, const bf16* wpk,
+            const float* bias, bf16* Y, int ldy, int offy, bool relu, float* yf) {
+  if (Cin % 16 || Cout % 16 || ldx % 8 || offx % 8 || ldy % 8 || offy % 8) {
+    set_last_error("convolution channel counts and slices must be multiples of 16 and 8");
+    return -1;
+  }
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  unsigned int* err_dev = nullptr;
+  error_flag(&err_dev);
+  if (!enc || !err_dev) {
+    set_last_error("cuTensorMapEncodeTiled or the mapped error flag is unavailable");
+    return -1;
+  }
+  TcGeom G{};
+  G.TW = W >= TC_M ? TC_M : (pow2_at_least(W) < 8 ? 8 : pow2_at_least(W));
+  G.R = TC_M / G.TW;
+  G.copies = G.R == 1 ? 1 : 3;
+  G.boxw = G.R == 1 ? G.TW + 2 : G.TW;
+  const int rows = G.R + 2;
+  G.a_region = (rows * G.boxw * 16 + 127) / 128 * 128;
+  G.a_bytes = G.copies * 2 * G.a_region;
+  G.NT = conv_tile_channels(Cout);
+  G.b_bytes = 9 * G.NT * 32;
+  G.stage_bytes = (G.a_bytes + G.b_bytes + 1023) / 1024 * 1024;
+  G.tx_bytes = G.copies * 2 * rows * G.boxw * 16 + G.b_bytes;
+  G.tmem_cols = pow2_at_least(G.NT < 32 ? 32 : G.NT);
+  G.nchunks = Cin / 16;
+  if (TC_STAGES * G.stage_bytes + 1024 > TC_SMEM) {
+    set_last_error("convolution tile does not fit in shared memory");
+    return -1;
+  }
+  CUtensorMap map;
+  cuuint64_t dims[3] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H};
+  cuuint64_t strides[2] = {(cuuint64_t)ldx * 2, (cuuint64_t)W * ldx * 2};
+  cuuint32_t box[3] = {8, (cuuint32_t)G.boxw, (cuuint32_t)rows};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(X + offx), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) {
+    set_last_error("cuTensorMapEncodeTiled rejected an activation view");
+    return -1;
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_conv3x3_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    cudaFuncSetAttribute(k_conv3x3_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    attr = true;
+  }
+  dim3 grd((W + G.TW - 1) / G.TW, (H + G.R - 1) / G.R, (Cout + G.NT - 1) / G.NT);
+  if (relu)
+    k_conv3x3_tc<true><<<grd, 128, TC_SMEM, s>>>(map, wpk, bias, Y, ldy, offy, yf, H, W, Cout, G, err_dev);
+  else
+    k_conv3x3_tc<false><<<grd, 128, TC_SMEM, s>>>(map, wpk, bias, Y, ldy, offy, yf, H, W, Cout, G, err_dev);
+  return 0;
+}
+
+}  // namespace nn
+}  // namespace ibm

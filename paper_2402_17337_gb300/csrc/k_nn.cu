@@ -7,11 +7,10 @@
 // are formed without copies.  Weights of a 3x3 convolution are [Cout][9][Cin]
 // (tap = 3*(dy+1) + (dx+1)), i.e. K-contiguous columns of the GEMM operand B.
 //
-// The convolutions are implicit GEMMs on the tensor cores (mma.sync
-// m16n8k16, BF16 inputs, FP32 accumulators): forward and data-gradient use
-// one kernel (the data gradient is the forward convolution of the output
-// gradient with the tap-flipped, channel-transposed weights), and the weight
-// gradient reduces over pixels with split-K atomics.
+// The forward and data-gradient convolutions run on the tcgen05 tensor cores
+// (k_conv_tc.cu).  The weight gradient here is a GEMM reduced over pixels on
+// the warp-level tensor-core path (mma.sync m16n8k16, BF16 inputs, FP32
+// accumulators), split over pixel chunks with atomics.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -26,14 +25,6 @@ namespace {
 
 __device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ inline void ldsm_x4(uint32_t (&r)[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
-}
-__device__ inline void ldsm_x2(uint32_t (&r)[2], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(smem_u32(p)));
-}
 __device__ inline void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
@@ -53,89 +44,7 @@ __device__ inline void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uin
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-constexpr int CP = 64;        // pixels per CTA (one row segment)
-constexpr int CN = 64;        // output channels per CTA
-constexpr int CK = 16;        // input channels per K chunk
-constexpr int SROW = CK + 8;  // padded smem row (bf16): 48 bytes, conflict-free ldmatrix
-
-// 3x3 convolution, zero padding, Y = act(conv(X, Wt) + bias).
-// Grid (ceil(W/64), H, ceil(Cout/64)), block 128 (4 warps x 16 pixels).
-// Cin must be a multiple of 16.  If yf is non-null the FP32 result is
-// written there too (dense [H][W][Cout]).
-template <bool RELU>
-__global__ void __launch_bounds__(128) k_conv3x3(int H, int W, int Cin, int Cout, const bf16* __restrict__ X, int ldx,
-                                                 int offx, const bf16* __restrict__ Wt, const float* __restrict__ bias,
-                                                 bf16* __restrict__ Y, int ldy, int offy, float* __restrict__ yf) {
-  __shared__ __align__(16) bf16 sA[3][CP + 2][SROW];
-  __shared__ __align__(16) bf16 sB[CN][9][SROW];
-  const int y = blockIdx.y, x0 = blockIdx.x * CP, co0 = blockIdx.z * CN;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  float acc[CN / 8][4];
-#pragma unroll
-  for (int n = 0; n < CN / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-  for (int ci0 = 0; ci0 < Cin; ci0 += CK) {
-    // input halo tile: rows y-1..y+1, pixels x0-1..x0+CP, 16 channels (two 16-byte halves)
-    for (int t = tid; t < 3 * (CP + 2) * 2; t += 128) {
-      int half = t & 1, p = (t >> 1) % (CP + 2), r = (t >> 1) / (CP + 2);
-      int yy = y + r - 1, xx = x0 + p - 1;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-        v = *reinterpret_cast<const uint4*>(X + ((size_t)yy * W + xx) * ldx + offx + ci0 + 8 * half);
-      *reinterpret_cast<uint4*>(&sA[r][p][8 * half]) = v;
-    }
-    // weights: CN output channels x 9 taps x 16 input channels
-    for (int t = tid; t < CN * 9 * 2; t += 128) {
-      int half = t & 1, tap = (t >> 1) % 9, n = (t >> 1) / 9;
-      int co = co0 + n;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (co < Cout) v = *reinterpret_cast<const uint4*>(Wt + ((size_t)co * 9 + tap) * Cin + ci0 + 8 * half);
-      *reinterpret_cast<uint4*>(&sB[n][tap][8 * half]) = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int dy = tap / 3, dx = tap % 3;
-      uint32_t a[4];
-      // rows: pixels warp*16 + (lane & 15), shifted by dx; k half by lane >> 4
-      ldsm_x4(a, &sA[dy][warp * 16 + (lane & 15) + dx][(lane >> 4) * 8]);
-#pragma unroll
-      for (int n = 0; n < CN / 8; ++n) {
-        uint32_t b[2];
-        ldsm_x2(b, &sB[n * 8 + (lane & 7)][tap][((lane >> 3) & 1) * 8]);
-        mma_bf16(acc[n], a, b);
-      }
-    }
-    __syncthreads();
-  }
-  // epilogue: rows (pixels) lane>>2 and +8, columns (channels) 2*(lane&3), +1
-  const int g = lane >> 2, tq = lane & 3;
-#pragma unroll
-  for (int n = 0; n < CN / 8; ++n) {
-#pragma unroll
-    for (int hr = 0; hr < 2; ++hr) {
-      const int x = x0 + warp * 16 + g + 8 * hr;
-      const int co = co0 + n * 8 + 2 * tq;
-      if (x >= W || co >= Cout) continue;
-      float v0 = acc[n][2 * hr] + (bias ? bias[co] : 0.f);
-      float v1 = acc[n][2 * hr + 1] + (bias && co + 1 < Cout ? bias[co + 1] : 0.f);
-      if (RELU) {
-        v0 = fmaxf(v0, 0.f);
-        v1 = fmaxf(v1, 0.f);
-      }
-      const size_t o = ((size_t)y * W + x);
-      if (co + 1 < Cout) {
-        *reinterpret_cast<__nv_bfloat162*>(Y + o * ldy + offy + co) = __floats2bfloat162_rn(v0, v1);
-        if (yf) {
-          yf[o * Cout + co] = v0;
-          yf[o * Cout + co + 1] = v1;
-        }
-      } else {
-        Y[o * ldy + offy + co] = __float2bfloat16_rn(v0);
-        if (yf) yf[o * Cout + co] = v0;
-      }
-    }
-  }
-}
+constexpr int CN = 64;  // output channels per CTA of the weight gradient
 
 // Weight gradient of a 3x3 convolution for one tap:
 //   dW[co][tap][ci] += sum_p G[p][co] * X[p + shift(tap)][ci]
@@ -213,15 +122,6 @@ __global__ void __launch_bounds__(128) k_conv3x3_wgrad(int H, int W, int Cin, in
 }
 
 // ---------------------------------------------------------- elementwise
-
-// weights for the data gradient: Wt'[ci][tap'][co] = Wt[co][8 - tap'][ci] (BF16)
-__global__ void k_flip_weights(int Cin, int Cout, const bf16* __restrict__ w, bf16* __restrict__ wt) {
-  long n = (long)Cin * 9 * Cout;
-  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
-    int co = (int)(k % Cout), tap = (int)((k / Cout) % 9), ci = (int)(k / ((long)Cout * 9));
-    wt[((long)ci * 9 + tap) * Cout + co] = w[((long)co * 9 + (8 - tap)) * Cin + ci];
-  }
-}
 
 // G[p][c] (a slice) *= (Y[p][c] > 0): gradient through ReLU, in place
 __global__ void k_relu_grad(long npix, int C, bf16* __restrict__ G, int ldg, int offg, const bf16* __restrict__ Y,
@@ -362,15 +262,6 @@ inline int grid1(long n) {
 
 }  // namespace
 
-void conv3x3(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* X, int ldx, int offx, const bf16* Wt,
-             const float* bias, bf16* Y, int ldy, int offy, bool relu, float* yf) {
-  dim3 grd((W + CP - 1) / CP, H, (Cout + CN - 1) / CN);
-  if (relu)
-    k_conv3x3<true><<<grd, 128, 0, s>>>(H, W, Cin, Cout, X, ldx, offx, Wt, bias, Y, ldy, offy, yf);
-  else
-    k_conv3x3<false><<<grd, 128, 0, s>>>(H, W, Cin, Cout, X, ldx, offx, Wt, bias, Y, ldy, offy, yf);
-}
-
 void conv3x3_wgrad(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* G, int ldg, int offg, const bf16* X,
                    int ldx, int offx, float* dW) {
   const long nchunks = (long)H * ((W + WP - 1) / WP);
@@ -378,9 +269,6 @@ void conv3x3_wgrad(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* 
   k_conv3x3_wgrad<<<grd, 128, 0, s>>>(H, W, Cin, Cout, G, ldg, offg, X, ldx, offx, dW);
 }
 
-void flip_weights(cudaStream_t s, int Cin, int Cout, const bf16* w, bf16* wt) {
-  k_flip_weights<<<grid1((long)Cin * 9 * Cout), 256, 0, s>>>(Cin, Cout, w, wt);
-}
 void relu_grad(cudaStream_t s, long npix, int C, bf16* G, int ldg, int offg, const bf16* Y, int ldy, int offy) {
   k_relu_grad<<<grid1(npix * C), 256, 0, s>>>(npix, C, G, ldg, offg, Y, ldy, offy);
 }

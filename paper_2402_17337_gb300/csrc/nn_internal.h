@@ -1,4 +1,4 @@
-// Launchers of the U-Net kernels (k_nn.cu).  Activations are BF16 NHWC; a
+// Launchers of the U-Net kernels (k_nn.cu, k_conv_tc.cu).  Activations are BF16 NHWC; a
 // view of an activation is (buffer, channels per pixel ld, first channel off).
 #pragma once
 #include <cuda_bf16.h>
@@ -9,14 +9,23 @@ namespace nn {
 
 using bf16 = __nv_bfloat16;
 
-// Y = act(conv3x3(X, Wt) + bias), zero padding; Cin % 16 == 0; yf: optional
-// dense FP32 copy of the output [H][W][Cout].
-void conv3x3(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* X, int ldx, int offx, const bf16* Wt,
-             const float* bias, bf16* Y, int ldy, int offy, bool relu, float* yf);
+// Y = act(conv3x3(X, W) + bias), zero padding, on the tcgen05 tensor cores
+// (k_conv_tc.cu); Cin, Cout % 16 == 0, ldx, offx, ldy, offy % 8 == 0; wpk:
+// the weights packed by pack_conv_weights; yf: optional dense FP32 copy of the
+// output [H][W][Cout].  Returns 0, or -1 with ibm_last_error set.
+int conv3x3(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* X, int ldx, int offx, const bf16* wpk,
+            const float* bias, bf16* Y, int ldy, int offy, bool relu, float* yf);
+// elements of the packed weights of a convolution with Cin inputs and Cout
+// outputs, and the packing of w[Cout][9][Cin] (flip: of the data-gradient
+// operator of a layer with weights w[Cin][9][Cout], W'[co][tap][ci] =
+// w[ci][8 - tap][co])
+size_t packed_conv_weights(int Cin, int Cout);
+void pack_conv_weights(cudaStream_t s, int Cin, int Cout, const bf16* w, bf16* wpk, bool flip);
+// true once a convolution kernel has given up a bounded wait
+bool conv_tc_failed();
 // dW[co][tap][ci] += sum_p G[p][co] X[p + shift(tap)][ci]
 void conv3x3_wgrad(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* G, int ldg, int offg, const bf16* X,
                    int ldx, int offx, float* dW);
-void flip_weights(cudaStream_t s, int Cin, int Cout, const bf16* w, bf16* wt);
 void relu_grad(cudaStream_t s, long npix, int C, bf16* G, int ldg, int offg, const bf16* Y, int ldy, int offy);
 void avgpool(cudaStream_t s, int H, int W, int C, const bf16* X, int ldx, int offx, bf16* Y, int ldy, int offy);
 void avgpool_grad(cudaStream_t s, int H, int W, int C, const bf16* dY, int ldy, int offy, bf16* dX, int ldx, int offx,

@@ -27,7 +27,8 @@ namespace {
 struct Conv {
   int cin, cout;
   bool relu;
-  size_t w, b;  // offsets of weights [cout][9][cin] and bias [cout] in the parameter vector
+  size_t w, b;     // offsets of weights [cout][9][cin] and bias [cout] in the parameter vector
+  size_t pk, pkf;  // offsets of the packed forward and data-gradient weights
 };
 
 // a view of an activation: buffer, channels per pixel, first channel, channels
@@ -50,7 +51,10 @@ struct ibm_unet {
   std::vector<Conv> conv;
   size_t nparam = 0;
   float *pw = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;  // FP32 master, gradient, Adam moments
-  bf16 *wb = nullptr, *wflip = nullptr;                                // BF16 weights, flipped copies
+  bf16* wb = nullptr;                                                  // BF16 weights
+  bf16 *wpk = nullptr, *wpkf = nullptr;  // packed for the tensor-core convolutions: forward, data gradient
+  size_t npk = 0, npkf = 0;
+  bool wdirty = true;  // wb changed since the packed copies were made
   long long adam_t = 0;
   // activations for the current size
   int H = 0, W = 0;
@@ -62,7 +66,7 @@ struct ibm_unet {
 
   ~ibm_unet() {
     free_acts();
-    void* ps[] = {pw, grad, m, v, wb, wflip, loss_d};
+    void* ps[] = {pw, grad, m, v, wb, wpk, wpkf, loss_d};
     for (void* p : ps)
       if (p) cudaFree(p);
   }
@@ -181,14 +185,27 @@ int level_of(ibm_unet* n, const Act& a) {
   return a.p == n->e3 ? 3 : 0;
 }
 
-void forward(ibm_unet* n, cudaStream_t s) {
+// packed copies of the BF16 weights for the convolution kernels, after the
+// weights changed (creation, new parameters, an Adam step)
+void ensure_packed(ibm_unet* n, cudaStream_t s) {
+  if (!n->wdirty) return;
+  for (const Conv& c : n->conv) {
+    pack_conv_weights(s, c.cin, c.cout, n->wb + c.w, n->wpk + c.pk, false);
+    pack_conv_weights(s, c.cout, c.cin, n->wb + c.w, n->wpkf + c.pkf, true);
+  }
+  n->wdirty = false;
+}
+
+int forward(ibm_unet* n, cudaStream_t s) {
   const int* w = n->w;
   std::vector<Edge> E = edges(n);
+  ensure_packed(n, s);
+  int rc = 0;
   auto run = [&](const Edge& e) {
     const Conv& c = n->conv[e.conv];
     Level& L = n->lv[level_of(n, e.x)];
-    conv3x3(s, L.H, L.W, c.cin, c.cout, e.x.p, e.x.ld, e.x.off, n->wb + c.w, n->pw + c.b, e.y.p, e.y.ld, e.y.off,
-            c.relu, e.conv == 14 ? n->outf : nullptr);
+    rc |= conv3x3(s, L.H, L.W, c.cin, c.cout, e.x.p, e.x.ld, e.x.off, n->wpk + c.pk, n->pw + c.b, e.y.p, e.y.ld,
+                  e.y.off, c.relu, e.conv == 14 ? n->outf : nullptr);
   };
   // encoder
   for (int l = 0; l < 4; ++l) {
@@ -208,11 +225,12 @@ void forward(ibm_unet* n, cudaStream_t s) {
     run(E[k + 1]);
   }
   run(E[14]);
+  return rc;
 }
 
 // one conv's backward: mask the output gradient, accumulate dW and db, and
 // write the input gradient (unless it is the network input)
-void conv_backward(ibm_unet* n, const Edge& e, cudaStream_t s, bool need_dx) {
+int conv_backward(ibm_unet* n, const Edge& e, cudaStream_t s, bool need_dx) {
   const Conv& c = n->conv[e.conv];
   Level& L = n->lv[level_of(n, e.x)];
   Act gy = grad_of(n, e.y), gx = grad_of(n, e.x);
@@ -221,20 +239,19 @@ void conv_backward(ibm_unet* n, const Edge& e, cudaStream_t s, bool need_dx) {
   conv3x3_wgrad(s, L.H, L.W, c.cin, c.cout, gy.p, gy.ld, gy.off, e.x.p, e.x.ld, e.x.off, n->grad + c.w);
   bias_grad(s, npix, c.cout, gy.p, gy.ld, gy.off, n->grad + c.b);
   if (need_dx)
-    conv3x3(s, L.H, L.W, c.cout, c.cin, gy.p, gy.ld, gy.off, n->wflip + c.w, nullptr, gx.p, gx.ld, gx.off, false,
-            nullptr);
+    return conv3x3(s, L.H, L.W, c.cout, c.cin, gy.p, gy.ld, gy.off, n->wpkf + c.pkf, nullptr, gx.p, gx.ld, gx.off,
+                   false, nullptr);
+  return 0;
 }
 
-void backward(ibm_unet* n, cudaStream_t s) {
+int backward(ibm_unet* n, cudaStream_t s) {
   const int* w = n->w;
   std::vector<Edge> E = edges(n);
-  // flipped weights for the data gradients
-  for (const Conv& c : n->conv) flip_weights(s, c.cin, c.cout, n->wb + c.w, n->wflip + c.w);
-  conv_backward(n, E[14], s, true);  // head -> d(d0)
+  int rc = conv_backward(n, E[14], s, true);  // head -> d(d0)
   for (int l = 0, k = 12; l <= 2; ++l, k -= 2) {
     Level& L = n->lv[l];
-    conv_backward(n, E[k + 1], s, true);  // d(d_l) -> d(bb_l)
-    conv_backward(n, E[k], s, true);      // d(bb_l) -> d(cat_l), both parts
+    rc |= conv_backward(n, E[k + 1], s, true);  // d(d_l) -> d(bb_l)
+    rc |= conv_backward(n, E[k], s, true);      // d(bb_l) -> d(cat_l), both parts
     // the upsampled part of cat_l comes from d_{l+1} (or e3)
     if (l < 2)
       upsample_grad(s, L.H, L.W, L.cup, L.gcat, L.cup + w[l], 0, n->lv[l + 1].gd, L.cup, 0, false);
@@ -244,13 +261,14 @@ void backward(ibm_unet* n, cudaStream_t s) {
   // encoder, from the bottom: e_l's gradient is in the skip slice of gcat_l
   // (decoder path) plus the pooling path of level l+1
   for (int l = 3; l >= 0; --l) {
-    conv_backward(n, E[2 * l + 1], s, true);   // d(e_l) -> d(a_l)
-    conv_backward(n, E[2 * l], s, l > 0);       // d(a_l) -> d(in_l)
+    rc |= conv_backward(n, E[2 * l + 1], s, true);  // d(e_l) -> d(a_l)
+    rc |= conv_backward(n, E[2 * l], s, l > 0);      // d(a_l) -> d(in_l)
     if (l > 0) {
       Level& P = n->lv[l - 1];
       avgpool_grad(s, P.H, P.W, w[l - 1], n->lv[l].gin, w[l - 1], 0, P.gcat, P.cup + w[l - 1], P.cup, true);
     }
   }
+  return rc;
 }
 
 }  // namespace
@@ -265,10 +283,12 @@ int ibm_unet_create(const int widths[4], unsigned long long seed, ibm_unet** out
   std::memcpy(n->w, widths, sizeof(n->w));
   const int* w = n->w;
   auto add = [&](int cin, int cout, bool relu) {
-    Conv c{cin, cout, relu, n->nparam, 0};
+    Conv c{cin, cout, relu, n->nparam, 0, n->npk, n->npkf};
     n->nparam += (size_t)cout * 9 * cin;
     c.b = n->nparam;
     n->nparam += cout;
+    n->npk += packed_conv_weights(cin, cout);
+    n->npkf += packed_conv_weights(cout, cin);
     n->conv.push_back(c);
   };
   add(16, w[0], true);
@@ -302,7 +322,8 @@ int ibm_unet_create(const int widths[4], unsigned long long seed, ibm_unet** out
   A((void**)&n->m, n->nparam * 4);
   A((void**)&n->v, n->nparam * 4);
   A((void**)&n->wb, n->nparam * 2);
-  A((void**)&n->wflip, n->nparam * 2);
+  A((void**)&n->wpk, n->npk * 2);
+  A((void**)&n->wpkf, n->npkf * 2);
   A((void**)&n->loss_d, 8);
   if (!rc && cudaMemcpy(n->pw, h.data(), n->nparam * 4, cudaMemcpyHostToDevice) != cudaSuccess) rc = IBM_E_CUDA;
   if (!rc) {
@@ -326,6 +347,7 @@ int ibm_unet_params(ibm_unet* n, float* host, long long count, int set) {
   if (set) {
     UCUDA(cudaMemcpy(n->pw, host, n->nparam * 4, cudaMemcpyHostToDevice));
     to_bf16(0, (long)n->nparam, n->pw, n->wb);
+    n->wdirty = true;
     UCUDA(cudaMemset(n->m, 0, n->nparam * 4));
     UCUDA(cudaMemset(n->v, 0, n->nparam * 4));
     n->adam_t = 0;
@@ -358,8 +380,9 @@ int ibm_unet_forward(ibm_unet* n, const float* feat, int H, int W, float* out, v
   cudaStream_t s = (cudaStream_t)stream;
   int rc = ensure_acts(n, H, W);
   if (rc) return rc;
+  if (conv_tc_failed()) return ufail(IBM_E_TIMEOUT, "a U-Net convolution gave up a bounded wait earlier");
   pack_input(s, (long)H * W, 4, 16, feat, n->lv[0].in);
-  forward(n, s);
+  if (forward(n, s)) return IBM_E_CUDA;
   UCUDA(cudaMemcpy2DAsync(out, sizeof(float), n->outf, 16 * sizeof(float), sizeof(float), (size_t)H * W,
                           cudaMemcpyDeviceToDevice, s));
   UCUDA(cudaGetLastError());
@@ -374,21 +397,23 @@ int ibm_unet_train_step(ibm_unet* n, const float* feat, const float* target, int
   int rc = ensure_acts(n, H, W);
   if (rc) return rc;
   pack_input(s, (long)H * W, 4, 16, feat, n->lv[0].in);
-  forward(n, s);
+  if (forward(n, s)) return IBM_E_CUDA;
   UCUDA(cudaMemsetAsync(n->grad, 0, n->nparam * 4, s));
   UCUDA(cudaMemsetAsync(n->loss_d, 0, 8, s));
   const long npix = (long)H * W;
   mse(s, npix, n->outf, 16, target, nullptr, 1.f / (float)npix, n->gout, 16, n->loss_d);
-  backward(n, s);
+  if (backward(n, s)) return IBM_E_CUDA;
   if (apply) {
     n->adam_t += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f / (1.f - std::pow(b1, (float)n->adam_t)), c2 = 1.f / (1.f - std::pow(b2, (float)n->adam_t));
     adam(s, (long)n->nparam, n->pw, n->grad, n->m, n->v, n->wb, lr, b1, b2, 1e-8f, c1, c2);
+    n->wdirty = true;
   }
   double l = 0.0;
   UCUDA(cudaMemcpyAsync(&l, n->loss_d, 8, cudaMemcpyDeviceToHost, s));
   UCUDA(cudaStreamSynchronize(s));
+  if (conv_tc_failed()) return ufail(IBM_E_TIMEOUT, "a U-Net convolution gave up a bounded wait");
   if (loss) *loss = l;
   UCUDA(cudaGetLastError());
   return IBM_OK;
