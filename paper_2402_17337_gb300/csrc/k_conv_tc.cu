@@ -22,12 +22,14 @@
 //   B (output channels x channels): weights pre-packed (k_pack_conv_weights)
 //   into the exact shared-memory image of a chunk, copied by one bulk copy.
 //
-// One thread issues the TMA loads and the MMAs (two-stage pipeline on
-// mbarriers: full = data landed, empty = the MMAs reading a stage are done,
-// signalled by tcgen05.commit); the four warps then read the accumulator
-// from tensor memory (warp w owns lanes 32 w .. 32 w + 31, i.e. pixels) and
-// apply bias and ReLU.  Every wait is bounded: a wait that gives up sets a
-// flag in mapped host memory and the CTA skips the rest of its work.
+// The CTAs are persistent and loop over tiles.  One thread issues the TMA
+// loads and another the MMAs (a pipeline of 2-3 stages on mbarriers: full =
+// data landed, empty = the MMAs reading a stage are done, signalled by
+// tcgen05.commit); four epilogue warps read the accumulator from tensor
+// memory (warp w owns lanes 32 w .. 32 w + 31, i.e. pixels) and apply bias
+// and ReLU, while the next tile accumulates into a second accumulator.
+// Every wait is bounded: a wait that gives up sets a flag in mapped host
+// memory and the CTA skips the rest of its work.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -44,8 +46,10 @@ namespace nn {
 namespace {
 
 constexpr int TC_M = 128;
-constexpr int TC_STAGES = 2;
-constexpr int TC_SMEM = 200 * 1024;  // dynamic shared memory of every launch
+constexpr int TC_THREADS = 192;  // warps 0-3: epilogue; warp 4: TMA loads; warp 5: MMAs
+constexpr int TC_STAGES_MAX = 4;
+constexpr int TC_SMEM_MAX = 200 * 1024;  // dynamic shared memory a launch may ask for
+constexpr int SM_SMEM = 228 * 1024;      // shared memory of one SM
 constexpr long long TC_WAIT_CYCLES = 4000000000ll;  // about 2 s at the SM clock
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -55,6 +59,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
   uint32_t ok;
@@ -129,25 +136,46 @@ struct TcGeom {
   int TW, R;           // pixels per tile row, rows per tile (TW R = 128)
   int copies, boxw;    // A boxes per channel group (1 or 3), pixels per box row
   int a_region;        // bytes of one A box in shared memory (padded to 128)
-  int a_bytes, b_bytes, stage_bytes, tx_bytes;
+  int a_bytes, b_bytes, stage_bytes, tx_bytes, stages;
   int NT, tmem_cols, nchunks;
+  int tiles_x, tiles_z, ntiles;  // tiles: TW-pixel columns x R-row bands x NT-channel groups
 };
 
-// Y[.., co] = act(sum over taps and channels + bias), the tile of CTA
-// (blockIdx.x: TW-pixel column, blockIdx.y: R-row band, blockIdx.z: NT
-// output channels).  wpk: this convolution's packed weights.
+// waits for the phase with the given parity of an mbarrier unless the CTA
+// has given up; gives up (sets *abort) after TC_WAIT_CYCLES
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > TC_WAIT_CYCLES) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+// Persistent: CTA b computes tiles b, b + gridDim.x, ...  Warps 0-3 drain
+// the accumulators (TMEM lanes 0-127 = the tile's pixels) and write the
+// outputs; lane 0 of warp 4 issues the loads (a ring of G.stages stages over
+// the sequence of (tile, chunk) pairs), lane 0 of warp 5 the MMAs.  Two accumulators in
+// tensor memory alternate between tiles, so the MMAs of a tile run while
+// the previous tile's epilogue reads the other one.
 template <bool RELU>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(TC_THREADS, 1)
     k_conv3x3_tc(const __grid_constant__ CUtensorMap tmX, const bf16* __restrict__ wpk, const float* __restrict__ bias,
                  bf16* __restrict__ Y, int ldy, int offy, float* __restrict__ yf, int H, int W, int Cout, TcGeom G,
                  unsigned int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) unsigned long long bar_full[TC_STAGES], bar_empty[TC_STAGES], bar_acc;
+  __shared__ __align__(8) unsigned long long bar_full[TC_STAGES_MAX], bar_empty[TC_STAGES_MAX];
+  __shared__ __align__(8) unsigned long long bar_tfull[2], bar_tempty[2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int failed;
+  __shared__ int abort_flag;
+  volatile int* abort = &abort_flag;
   const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int x0 = blockIdx.x * G.TW, y0 = blockIdx.y * G.R, n0 = blockIdx.z * G.NT;
+  const int nmine = (int)blockIdx.x < G.ntiles ? (G.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const uint32_t half_cols = (uint32_t)G.tmem_cols / 2;  // column of the second accumulator
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(G.tmem_cols)
@@ -155,105 +183,131 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (threadIdx.x == 32) {
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < G.stages; ++s) {
       mbar_init(smem_u32(&bar_full[s]), 1);
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
-    mbar_init(smem_u32(&bar_acc), 1);
-    failed = 0;
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bar_tfull[b]), 1);
+      mbar_init(smem_u32(&bar_tempty[b]), 4);  // one arrival per epilogue warp
+    }
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  auto coords = [&](int li, int& x0, int& y0, int& z) {
+    int t = (int)blockIdx.x + li * (int)gridDim.x;
+    z = t % G.tiles_z;
+    t /= G.tiles_z;
+    x0 = (t % G.tiles_x) * G.TW;
+    y0 = (t / G.tiles_x) * G.R;
+  };
 
-  if (threadIdx.x == 0) {
-    const uint32_t idesc = instr_desc(G.NT);
-    const size_t wchunk = (size_t)2 * 9 * G.NT * 8;  // bf16 elements of one chunk's weights
-    const bf16* wtile = wpk + (size_t)blockIdx.z * G.nchunks * wchunk;
-    auto load = [&](int ch, int s) {
-      const uint32_t st = sbase + s * G.stage_bytes, bar = smem_u32(&bar_full[s]);
-      mbar_expect_tx(bar, G.tx_bytes);
-      for (int cp = 0; cp < G.copies; ++cp)
-        for (int g = 0; g < 2; ++g)
-          tma_load_3d(st + (cp * 2 + g) * G.a_region, &tmX, ch * 16 + g * 8, G.copies == 1 ? x0 - 1 : x0 + cp - 1,
-                      y0 - 1, bar);
-      bulk_load(st + G.a_bytes, wtile + ch * wchunk, G.b_bytes, bar);
-    };
-    const int npre = G.nchunks < TC_STAGES ? G.nchunks : TC_STAGES;
-    for (int s = 0; s < npre; ++s) load(s, s);
-    int issued = npre;  // chunks whose loads were issued
-    bool ok = true;
-    for (int ch = 0; ch < G.nchunks; ++ch) {
-      const int s = ch % TC_STAGES;
-      const uint32_t par = (uint32_t)(ch / TC_STAGES) & 1u;
-      if (!mbar_wait(smem_u32(&bar_full[s]), par)) {
-        ok = false;
+  const int nc = G.nchunks, S = G.stages, nq = nmine * nc;
+  if (warp == 4) {
+    // TMA producer: the ring of stages over the sequence of (tile, chunk)
+    // pairs q = li nc + ch; a stage is reloaded once the MMAs that read it
+    // have completed (empty barrier, committed by the MMA thread)
+    if (lane == 0) {
+      const size_t wchunk = (size_t)2 * 9 * G.NT * 8;  // bf16 elements of one chunk's weights
+      int issued = 0;
+      for (int q = 0; q < nq; ++q) {
+        const int li = q / nc, ch = q % nc, s = q % S;
+        if (q >= S && !wait_or_abort(smem_u32(&bar_empty[s]), (uint32_t)(q / S - 1) & 1u, abort)) break;
+        int x0, y0, z;
+        coords(li, x0, y0, z);
+        const uint32_t st = sbase + s * G.stage_bytes, bar = smem_u32(&bar_full[s]);
+        mbar_expect_tx(bar, G.tx_bytes);
+        for (int cp = 0; cp < G.copies; ++cp)
+          for (int g = 0; g < 2; ++g)
+            tma_load_3d(st + (cp * 2 + g) * G.a_region, &tmX, ch * 16 + g * 8, G.copies == 1 ? x0 - 1 : x0 + cp - 1,
+                        y0 - 1, bar);
+        bulk_load(st + G.a_bytes, wpk + ((size_t)z * nc + ch) * wchunk, G.b_bytes, bar);
+        issued = q + 1;
+      }
+      if (*abort && issued > 0)  // the last load issued has landed (bounded) before the CTA may exit
+        mbar_wait(smem_u32(&bar_full[(issued - 1) % S]), (uint32_t)((issued - 1) / S) & 1u);
+    }
+    __syncwarp();
+  } else if (warp == 5) {
+    // MMA issuer: never waits for its own MMAs, only for data (full) and for
+    // the epilogue to have drained an accumulator (tempty)
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(G.NT);
+      int done = 0;
+      for (int q = 0; q < nq; ++q) {
+        const int li = q / nc, ch = q % nc, s = q % S, buf = li & 1;
+        if (ch == 0 && li >= 2 && !wait_or_abort(smem_u32(&bar_tempty[buf]), (uint32_t)((li >> 1) - 1) & 1u, abort))
+          break;
+        if (!wait_or_abort(smem_u32(&bar_full[s]), (uint32_t)(q / S) & 1u, abort)) break;
+        tc_fence_after();
+        const uint32_t st = sbase + s * G.stage_bytes, d = tmem + (uint32_t)buf * half_cols;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          const int dy = tap / 3, dx = tap % 3;
+          const uint32_t a =
+              G.copies == 1 ? st + (dy * G.boxw + dx) * 16 : st + dx * 2 * G.a_region + dy * G.TW * 16;
+          // B: [tap][8-row group of output channels][channel group][8 rows][16 bytes]
+          const uint32_t b = st + G.a_bytes + tap * G.NT * 32;
+          tc_mma(d, smem_desc(a, G.a_region, 128), smem_desc(b, 128, 256), idesc, (ch | tap) != 0);
+        }
+        tc_commit(smem_u32(&bar_empty[s]));
+        if (ch == nc - 1) tc_commit(smem_u32(&bar_tfull[buf]));
+        done = q + 1;
+      }
+      if (*abort) {
+        // the MMAs issued have completed (bounded) before the accumulators are freed
+        if (done > 0) mbar_wait(smem_u32(&bar_empty[(done - 1) % S]), (uint32_t)((done - 1) / S) & 1u);
+        atomicOr_system(err, 1u);
+      }
+    }
+    __syncwarp();
+  } else {
+    const int m = warp * 32 + lane;
+    for (int li = 0; li < nmine; ++li) {
+      const int buf = li & 1;
+      if (!wait_or_abort(smem_u32(&bar_tfull[buf]), (uint32_t)(li >> 1) & 1u, abort)) {
+        if (lane == 0) atomicOr_system(err, 1u);
         break;
       }
       tc_fence_after();
-      const uint32_t st = sbase + s * G.stage_bytes;
+      int x0, y0, z;
+      coords(li, x0, y0, z);
+      const int y = y0 + m / G.TW, x = x0 + m % G.TW, n0 = z * G.NT;
+      const bool valid = x < W && y < H;
+      const size_t p = (size_t)y * W + x;
+      for (int c0 = 0; c0 < G.NT; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)buf * half_cols + (uint32_t)c0, v);
+        const int co = n0 + c0;
+        if (!valid || co >= Cout) continue;
 #pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap % 3;
-        const uint32_t a = G.copies == 1 ? st + (dy * G.boxw + dx) * 16 : st + dx * 2 * G.a_region + dy * G.TW * 16;
-        // B: [tap][8-row group of output channels][channel group][8 rows][16 bytes]
-        const uint32_t b = st + G.a_bytes + tap * G.NT * 32;
-        tc_mma(tmem, smem_desc(a, G.a_region, 128), smem_desc(b, 128, 256), idesc, (ch | tap) != 0);
-      }
-      tc_commit(smem_u32(&bar_empty[s]));
-      if (ch + TC_STAGES < G.nchunks) {
-        if (!mbar_wait(smem_u32(&bar_empty[s]), par)) {
-          ok = false;
-          break;
+        for (int j = 0; j < 16; ++j) {
+          float t = v[j] + (bias ? bias[co + j] : 0.f);
+          v[j] = RELU ? fmaxf(t, 0.f) : t;
         }
-        load(ch + TC_STAGES, s);
-        ++issued;
+        uint4 o[2];
+        uint32_t* ow = reinterpret_cast<uint32_t*>(o);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+          ow[j] = *reinterpret_cast<uint32_t*>(&h);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(Y + p * ldy + offy + co);
+        dst[0] = o[0];
+        dst[1] = o[1];
+        if (yf) {
+          float4* f = reinterpret_cast<float4*>(yf + p * Cout + co);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) f[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
       }
-    }
-    tc_commit(smem_u32(&bar_acc));
-    if (!ok) {
-      // wait (bounded) for every load still in flight before giving up
-      failed = 1;
-      for (int ch = 0; ch < issued; ++ch) mbar_wait(smem_u32(&bar_full[ch % TC_STAGES]), (ch / TC_STAGES) & 1u);
-    }
-  }
-  __syncwarp();
-  const bool acc_ok = mbar_wait(smem_u32(&bar_acc), 0);
-  tc_fence_after();
-  __syncthreads();  // 'failed' is read below
-  const bool good = acc_ok && !failed;
-  if (!good && threadIdx.x == 0) atomicOr_system(err, 1u);
-
-  const int m = warp * 32 + lane;
-  const int y = y0 + m / G.TW, x = x0 + m % G.TW;
-  const bool valid = good && x < W && y < H;
-  const size_t p = (size_t)y * W + x;
-  for (int c0 = 0; c0 < G.NT; c0 += 16) {
-    float v[16];
-    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-    const int co = n0 + c0;
-    if (!valid || co >= Cout) continue;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      float t = v[j] + (bias ? bias[co + j] : 0.f);
-      v[j] = RELU ? fmaxf(t, 0.f) : t;
-    }
-    uint4 o[2];
-    uint32_t* ow = reinterpret_cast<uint32_t*>(o);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-      ow[j] = *reinterpret_cast<uint32_t*>(&h);
-    }
-    uint4* dst = reinterpret_cast<uint4*>(Y + p * ldy + offy + co);
-    dst[0] = o[0];
-    dst[1] = o[1];
-    if (yf) {
-      float4* f = reinterpret_cast<float4*>(yf + p * Cout + co);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) f[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[buf]));
     }
   }
   tc_fence_before();
@@ -375,9 +429,20 @@ int conv3x3(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* X, int 
   G.b_bytes = 9 * G.NT * 32;
   G.stage_bytes = (G.a_bytes + G.b_bytes + 1023) / 1024 * 1024;
   G.tx_bytes = G.copies * 2 * rows * G.boxw * 16 + G.b_bytes;
-  G.tmem_cols = pow2_at_least(G.NT < 32 ? 32 : G.NT);
+  G.tmem_cols = pow2_at_least(2 * G.NT < 64 ? 64 : 2 * G.NT);  // two accumulators, each at least 32 columns
   G.nchunks = Cin / 16;
-  if (TC_STAGES * G.stage_bytes + 1024 > TC_SMEM) {
+  G.stages = 3 * G.stage_bytes + 1024 <= TC_SMEM_MAX ? 3 : 2;
+  G.tiles_x = (W + G.TW - 1) / G.TW;
+  G.tiles_z = (Cout + G.NT - 1) / G.NT;
+  G.ntiles = G.tiles_x * ((H + G.R - 1) / G.R) * G.tiles_z;
+  // Dynamic shared memory: the stages plus alignment slack, and at least
+  // enough that the CTAs resident on one SM (bounded by shared memory) hold
+  // no more than the SM's 512 tensor-memory columns, so an allocation never
+  // waits for another CTA's.
+  int smem = G.stages * G.stage_bytes + 1024;
+  const int smem_tmem = (int)(((long)SM_SMEM * G.tmem_cols + 511) / 512);
+  if (smem < smem_tmem) smem = smem_tmem;
+  if (smem > TC_SMEM_MAX) {
     set_last_error("convolution tile does not fit in shared memory");
     return -1;
   }
@@ -395,15 +460,27 @@ int conv3x3(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* X, int 
   }
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_conv3x3_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    cudaFuncSetAttribute(k_conv3x3_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    // the largest shared-memory carveout, so that several CTAs fit on an SM
+    for (auto k : {k_conv3x3_tc<true>, k_conv3x3_tc<false>}) {
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_MAX);
+      cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    }
     attr = true;
   }
-  dim3 grd((W + G.TW - 1) / G.TW, (H + G.R - 1) / G.R, (Cout + G.NT - 1) / G.NT);
-  if (relu)
-    k_conv3x3_tc<true><<<grd, 128, TC_SMEM, s>>>(map, wpk, bias, Y, ldy, offy, yf, H, W, Cout, G, err_dev);
-  else
-    k_conv3x3_tc<false><<<grd, 128, TC_SMEM, s>>>(map, wpk, bias, Y, ldy, offy, yf, H, W, Cout, G, err_dev);
+  // persistent CTAs: as many as fit on the device at once (shared memory,
+  // with 1 KB static and 1 KB reserved per CTA; threads; tensor-memory
+  // columns), at most one per tile
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  auto kern = relu ? k_conv3x3_tc<true> : k_conv3x3_tc<false>;
+  int per_sm = SM_SMEM / (smem + 2048);
+  if (per_sm > 2048 / TC_THREADS) per_sm = 2048 / TC_THREADS;
+  if (per_sm > 512 / G.tmem_cols) per_sm = 512 / G.tmem_cols;
+  if (per_sm < 1) per_sm = 1;
+  const long slots = (long)nsm * per_sm;
+  const int grid = (int)(G.ntiles < slots ? G.ntiles : slots);
+  kern<<<grid, TC_THREADS, smem, s>>>(map, wpk, bias, Y, ldy, offy, yf, H, W, Cout, G, err_dev);
   return 0;
 }
 

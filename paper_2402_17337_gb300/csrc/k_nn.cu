@@ -135,18 +135,39 @@ __global__ void k_relu_grad(long npix, int C, bf16* __restrict__ G, int ldg, int
   }
 }
 
-// 2x2 average pool (H, W even): out[y][x][c] = mean of the 2x2 block
+// 2x2 average pool (H, W even): out[y][x][c] = mean of the 2x2 block; one
+// thread per output pixel and 8 channels (C, the slices' ld and off are
+// multiples of 8: 16-byte loads and stores)
+__device__ inline void bf16x8_to_float(const uint4& u, float (&f)[8]) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float2 t = __bfloat1622float2(h[j]);
+    f[2 * j] = t.x;
+    f[2 * j + 1] = t.y;
+  }
+}
 __global__ void k_avgpool(int H, int W, int C, const bf16* __restrict__ X, int ldx, int offx, bf16* __restrict__ Y,
                           int ldy, int offy) {
-  const int H2 = H / 2, W2 = W / 2;
-  long n = (long)H2 * W2 * C;
-  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
-    int c = (int)(k % C);
-    long p = k / C;
-    int x = (int)(p % W2), y = (int)(p / W2);
-    auto at = [&](int yy, int xx) { return __bfloat162float(X[((long)yy * W + xx) * ldx + offx + c]); };
-    float v = 0.25f * (at(2 * y, 2 * x) + at(2 * y, 2 * x + 1) + at(2 * y + 1, 2 * x) + at(2 * y + 1, 2 * x + 1));
-    Y[p * ldy + offy + c] = __float2bfloat16_rn(v);
+  const int H2 = H / 2, W2 = W / 2, G = C / 8;
+  const int n = H2 * W2 * G;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int g = k % G, p = k / G, x = p % W2, y = p / W2;
+    auto at = [&](int yy, int xx) {
+      return *reinterpret_cast<const uint4*>(X + ((size_t)yy * W + xx) * ldx + offx + 8 * g);
+    };
+    float a[8], b[8], c[8], d[8];
+    bf16x8_to_float(at(2 * y, 2 * x), a);
+    bf16x8_to_float(at(2 * y, 2 * x + 1), b);
+    bf16x8_to_float(at(2 * y + 1, 2 * x), c);
+    bf16x8_to_float(at(2 * y + 1, 2 * x + 1), d);
+    uint4 o;
+    __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      oh[j] = __floats2bfloat162_rn(0.25f * (a[2 * j] + b[2 * j] + c[2 * j] + d[2 * j]),
+                                    0.25f * (a[2 * j + 1] + b[2 * j + 1] + c[2 * j + 1] + d[2 * j + 1]));
+    *reinterpret_cast<uint4*>(Y + (size_t)p * ldy + offy + 8 * g) = o;
   }
 }
 
@@ -164,15 +185,15 @@ __global__ void k_avgpool_grad(int H, int W, int C, const bf16* __restrict__ dY,
   }
 }
 
-// nearest 2x upsampling of a (H/2 x W/2) map into a (H x W) channel slice
+// nearest 2x upsampling of a (H/2 x W/2) map into a (H x W) channel slice;
+// one thread per output pixel and 8 channels
 __global__ void k_upsample(int H, int W, int C, const bf16* __restrict__ X, int ldx, int offx, bf16* __restrict__ Y,
                            int ldy, int offy) {
-  long n = (long)H * W * C;
-  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
-    int c = (int)(k % C);
-    long p = k / C;
-    int x = (int)(p % W), y = (int)(p / W);
-    Y[p * ldy + offy + c] = X[((long)(y / 2) * (W / 2) + x / 2) * ldx + offx + c];
+  const int G = C / 8, n = H * W * G;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int g = k % G, p = k / G, x = p % W, y = p / W;
+    *reinterpret_cast<uint4*>(Y + (size_t)p * ldy + offy + 8 * g) =
+        *reinterpret_cast<const uint4*>(X + ((size_t)(y / 2) * (W / 2) + x / 2) * ldx + offx + 8 * g);
   }
 }
 
@@ -245,13 +266,22 @@ __global__ void k_to_bf16(long n, const float* __restrict__ a, bf16* __restrict_
     b[k] = __float2bfloat16_rn(a[k]);
 }
 
-// FP32 [H][W][cin] features -> BF16 [H][W][cpad] (zero padded channels)
+// FP32 [H][W][cin] features -> BF16 [H][W][cpad] (zero padded channels;
+// cpad a multiple of 8); one thread per pixel and 8 channels
 __global__ void k_pack_input(long npix, int cin, int cpad, const float* __restrict__ f, bf16* __restrict__ x) {
-  long n = npix * cpad;
+  const int G = cpad / 8;
+  const long n = npix * G;
   for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
-    long p = k / cpad;
-    int c = (int)(k % cpad);
-    x[k] = __float2bfloat16_rn(c < cin ? f[p * cin + c] : 0.f);
+    const long p = k / G;
+    const int c0 = (int)(k % G) * 8;
+    uint4 o;
+    __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + 2 * j;
+      oh[j] = __floats2bfloat162_rn(c < cin ? f[p * cin + c] : 0.f, c + 1 < cin ? f[p * cin + c + 1] : 0.f);
+    }
+    *reinterpret_cast<uint4*>(x + p * cpad + c0) = o;
   }
 }
 
@@ -273,14 +303,14 @@ void relu_grad(cudaStream_t s, long npix, int C, bf16* G, int ldg, int offg, con
   k_relu_grad<<<grid1(npix * C), 256, 0, s>>>(npix, C, G, ldg, offg, Y, ldy, offy);
 }
 void avgpool(cudaStream_t s, int H, int W, int C, const bf16* X, int ldx, int offx, bf16* Y, int ldy, int offy) {
-  k_avgpool<<<grid1((long)H * W * C / 4), 256, 0, s>>>(H, W, C, X, ldx, offx, Y, ldy, offy);
+  k_avgpool<<<grid1((long)H * W * C / 32), 256, 0, s>>>(H, W, C, X, ldx, offx, Y, ldy, offy);
 }
 void avgpool_grad(cudaStream_t s, int H, int W, int C, const bf16* dY, int ldy, int offy, bf16* dX, int ldx, int offx,
                   bool acc) {
   k_avgpool_grad<<<grid1((long)H * W * C), 256, 0, s>>>(H, W, C, dY, ldy, offy, dX, ldx, offx, acc ? 1 : 0);
 }
 void upsample(cudaStream_t s, int H, int W, int C, const bf16* X, int ldx, int offx, bf16* Y, int ldy, int offy) {
-  k_upsample<<<grid1((long)H * W * C), 256, 0, s>>>(H, W, C, X, ldx, offx, Y, ldy, offy);
+  k_upsample<<<grid1((long)H * W * C / 8), 256, 0, s>>>(H, W, C, X, ldx, offx, Y, ldy, offy);
 }
 void upsample_grad(cudaStream_t s, int H, int W, int C, const bf16* dY, int ldy, int offy, bf16* dX, int ldx, int offx,
                    bool acc) {
@@ -300,7 +330,7 @@ void adam(cudaStream_t s, long n, float* w, const float* g, float* m, float* v, 
 }
 void to_bf16(cudaStream_t s, long n, const float* a, bf16* b) { k_to_bf16<<<grid1(n), 256, 0, s>>>(n, a, b); }
 void pack_input(cudaStream_t s, long npix, int cin, int cpad, const float* f, bf16* x) {
-  k_pack_input<<<grid1(npix * cpad), 256, 0, s>>>(npix, cin, cpad, f, x);
+  k_pack_input<<<grid1(npix * cpad / 8), 256, 0, s>>>(npix, cin, cpad, f, x);
 }
 
 }  // namespace nn
