@@ -283,9 +283,16 @@ int ibm_get_profile(const ibm_ctx* ctx, ibm_profile* out);
  * activation buffers are allocated by the first forward or training step
  * at a given H x W and reallocated when the size changes, so a size change
  * must not happen while a stream that uses the network is being captured.
+ * The 3x3 convolutions of the forward pass and of the data gradient run on
+ * the tcgen05 tensor cores (tensor-memory accumulators, TMA-loaded tiles);
+ * their waits are bounded (about 2 s).  The BF16 weights are repacked for
+ * those kernels on the stream after every change (creation, new parameters,
+ * an Adam step), inside the next forward pass.
  * Errors: IBM_E_INVAL (widths not positive multiples of 16, n different
  * from ibm_unet_num_params, H or W not multiples of 8, NULL pointers),
- * IBM_E_CUDA. */
+ * IBM_E_CUDA, IBM_E_TIMEOUT (a convolution kernel gave up a bounded wait;
+ * reported by the first forward or training call after it, and by every
+ * later one: the device state is then suspect). */
 typedef struct ibm_unet ibm_unet;
 int ibm_unet_create(const int widths[4], unsigned long long seed, ibm_unet** out);
 void ibm_unet_destroy(ibm_unet* net);
