@@ -22,7 +22,9 @@
 //   B (output channels x channels): weights pre-packed (k_pack_conv_weights)
 //   into the exact shared-memory image of a chunk, copied by one bulk copy.
 //
-// The CTAs are persistent and loop over tiles.  One thread issues the TMA
+// Consecutive convolutions are programmatic dependent launches (the next
+// kernel's set-up overlaps the previous one's tail).  The CTAs are
+// persistent and loop over tiles.  One thread issues the TMA
 // loads and another the MMAs (a pipeline of 2-3 stages on mbarriers: full =
 // data landed, empty = the MMAs reading a stage are done, signalled by
 // tcgen05.commit); four epilogue warps read the accumulator from tensor
@@ -198,6 +200,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  // Launched as a programmatic dependent of the previous kernel on the
+  // stream: the set-up above (tensor memory, barriers) overlaps that
+  // kernel's tail, and no thread touches global memory before the previous
+  // kernel has completed and its writes are visible (griddepcontrol.wait);
+  // then the next launch may be scheduled.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   auto coords = [&](int li, int& x0, int& y0, int& z) {
     int t = (int)blockIdx.x + li * (int)gridDim.x;
     z = t % G.tiles_z;
@@ -480,7 +489,20 @@ int conv3x3(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* X, int 
   if (per_sm < 1) per_sm = 1;
   const long slots = (long)nsm * per_sm;
   const int grid = (int)(G.ntiles < slots ? G.ntiles : slots);
-  kern<<<grid, TC_THREADS, smem, s>>>(map, wpk, bias, Y, ldy, offy, yf, H, W, Cout, G, err_dev);
+  cudaLaunchConfig_t lc{};
+  lc.gridDim = dim3(grid);
+  lc.blockDim = dim3(TC_THREADS);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  if (cudaLaunchKernelEx(&lc, kern, map, wpk, bias, Y, ldy, offy, yf, H, W, Cout, G, err_dev) != cudaSuccess) {
+    set_last_error("convolution launch failed");
+    return -1;
+  }
   return 0;
 }
 

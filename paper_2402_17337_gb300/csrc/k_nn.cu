@@ -135,6 +135,28 @@ __global__ void k_relu_grad(long npix, int C, bf16* __restrict__ G, int ldg, int
   }
 }
 
+// Kernels of the forward pass are programmatic dependent launches: each
+// waits for the previous kernel on the stream to complete (and its writes to
+// be visible) before touching global memory, then lets the next one start.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*k)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t lc{};
+  lc.gridDim = dim3(grid);
+  lc.blockDim = dim3(block);
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  cudaLaunchKernelEx(&lc, k, static_cast<KArgs>(args)...);
+}
+
 // 2x2 average pool (H, W even): out[y][x][c] = mean of the 2x2 block; one
 // thread per output pixel and 8 channels (C, the slices' ld and off are
 // multiples of 8: 16-byte loads and stores)
@@ -149,6 +171,7 @@ __device__ inline void bf16x8_to_float(const uint4& u, float (&f)[8]) {
 }
 __global__ void k_avgpool(int H, int W, int C, const bf16* __restrict__ X, int ldx, int offx, bf16* __restrict__ Y,
                           int ldy, int offy) {
+  pdl_enter();
   const int H2 = H / 2, W2 = W / 2, G = C / 8;
   const int n = H2 * W2 * G;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
@@ -189,6 +212,7 @@ __global__ void k_avgpool_grad(int H, int W, int C, const bf16* __restrict__ dY,
 // one thread per output pixel and 8 channels
 __global__ void k_upsample(int H, int W, int C, const bf16* __restrict__ X, int ldx, int offx, bf16* __restrict__ Y,
                            int ldy, int offy) {
+  pdl_enter();
   const int G = C / 8, n = H * W * G;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int g = k % G, p = k / G, x = p % W, y = p / W;
@@ -269,6 +293,7 @@ __global__ void k_to_bf16(long n, const float* __restrict__ a, bf16* __restrict_
 // FP32 [H][W][cin] features -> BF16 [H][W][cpad] (zero padded channels;
 // cpad a multiple of 8); one thread per pixel and 8 channels
 __global__ void k_pack_input(long npix, int cin, int cpad, const float* __restrict__ f, bf16* __restrict__ x) {
+  pdl_enter();
   const int G = cpad / 8;
   const long n = npix * G;
   for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
@@ -303,14 +328,14 @@ void relu_grad(cudaStream_t s, long npix, int C, bf16* G, int ldg, int offg, con
   k_relu_grad<<<grid1(npix * C), 256, 0, s>>>(npix, C, G, ldg, offg, Y, ldy, offy);
 }
 void avgpool(cudaStream_t s, int H, int W, int C, const bf16* X, int ldx, int offx, bf16* Y, int ldy, int offy) {
-  k_avgpool<<<grid1((long)H * W * C / 32), 256, 0, s>>>(H, W, C, X, ldx, offx, Y, ldy, offy);
+  launch_pdl(k_avgpool, grid1((long)H * W * C / 32), 256, s, H, W, C, X, ldx, offx, Y, ldy, offy);
 }
 void avgpool_grad(cudaStream_t s, int H, int W, int C, const bf16* dY, int ldy, int offy, bf16* dX, int ldx, int offx,
                   bool acc) {
   k_avgpool_grad<<<grid1((long)H * W * C), 256, 0, s>>>(H, W, C, dY, ldy, offy, dX, ldx, offx, acc ? 1 : 0);
 }
 void upsample(cudaStream_t s, int H, int W, int C, const bf16* X, int ldx, int offx, bf16* Y, int ldy, int offy) {
-  k_upsample<<<grid1((long)H * W * C / 8), 256, 0, s>>>(H, W, C, X, ldx, offx, Y, ldy, offy);
+  launch_pdl(k_upsample, grid1((long)H * W * C / 8), 256, s, H, W, C, X, ldx, offx, Y, ldy, offy);
 }
 void upsample_grad(cudaStream_t s, int H, int W, int C, const bf16* dY, int ldy, int offy, bf16* dX, int ldx, int offx,
                    bool acc) {
@@ -330,7 +355,7 @@ void adam(cudaStream_t s, long n, float* w, const float* g, float* m, float* v, 
 }
 void to_bf16(cudaStream_t s, long n, const float* a, bf16* b) { k_to_bf16<<<grid1(n), 256, 0, s>>>(n, a, b); }
 void pack_input(cudaStream_t s, long npix, int cin, int cpad, const float* f, bf16* x) {
-  k_pack_input<<<grid1(npix * cpad / 8), 256, 0, s>>>(npix, cin, cpad, f, x);
+  launch_pdl(k_pack_input, grid1(npix * cpad / 8), 256, s, npix, cin, cpad, f, x);
 }
 
 }  // namespace nn
