@@ -327,6 +327,142 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
+// ------------------------------------------------------- weight gradient
+//
+// dW[co][tap][ci] += sum over pixels p of G[p][co] X[p + shift(tap)][ci], a
+// GEMM per tap with M = 128 output channels (rows beyond Cout zero), N = NT
+// input channels, K = pixels.  Both operands come as TMA boxes of [pixel][8
+// channels], i.e. MN-major: a core matrix is 8 pixels (K) x 8 channels (MN),
+// 16 bytes per pixel; K groups of 8 pixels are 128 bytes apart, MN groups of
+// 8 channels one box apart.  A CTA owns one tap row dy (taps 3 dy .. 3 dy + 2,
+// one accumulator of NT columns each), one NT-channel tile and a range of
+// pixel chunks (P pixels of one image row); the X box of a chunk spans P + 2
+// pixels of row y + dy, and tap dx reads it dx pixels further.  After its
+// chunks the CTA adds its accumulators to dW (vector atomics).
+struct WgGeom {
+  int P;                // pixels per chunk (a multiple of 16, <= 128)
+  int NT, ntiles_ci;    // input channels per tile, tiles
+  int cog;              // 8-channel groups of G that hold channels (< Cout)
+  int a_region, b_region, a_bytes, b_bytes, stage_bytes, tx_bytes, stages;
+  int tmem_cols, chunks_x, nchunks, ksplit;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_conv3x3_wgrad_tc(const __grid_constant__ CUtensorMap tmG, const __grid_constant__ CUtensorMap tmX, int Cin,
+                       int Cout, float* __restrict__ dW, WgGeom G, unsigned int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bar_full[TC_STAGES_MAX], bar_empty[TC_STAGES_MAX], bar_acc;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  volatile int* abort = &abort_flag;
+  const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // work unit: blockIdx.x = (ksplit part, tap row, channel tile)
+  const int part = blockIdx.x % G.ksplit, rest = blockIdx.x / G.ksplit;
+  const int dy = rest % 3, zt = rest / 3;
+  const int c_begin = (int)((long)G.nchunks * part / G.ksplit), c_end = (int)((long)G.nchunks * (part + 1) / G.ksplit);
+  const int nq = c_end - c_begin, S = G.stages;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(G.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // the MN groups of A beyond Cout are never loaded: zero them in every stage
+  const int zero_bytes = (16 - G.cog) * G.a_region;
+  for (int s = 0; s < S; ++s) {
+    uint4* z = reinterpret_cast<uint4*>(smem_raw + (sbase - smem_u32(smem_raw)) + s * G.stage_bytes +
+                                        G.cog * G.a_region);
+    for (int k = threadIdx.x; k < zero_bytes / 16; k += blockDim.x) z[k] = make_uint4(0, 0, 0, 0);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes seen by the tensor cores
+  if (threadIdx.x == 32) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bar_acc), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
+  if (warp == 4) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int q = 0; q < nq; ++q) {
+        const int s = q % S, c = c_begin + q;
+        if (q >= S && !wait_or_abort(smem_u32(&bar_empty[s]), (uint32_t)(q / S - 1) & 1u, abort)) break;
+        const int x0 = (c % G.chunks_x) * G.P, y = c / G.chunks_x;
+        const uint32_t st = sbase + s * G.stage_bytes, bar = smem_u32(&bar_full[s]);
+        mbar_expect_tx(bar, G.tx_bytes);
+        for (int g = 0; g < G.cog; ++g) tma_load_3d(st + g * G.a_region, &tmG, 8 * g, x0, y, bar);
+        for (int g = 0; g < G.NT / 8; ++g)
+          tma_load_3d(st + G.a_bytes + g * G.b_region, &tmX, zt * G.NT + 8 * g, x0 - 1, y + dy - 1, bar);
+        issued = q + 1;
+      }
+      if (*abort && issued > 0) mbar_wait(smem_u32(&bar_full[(issued - 1) % S]), (uint32_t)((issued - 1) / S) & 1u);
+    }
+    __syncwarp();
+  } else if (warp == 5) {
+    if (lane == 0) {
+      // both operands MN-major (transpose bits), N = NT, M = 128
+      const uint32_t idesc = instr_desc(G.NT) | (1u << 15) | (1u << 16);
+      int done = 0;
+      for (int q = 0; q < nq; ++q) {
+        const int s = q % S;
+        if (!wait_or_abort(smem_u32(&bar_full[s]), (uint32_t)(q / S) & 1u, abort)) break;
+        tc_fence_after();
+        const uint32_t st = sbase + s * G.stage_bytes;
+        for (int ks = 0; ks < G.P / 16; ++ks) {
+          const uint64_t a = smem_desc(st + ks * 256, 128, G.a_region);
+#pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            const uint64_t b = smem_desc(st + G.a_bytes + (ks * 16 + t) * 16, 128, G.b_region);
+            tc_mma(tmem + (uint32_t)(t * G.NT), a, b, idesc, (q | ks) != 0);
+          }
+        }
+        tc_commit(smem_u32(&bar_empty[s]));
+        done = q + 1;
+      }
+      tc_commit(smem_u32(&bar_acc));
+      if (*abort) {
+        if (done > 0) mbar_wait(smem_u32(&bar_empty[(done - 1) % S]), (uint32_t)((done - 1) / S) & 1u);
+        atomicOr_system(err, 1u);
+      }
+    }
+    __syncwarp();
+  } else if (nq > 0) {
+    // epilogue: lane = output channel co, 16 input channels per load
+    if (wait_or_abort(smem_u32(&bar_acc), 0u, abort)) {
+      tc_fence_after();
+      const int co = warp * 32 + lane;
+      for (int t = 0; t < 3; ++t)
+        for (int c0 = 0; c0 < G.NT; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * G.NT + c0), v);
+          if (co >= Cout || zt * G.NT + c0 >= Cin) continue;
+          float4* dst = reinterpret_cast<float4*>(dW + ((size_t)co * 9 + 3 * dy + t) * Cin + zt * G.NT + c0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) atomicAdd(dst + j, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+        }
+    } else if (lane == 0) {
+      atomicOr_system(err, 1u);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G.tmem_cols) : "memory");
+  }
+}
+
 // Packed weights of a convolution with Cin input and Cout output channels:
 // for output-channel tile t (NT channels) and input-channel chunk ch (16
 // channels), the chunk's shared-memory image
@@ -385,6 +521,15 @@ unsigned int* error_flag(unsigned int** dev) {
   return host;
 }
 
+// Least dynamic shared memory per CTA such that the CTAs that fit on one SM
+// by shared memory (1 KB static and 1 KB reserved each) hold no more than the
+// SM's 512 tensor-memory columns: then an allocation never waits for
+// another CTA's.
+int tmem_min_smem(int cols) {
+  const int k = 512 / cols;  // CTAs whose columns fit
+  return SM_SMEM / (k + 1) - 2048 + 1;
+}
+
 int pow2_at_least(int v) {
   int p = 1;
   while (p < v) p <<= 1;
@@ -405,6 +550,98 @@ void pack_conv_weights(cudaStream_t s, int Cin, int Cout, const bf16* w, bf16* w
   const long n = (long)packed_conv_weights(Cin, Cout);
   long b = (n + 255) / 256;
   k_pack_conv_weights<<<(int)(b > 4096 ? 4096 : b), 256, 0, s>>>(Cin, Cout, NT, ntiles, w, wpk, flip ? 1 : 0);
+}
+
+int conv3x3_wgrad(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* Gd, int ldg, int offg, const bf16* X,
+                   int ldx, int offx, float* dW) {
+  // channel counts and slices were checked by the forward convolutions of the same layer
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  unsigned int* err_dev = nullptr;
+  error_flag(&err_dev);
+  if (!enc || !err_dev || Cout > 128 || Cin % 16 || Cout % 16) {
+    set_last_error("weight gradient: unsupported channel counts or no tensor-map encoder");
+    return -1;
+  }
+  WgGeom G{};
+  G.P = W >= 128 ? 128 : (pow2_at_least(W) < 16 ? 16 : pow2_at_least(W));
+  G.NT = Cin <= 128 ? Cin : 128;
+  G.ntiles_ci = (Cin + G.NT - 1) / G.NT;
+  G.cog = Cout / 8;
+  G.a_region = G.P * 16;
+  G.a_bytes = 16 * G.a_region;
+  G.b_region = ((G.P + 2) * 16 + 127) / 128 * 128;
+  G.b_bytes = (G.NT / 8) * G.b_region;
+  G.stage_bytes = (G.a_bytes + G.b_bytes + 1023) / 1024 * 1024;
+  G.tx_bytes = G.cog * G.P * 16 + (G.NT / 8) * (G.P + 2) * 16;
+  G.stages = 3 * G.stage_bytes + 1024 <= TC_SMEM_MAX ? 3 : 2;
+  G.tmem_cols = pow2_at_least(3 * G.NT < 32 ? 32 : 3 * G.NT);
+  G.chunks_x = (W + G.P - 1) / G.P;
+  G.nchunks = H * G.chunks_x;
+  int smem = G.stages * G.stage_bytes + 1024;
+  const int smem_tmem = tmem_min_smem(G.tmem_cols);
+  if (smem < smem_tmem) smem = smem_tmem;
+  if (smem > TC_SMEM_MAX) {
+    set_last_error("weight-gradient tile does not fit in shared memory");
+    return -1;
+  }
+  CUtensorMap mg, mx;
+  cuuint32_t estr[3] = {1, 1, 1};
+  {
+    cuuint64_t dims[3] = {(cuuint64_t)Cout, (cuuint64_t)W, (cuuint64_t)H};
+    cuuint64_t strides[2] = {(cuuint64_t)ldg * 2, (cuuint64_t)W * ldg * 2};
+    cuuint32_t box[3] = {8, (cuuint32_t)G.P, 1};
+    if (enc(&mg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(Gd + offg), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+      set_last_error("cuTensorMapEncodeTiled rejected a gradient view");
+      return -1;
+    }
+  }
+  {
+    cuuint64_t dims[3] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H};
+    cuuint64_t strides[2] = {(cuuint64_t)ldx * 2, (cuuint64_t)W * ldx * 2};
+    cuuint32_t box[3] = {8, (cuuint32_t)(G.P + 2), 1};
+    if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(X + offx), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+      set_last_error("cuTensorMapEncodeTiled rejected an activation view");
+      return -1;
+    }
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_conv3x3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_MAX);
+    cudaFuncSetAttribute(k_conv3x3_wgrad_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+    attr = true;
+  }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = SM_SMEM / (smem + 2048);
+  if (per_sm > 2048 / TC_THREADS) per_sm = 2048 / TC_THREADS;
+  if (per_sm > 512 / G.tmem_cols) per_sm = 512 / G.tmem_cols;
+  if (per_sm < 1) per_sm = 1;
+  // split the pixel chunks so that the CTAs fill the device once
+  const int units = 3 * G.ntiles_ci;
+  G.ksplit = (int)((long)nsm * per_sm / units);
+  if (G.ksplit < 1) G.ksplit = 1;
+  if (G.ksplit > G.nchunks) G.ksplit = G.nchunks;
+  cudaLaunchConfig_t lc{};
+  lc.gridDim = dim3(units * G.ksplit);
+  lc.blockDim = dim3(TC_THREADS);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  if (cudaLaunchKernelEx(&lc, k_conv3x3_wgrad_tc, mg, mx, Cin, Cout, dW, G, err_dev) != cudaSuccess) {
+    set_last_error("weight-gradient launch failed");
+    return -1;
+  }
+  return 0;
 }
 
 bool conv_tc_failed() {
@@ -444,12 +681,10 @@ int conv3x3(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* X, int 
   G.tiles_x = (W + G.TW - 1) / G.TW;
   G.tiles_z = (Cout + G.NT - 1) / G.NT;
   G.ntiles = G.tiles_x * ((H + G.R - 1) / G.R) * G.tiles_z;
-  // Dynamic shared memory: the stages plus alignment slack, and at least
-  // enough that the CTAs resident on one SM (bounded by shared memory) hold
-  // no more than the SM's 512 tensor-memory columns, so an allocation never
-  // waits for another CTA's.
+  // dynamic shared memory: the stages plus alignment slack, at least
+  // tmem_min_smem
   int smem = G.stages * G.stage_bytes + 1024;
-  const int smem_tmem = (int)(((long)SM_SMEM * G.tmem_cols + 511) / 512);
+  const int smem_tmem = tmem_min_smem(G.tmem_cols);
   if (smem < smem_tmem) smem = smem_tmem;
   if (smem > TC_SMEM_MAX) {
     set_last_error("convolution tile does not fit in shared memory");

@@ -7,10 +7,9 @@
 // are formed without copies.  Weights of a 3x3 convolution are [Cout][9][Cin]
 // (tap = 3*(dy+1) + (dx+1)), i.e. K-contiguous columns of the GEMM operand B.
 //
-// The forward and data-gradient convolutions run on the tcgen05 tensor cores
-// (k_conv_tc.cu).  The weight gradient here is a GEMM reduced over pixels on
-// the warp-level tensor-core path (mma.sync m16n8k16, BF16 inputs, FP32
-// accumulators), split over pixel chunks with atomics.
+// The convolutions (forward, data gradient, weight gradient) run on the
+// tcgen05 tensor cores (k_conv_tc.cu); this file holds the element-wise
+// kernels around them.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -22,104 +21,6 @@ namespace nn {
 using bf16 = __nv_bfloat16;
 
 namespace {
-
-__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ inline void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
-}
-__device__ inline void ldsm_x2_t(uint32_t (&r)[2], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
-               : "=r"(r[0]), "=r"(r[1])
-               : "r"(smem_u32(p)));
-}
-// D = A (16x16, row) * B (16x8, col) + D, BF16 in, FP32 accumulate
-__device__ inline void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-constexpr int CN = 64;  // output channels per CTA of the weight gradient
-
-// Weight gradient of a 3x3 convolution for one tap:
-//   dW[co][tap][ci] += sum_p G[p][co] * X[p + shift(tap)][ci]
-// GEMM with M = co (64 per CTA), N = ci (16 per CTA), K = pixels (64 per
-// chunk, one row segment per chunk).  Grid (pixel chunks / CHUNKS, 9, tiles of
-// (Cout/64) x (Cin/32)), block 128: warp w takes co rows 16 w .. 16 w + 15.
-// G and X are loaded pixel-major, so both fragments come from ldmatrix.trans.
-constexpr int WP = 64;       // pixels per K chunk
-constexpr int WCI = 16;      // input channels per CTA
-constexpr int WCHUNKS = 16;  // K chunks per CTA (split-K, then atomics)
-
-__global__ void __launch_bounds__(128) k_conv3x3_wgrad(int H, int W, int Cin, int Cout, const bf16* __restrict__ G,
-                                                       int ldg, int offg, const bf16* __restrict__ X, int ldx, int offx,
-                                                       float* __restrict__ dW) {
-  __shared__ __align__(16) bf16 sG[WP][CN + 8];   // [pixel][co]
-  __shared__ __align__(16) bf16 sX[WP][WCI + 8];  // [pixel][ci]
-  const int tap = blockIdx.y, dy = tap / 3 - 1, dx = tap % 3 - 1;
-  const int ntile_ci = Cin / WCI;
-  const int co0 = (blockIdx.z / ntile_ci) * CN, ci0 = (blockIdx.z % ntile_ci) * WCI;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wchunks = (W + WP - 1) / WP;
-  const long nchunks = (long)H * wchunks;
-  float acc[WCI / 8][4];
-#pragma unroll
-  for (int n = 0; n < WCI / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-  for (long ch = (long)blockIdx.x * WCHUNKS; ch < nchunks && ch < (long)(blockIdx.x + 1) * WCHUNKS; ++ch) {
-    const int y = (int)(ch / wchunks), x0 = (int)(ch % wchunks) * WP;
-    const int yy = y + dy;
-    for (int t = tid; t < WP * (CN / 8); t += 128) {
-      int p = t / (CN / 8), q = t % (CN / 8);
-      int x = x0 + p, co = co0 + 8 * q;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (x < W && co < Cout) v = *reinterpret_cast<const uint4*>(G + ((size_t)y * W + x) * ldg + offg + co);
-      *reinterpret_cast<uint4*>(&sG[p][8 * q]) = v;
-    }
-    for (int t = tid; t < WP * (WCI / 8); t += 128) {
-      int p = t / (WCI / 8), q = t % (WCI / 8);
-      int x = x0 + p, xx = x + dx;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (x < W && yy >= 0 && yy < H && xx >= 0 && xx < W)
-        v = *reinterpret_cast<const uint4*>(X + ((size_t)yy * W + xx) * ldx + offx + ci0 + 8 * q);
-      *reinterpret_cast<uint4*>(&sX[p][8 * q]) = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k0 = 0; k0 < WP; k0 += 16) {
-      // A (16 co x 16 px, row-major) from the pixel-major tile: 8x8 blocks
-      // (co 0-7 | 8-15) x (px 0-7 | 8-15), each read transposed
-      uint32_t a[4];
-      {
-        const int blk = lane >> 3, r = lane & 7;
-        const int px = k0 + r + ((blk >> 1) & 1) * 8, co = warp * 16 + (blk & 1) * 8;
-        ldsm_x4_t(a, &sG[px][co]);
-      }
-#pragma unroll
-      for (int n = 0; n < WCI / 8; ++n) {
-        uint32_t b[2];
-        const int blk = (lane >> 3) & 1, r = lane & 7;
-        ldsm_x2_t(b, &sX[k0 + r + blk * 8][n * 8]);
-        mma_bf16(acc[n], a, b);
-      }
-    }
-    __syncthreads();
-  }
-  const int g = lane >> 2, tq = lane & 3;
-#pragma unroll
-  for (int n = 0; n < WCI / 8; ++n)
-#pragma unroll
-    for (int hr = 0; hr < 2; ++hr) {
-      const int co = co0 + warp * 16 + g + 8 * hr, ci = ci0 + n * 8 + 2 * tq;
-      if (co >= Cout) continue;
-      atomicAdd(&dW[((size_t)co * 9 + tap) * Cin + ci], acc[n][2 * hr]);
-      atomicAdd(&dW[((size_t)co * 9 + tap) * Cin + ci + 1], acc[n][2 * hr + 1]);
-    }
-}
 
 // ---------------------------------------------------------- elementwise
 
@@ -316,13 +217,6 @@ inline int grid1(long n) {
 }
 
 }  // namespace
-
-void conv3x3_wgrad(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* G, int ldg, int offg, const bf16* X,
-                   int ldx, int offx, float* dW) {
-  const long nchunks = (long)H * ((W + WP - 1) / WP);
-  dim3 grd((unsigned)((nchunks + WCHUNKS - 1) / WCHUNKS), 9, ((Cout + CN - 1) / CN) * (Cin / WCI));
-  k_conv3x3_wgrad<<<grd, 128, 0, s>>>(H, W, Cin, Cout, G, ldg, offg, X, ldx, offx, dW);
-}
 
 void relu_grad(cudaStream_t s, long npix, int C, bf16* G, int ldg, int offg, const bf16* Y, int ldy, int offy) {
   k_relu_grad<<<grid1(npix * C), 256, 0, s>>>(npix, C, G, ldg, offg, Y, ldy, offy);

@@ -23,8 +23,9 @@ size_t packed_conv_weights(int Cin, int Cout);
 void pack_conv_weights(cudaStream_t s, int Cin, int Cout, const bf16* w, bf16* wpk, bool flip);
 // true once a convolution kernel has given up a bounded wait
 bool conv_tc_failed();
-// dW[co][tap][ci] += sum_p G[p][co] X[p + shift(tap)][ci]
-void conv3x3_wgrad(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* G, int ldg, int offg, const bf16* X,
+// dW[co][tap][ci] += sum_p G[p][co] X[p + shift(tap)][ci] on the tcgen05 tensor
+// cores (k_conv_tc.cu); Cout <= 128; returns 0, or -1 with ibm_last_error set
+int conv3x3_wgrad(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* G, int ldg, int offg, const bf16* X,
                    int ldx, int offx, float* dW);
 void relu_grad(cudaStream_t s, long npix, int C, bf16* G, int ldg, int offg, const bf16* Y, int ldy, int offy);
 void avgpool(cudaStream_t s, int H, int W, int C, const bf16* X, int ldx, int offx, bf16* Y, int ldy, int offy);

@@ -236,7 +236,7 @@ int conv_backward(ibm_unet* n, const Edge& e, cudaStream_t s, bool need_dx) {
   Act gy = grad_of(n, e.y), gx = grad_of(n, e.x);
   const long npix = (long)L.H * L.W;
   if (c.relu) relu_grad(s, npix, c.cout, gy.p, gy.ld, gy.off, e.y.p, e.y.ld, e.y.off);
-  conv3x3_wgrad(s, L.H, L.W, c.cin, c.cout, gy.p, gy.ld, gy.off, e.x.p, e.x.ld, e.x.off, n->grad + c.w);
+  if (conv3x3_wgrad(s, L.H, L.W, c.cin, c.cout, gy.p, gy.ld, gy.off, e.x.p, e.x.ld, e.x.off, n->grad + c.w)) return -1;
   bias_grad(s, npix, c.cout, gy.p, gy.ld, gy.off, n->grad + c.b);
   if (need_dx)
     return conv3x3(s, L.H, L.W, c.cout, c.cin, gy.p, gy.ld, gy.off, n->wpkf + c.pkf, nullptr, gx.p, gx.ld, gx.off,
