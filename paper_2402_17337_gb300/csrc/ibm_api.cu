@@ -1168,8 +1168,8 @@ int step_pre(ibm_ctx* c, ibm_step_stats* st, double* thr) {
     if (c->ws_mode == 1) {
       // the plain guess is kept; the learned one replaces it only if it
       // starts the solve with less than half the residual (the plain
-      // iteration is the fallback and the judge; a merely smaller maximum
-      // residual did not mean fewer sweeps)
+      // iteration is the fallback and decides when the solve ends; a merely
+      // smaller maximum residual did not mean fewer sweeps)
       rc = ibm_unet_forward(c->ws_net, c->ws_feat, c->Hc, c->Wc, c->ws_out, c->stream);
       if (rc) return rc;
       CUDA_TRY(cudaMemcpyAsync(c->phi_old, c->phi, c->nelem * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));

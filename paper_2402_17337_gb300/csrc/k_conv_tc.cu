@@ -470,10 +470,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // of W'[co][tap][ci], zero for co >= Cout.  W' is the layer's weights
 // w[Cout][9][Cin]; with flip it is the data-gradient operator of a layer
 // whose weights are w[Cin][9][Cout]: W'[co][tap][ci] = w[ci][8 - tap][co].
-__global__ void k_pack_conv_weights(int Cin, int Cout, int NT, int ntiles, const bf16* __restrict__ w,
-                                    bf16* __restrict__ wpk, int flip) {
-  const int nchunks = Cin / 16;
-  const long n = (long)ntiles * nchunks * 9 * NT * 16;
+// One launch packs every job (blockIdx.y = job).
+__global__ void k_pack_conv_weights(const PackJob* __restrict__ jobs) {
+  const PackJob J = jobs[blockIdx.y];
+  const int Cin = J.cin, Cout = J.cout, NT = J.nt, nchunks = Cin / 16;
+  const long n = (long)J.ntiles * nchunks * 9 * NT * 16;
   for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
     const int e = (int)(k & 7), row = (int)((k >> 3) & 7), g = (int)((k >> 6) & 1);
     long r = k >> 7;
@@ -484,8 +485,9 @@ __global__ void k_pack_conv_weights(int Cin, int Cout, int NT, int ntiles, const
     const int ch = (int)(r % nchunks), t = (int)(r / nchunks);
     const int co = t * NT + ngrp * 8 + row, ci = ch * 16 + g * 8 + e;
     bf16 v = __float2bfloat16_rn(0.f);
-    if (co < Cout) v = flip ? w[((size_t)ci * 9 + (8 - tap)) * Cout + co] : w[((size_t)co * 9 + tap) * Cin + ci];
-    wpk[k] = v;
+    if (co < Cout)
+      v = J.flip ? J.w[((size_t)ci * 9 + (8 - tap)) * Cout + co] : J.w[((size_t)co * 9 + tap) * Cin + ci];
+    J.wpk[k] = v;
   }
 }
 
@@ -545,11 +547,21 @@ size_t packed_conv_weights(int Cin, int Cout) {
   return (size_t)ntiles * NT * 9 * Cin;
 }
 
-void pack_conv_weights(cudaStream_t s, int Cin, int Cout, const bf16* w, bf16* wpk, bool flip) {
-  const int NT = conv_tile_channels(Cout), ntiles = (Cout + NT - 1) / NT;
-  const long n = (long)packed_conv_weights(Cin, Cout);
-  long b = (n + 255) / 256;
-  k_pack_conv_weights<<<(int)(b > 4096 ? 4096 : b), 256, 0, s>>>(Cin, Cout, NT, ntiles, w, wpk, flip ? 1 : 0);
+PackJob pack_job(int Cin, int Cout, const bf16* w, bf16* wpk, bool flip) {
+  PackJob j{};
+  j.cin = Cin;
+  j.cout = Cout;
+  j.nt = conv_tile_channels(Cout);
+  j.ntiles = (Cout + j.nt - 1) / j.nt;
+  j.flip = flip ? 1 : 0;
+  j.w = w;
+  j.wpk = wpk;
+  return j;
+}
+
+void pack_conv_weights(cudaStream_t s, const PackJob* jobs_dev, int njobs, long max_elems) {
+  long b = (max_elems + 255) / 256;
+  k_pack_conv_weights<<<dim3((unsigned)(b > 1024 ? 1024 : b), (unsigned)njobs), 256, 0, s>>>(jobs_dev);
 }
 
 int conv3x3_wgrad(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* Gd, int ldg, int offg, const bf16* X,

@@ -22,20 +22,6 @@ using bf16 = __nv_bfloat16;
 
 namespace {
 
-// ---------------------------------------------------------- elementwise
-
-// G[p][c] (a slice) *= (Y[p][c] > 0): gradient through ReLU, in place
-__global__ void k_relu_grad(long npix, int C, bf16* __restrict__ G, int ldg, int offg, const bf16* __restrict__ Y,
-                            int ldy, int offy) {
-  long n = npix * C;
-  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
-    long p = k / C;
-    int c = (int)(k % C);
-    bf16& g = G[p * ldg + offg + c];
-    if (!(__bfloat162float(Y[p * ldy + offy + c]) > 0.f)) g = __float2bfloat16_rn(0.f);
-  }
-}
-
 // Kernels of the forward pass are programmatic dependent launches: each
 // waits for the previous kernel on the stream to complete (and its writes to
 // be visible) before touching global memory, then lets the next one start.
@@ -58,9 +44,7 @@ void launch_pdl(void (*k)(KArgs...), int grid, int block, cudaStream_t s, Args..
   cudaLaunchKernelEx(&lc, k, static_cast<KArgs>(args)...);
 }
 
-// 2x2 average pool (H, W even): out[y][x][c] = mean of the 2x2 block; one
-// thread per output pixel and 8 channels (C, the slices' ld and off are
-// multiples of 8: 16-byte loads and stores)
+// 8 BF16 channels (16 bytes) to FP32
 __device__ inline void bf16x8_to_float(const uint4& u, float (&f)[8]) {
   const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
@@ -70,6 +54,42 @@ __device__ inline void bf16x8_to_float(const uint4& u, float (&f)[8]) {
     f[2 * j + 1] = t.y;
   }
 }
+
+// FP32 to 8 BF16 channels (16 bytes), round to nearest
+__device__ inline uint4 bf16x8_to(const float (&f)[8]) {
+  uint4 o;
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+  return o;
+}
+
+// ---------------------------------------------------------- elementwise
+
+// G[p][c] (a slice) *= (Y[p][c] > 0): gradient through ReLU, in place; one
+// thread per pixel and 8 channels (C, the slices' ld and off are multiples
+// of 8: 16-byte loads and stores)
+__global__ void k_relu_grad(long npix, int C, bf16* __restrict__ G, int ldg, int offg, const bf16* __restrict__ Y,
+                            int ldy, int offy) {
+  const int Gc = C / 8;
+  const long n = npix * Gc;
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    const long p = k / Gc;
+    const int c0 = (int)(k % Gc) * 8;
+    uint4* gp = reinterpret_cast<uint4*>(G + p * ldg + offg + c0);
+    float g[8], y[8];
+    bf16x8_to_float(*gp, g);
+    bf16x8_to_float(*reinterpret_cast<const uint4*>(Y + p * ldy + offy + c0), y);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (!(y[j] > 0.f)) g[j] = 0.f;
+    *gp = bf16x8_to(g);
+  }
+}
+
+// 2x2 average pool (H, W even): out[y][x][c] = mean of the 2x2 block; one
+// thread per output pixel and 8 channels (C, the slices' ld and off are
+// multiples of 8: 16-byte loads and stores)
 __global__ void k_avgpool(int H, int W, int C, const bf16* __restrict__ X, int ldx, int offx, bf16* __restrict__ Y,
                           int ldy, int offy) {
   pdl_enter();
@@ -95,17 +115,23 @@ __global__ void k_avgpool(int H, int W, int C, const bf16* __restrict__ X, int l
   }
 }
 
-// gradient of the average pool: dX[2y+a][2x+b][c] (+)= dY[y][x][c] / 4
+// gradient of the average pool: dX[2y+a][2x+b][c] (+)= dY[y][x][c] / 4; one
+// thread per fine pixel and 8 channels
 __global__ void k_avgpool_grad(int H, int W, int C, const bf16* __restrict__ dY, int ldy, int offy,
                                bf16* __restrict__ dX, int ldx, int offx, int accumulate) {
-  long n = (long)H * W * C;
-  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
-    int c = (int)(k % C);
-    long p = k / C;
-    int x = (int)(p % W), y = (int)(p / W);
-    float g = 0.25f * __bfloat162float(dY[((long)(y / 2) * (W / 2) + x / 2) * ldy + offy + c]);
-    bf16& d = dX[p * ldx + offx + c];
-    d = __float2bfloat16_rn(accumulate ? __bfloat162float(d) + g : g);
+  const int Gc = C / 8, n = H * W * Gc;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int c0 = (k % Gc) * 8, p = k / Gc, x = p % W, y = p / W;
+    float g[8], d[8];
+    bf16x8_to_float(*reinterpret_cast<const uint4*>(dY + ((size_t)(y / 2) * (W / 2) + x / 2) * ldy + offy + c0), g);
+    uint4* dp = reinterpret_cast<uint4*>(dX + (size_t)p * ldx + offx + c0);
+    if (accumulate) bf16x8_to_float(*dp, d);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float gj = 0.25f * g[j];
+      d[j] = accumulate ? d[j] + gj : gj;
+    }
+    *dp = bf16x8_to(d);
   }
 }
 
@@ -122,36 +148,57 @@ __global__ void k_upsample(int H, int W, int C, const bf16* __restrict__ X, int 
   }
 }
 
-// gradient of the upsampling: dX[y][x][c] (+)= sum of the 2x2 block of dY
+// gradient of the upsampling: dX[y][x][c] (+)= sum of the 2x2 block of dY;
+// one thread per coarse pixel and 8 channels
 __global__ void k_upsample_grad(int H, int W, int C, const bf16* __restrict__ dY, int ldy, int offy,
                                 bf16* __restrict__ dX, int ldx, int offx, int accumulate) {
-  const int H2 = H / 2, W2 = W / 2;
-  long n = (long)H2 * W2 * C;
-  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
-    int c = (int)(k % C);
-    long p = k / C;
-    int x = (int)(p % W2), y = (int)(p / W2);
-    auto at = [&](int yy, int xx) { return __bfloat162float(dY[((long)yy * W + xx) * ldy + offy + c]); };
-    float g = at(2 * y, 2 * x) + at(2 * y, 2 * x + 1) + at(2 * y + 1, 2 * x) + at(2 * y + 1, 2 * x + 1);
-    bf16& d = dX[p * ldx + offx + c];
-    d = __float2bfloat16_rn(accumulate ? __bfloat162float(d) + g : g);
+  const int H2 = H / 2, W2 = W / 2, Gc = C / 8, n = H2 * W2 * Gc;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int c0 = (k % Gc) * 8, p = k / Gc, x = p % W2, y = p / W2;
+    auto at = [&](int yy, int xx, float (&f)[8]) {
+      bf16x8_to_float(*reinterpret_cast<const uint4*>(dY + ((size_t)yy * W + xx) * ldy + offy + c0), f);
+    };
+    float a[8], b[8], c[8], e[8], d[8];
+    at(2 * y, 2 * x, a);
+    at(2 * y, 2 * x + 1, b);
+    at(2 * y + 1, 2 * x, c);
+    at(2 * y + 1, 2 * x + 1, e);
+    uint4* dp = reinterpret_cast<uint4*>(dX + (size_t)p * ldx + offx + c0);
+    if (accumulate) bf16x8_to_float(*dp, d);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float g = a[j] + b[j] + c[j] + e[j];
+      d[j] = accumulate ? d[j] + g : g;
+    }
+    *dp = bf16x8_to(d);
   }
 }
 
-// bias gradient: db[c] += sum_p G[p][c] (one block per channel group)
+// bias gradient: db[c] += sum_p G[p][c].  A block of 256 threads reads 256 /
+// (C / 8) pixels at a time, each thread 8 channels of one pixel (16 bytes),
+// sums over its pixels, then the block sums its threads' partials per channel
+// in shared memory and adds them to db (C <= 256).
 __global__ void k_bias_grad(long npix, int C, const bf16* __restrict__ G, int ldg, int offg, float* __restrict__ db) {
-  const int c = blockIdx.x;
-  float s = 0.f;
-  for (long p = threadIdx.x + (long)blockIdx.y * blockDim.x; p < npix; p += (long)blockDim.x * gridDim.y)
-    s += __bfloat162float(G[p * ldg + offg + c]);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  __shared__ float ws[32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __shared__ float part[256][9];  // [thread][8 channels], padded against bank conflicts
+  const int Gc = C / 8, rows = blockDim.x / Gc;
+  const int g = threadIdx.x % Gc, r = threadIdx.x / Gc;
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (r < rows) {
+    for (long p = (long)blockIdx.x * rows + r; p < npix; p += (long)gridDim.x * rows) {
+      float v[8];
+      bf16x8_to_float(*reinterpret_cast<const uint4*>(G + p * ldg + offg + 8 * g), v);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] += v[j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) part[threadIdx.x][j] = acc[j];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    float t = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
-    atomicAdd(&db[c], t);
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    const int cg = c / 8, j = c % 8;
+    float sum = 0.f;
+    for (int rr = 0; rr < rows; ++rr) sum += part[rr * Gc + cg][j];
+    atomicAdd(&db[c], sum);
   }
 }
 
@@ -219,25 +266,28 @@ inline int grid1(long n) {
 }  // namespace
 
 void relu_grad(cudaStream_t s, long npix, int C, bf16* G, int ldg, int offg, const bf16* Y, int ldy, int offy) {
-  k_relu_grad<<<grid1(npix * C), 256, 0, s>>>(npix, C, G, ldg, offg, Y, ldy, offy);
+  k_relu_grad<<<grid1(npix * C / 8), 256, 0, s>>>(npix, C, G, ldg, offg, Y, ldy, offy);
 }
 void avgpool(cudaStream_t s, int H, int W, int C, const bf16* X, int ldx, int offx, bf16* Y, int ldy, int offy) {
   launch_pdl(k_avgpool, grid1((long)H * W * C / 32), 256, s, H, W, C, X, ldx, offx, Y, ldy, offy);
 }
 void avgpool_grad(cudaStream_t s, int H, int W, int C, const bf16* dY, int ldy, int offy, bf16* dX, int ldx, int offx,
                   bool acc) {
-  k_avgpool_grad<<<grid1((long)H * W * C), 256, 0, s>>>(H, W, C, dY, ldy, offy, dX, ldx, offx, acc ? 1 : 0);
+  k_avgpool_grad<<<grid1((long)H * W * C / 8), 256, 0, s>>>(H, W, C, dY, ldy, offy, dX, ldx, offx, acc ? 1 : 0);
 }
 void upsample(cudaStream_t s, int H, int W, int C, const bf16* X, int ldx, int offx, bf16* Y, int ldy, int offy) {
   launch_pdl(k_upsample, grid1((long)H * W * C / 8), 256, s, H, W, C, X, ldx, offx, Y, ldy, offy);
 }
 void upsample_grad(cudaStream_t s, int H, int W, int C, const bf16* dY, int ldy, int offy, bf16* dX, int ldx, int offx,
                    bool acc) {
-  k_upsample_grad<<<grid1((long)H * W * C / 4), 256, 0, s>>>(H, W, C, dY, ldy, offy, dX, ldx, offx, acc ? 1 : 0);
+  k_upsample_grad<<<grid1((long)H * W * C / 32), 256, 0, s>>>(H, W, C, dY, ldy, offy, dX, ldx, offx, acc ? 1 : 0);
 }
 void bias_grad(cudaStream_t s, long npix, int C, const bf16* G, int ldg, int offg, float* db) {
-  dim3 grd(C, 32);
-  k_bias_grad<<<grd, 256, 0, s>>>(npix, C, G, ldg, offg, db);
+  const long rows = 256 / (C / 8);
+  long blocks = (npix + rows * 8 - 1) / (rows * 8);  // at least 8 pixels per thread
+  if (blocks > 608) blocks = 608;
+  if (blocks < 1) blocks = 1;
+  k_bias_grad<<<(int)blocks, 256, 0, s>>>(npix, C, G, ldg, offg, db);
 }
 void mse(cudaStream_t s, long npix, const float* out, int ldo, const float* target, const float* mask, float inv_count,
          bf16* dout, int ldd, double* loss) {

@@ -20,7 +20,15 @@ int conv3x3(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* X, int 
 // operator of a layer with weights w[Cin][9][Cout], W'[co][tap][ci] =
 // w[ci][8 - tap][co])
 size_t packed_conv_weights(int Cin, int Cout);
-void pack_conv_weights(cudaStream_t s, int Cin, int Cout, const bf16* w, bf16* wpk, bool flip);
+struct PackJob {
+  int cin, cout, nt, ntiles, flip;
+  const bf16* w;
+  bf16* wpk;
+};
+PackJob pack_job(int Cin, int Cout, const bf16* w, bf16* wpk, bool flip);
+// every job of the device array jobs_dev in one launch; max_elems: the
+// largest job's packed_conv_weights
+void pack_conv_weights(cudaStream_t s, const PackJob* jobs_dev, int njobs, long max_elems);
 // true once a convolution kernel has given up a bounded wait
 bool conv_tc_failed();
 // dW[co][tap][ci] += sum_p G[p][co] X[p + shift(tap)][ci] on the tcgen05 tensor

@@ -9,6 +9,7 @@
 // The four input features are zero-padded to 16 channels; H and W must be
 // multiples of 8.  Activations are BF16; weights are kept as FP32 master
 // copies (Adam) and BF16 working copies (tensor-core kernels).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <random>
@@ -55,6 +56,9 @@ struct ibm_unet {
   bf16 *wpk = nullptr, *wpkf = nullptr;  // packed for the tensor-core convolutions: forward, data gradient
   size_t npk = 0, npkf = 0;
   bool wdirty = true;  // wb changed since the packed copies were made
+  PackJob* pack_jobs = nullptr;  // device: one forward and one data-gradient job per convolution
+  int npack = 0;
+  long pack_max = 0;
   long long adam_t = 0;
   // activations for the current size
   int H = 0, W = 0;
@@ -66,7 +70,7 @@ struct ibm_unet {
 
   ~ibm_unet() {
     free_acts();
-    void* ps[] = {pw, grad, m, v, wb, wpk, wpkf, loss_d};
+    void* ps[] = {pw, grad, m, v, wb, wpk, wpkf, loss_d, pack_jobs};
     for (void* p : ps)
       if (p) cudaFree(p);
   }
@@ -189,10 +193,7 @@ int level_of(ibm_unet* n, const Act& a) {
 // weights changed (creation, new parameters, an Adam step)
 void ensure_packed(ibm_unet* n, cudaStream_t s) {
   if (!n->wdirty) return;
-  for (const Conv& c : n->conv) {
-    pack_conv_weights(s, c.cin, c.cout, n->wb + c.w, n->wpk + c.pk, false);
-    pack_conv_weights(s, c.cout, c.cin, n->wb + c.w, n->wpkf + c.pkf, true);
-  }
+  pack_conv_weights(s, n->pack_jobs, n->npack, n->pack_max);
   n->wdirty = false;
 }
 
@@ -324,6 +325,20 @@ int ibm_unet_create(const int widths[4], unsigned long long seed, ibm_unet** out
   A((void**)&n->wb, n->nparam * 2);
   A((void**)&n->wpk, n->npk * 2);
   A((void**)&n->wpkf, n->npkf * 2);
+  std::vector<PackJob> jobs;
+  if (!rc) {
+    for (const Conv& c : n->conv) {
+      jobs.push_back(pack_job(c.cin, c.cout, n->wb + c.w, n->wpk + c.pk, false));
+      jobs.push_back(pack_job(c.cout, c.cin, n->wb + c.w, n->wpkf + c.pkf, true));
+      n->pack_max = std::max(n->pack_max, (long)std::max(packed_conv_weights(c.cin, c.cout),
+                                                          packed_conv_weights(c.cout, c.cin)));
+    }
+    n->npack = (int)jobs.size();
+  }
+  A((void**)&n->pack_jobs, jobs.size() * sizeof(PackJob) + 16);
+  if (!rc && cudaMemcpy(n->pack_jobs, jobs.data(), jobs.size() * sizeof(PackJob), cudaMemcpyHostToDevice) !=
+                 cudaSuccess)
+    rc = IBM_E_CUDA;
   A((void**)&n->loss_d, 8);
   if (!rc && cudaMemcpy(n->pw, h.data(), n->nparam * 4, cudaMemcpyHostToDevice) != cudaSuccess) rc = IBM_E_CUDA;
   if (!rc) {
