@@ -287,8 +287,27 @@ def cpu_oracle_sample(cfg, state=None, max_seconds=60.0):
             "sweep_ms_all": 1e3 * sw_all, "sweep_ms_1thread": 1e3 * sw_one, "host": host_info()}
 
 
-def run_reference(args, cfg):
-    """--impl reference: the oracle on the host cores, same metric."""
+def workload_config(cfg, world):
+    """The `config` object of a single-grid workload: the same in both arms."""
+    return {"workload": cfg.name, "nx": cfg.nx, "ny": cfg.ny, "global_batch": world,
+            "parallelism": f"replicas x{world}",
+            "l2": f"state 14 FP64 fields x {cfg.cells * 8 / 1e6:.0f} MB > L2 (129 MB); FP32 sweep "
+                  f"arrays {cfg.cells * 16 / 1e6:.0f} MB; no flush"}
+
+
+def batch_config(cfgs, world):
+    """The `config` object of the batch workload: the same in both arms."""
+    cells = sum(c.cells for c in cfgs)
+    return {"workload": "batch64" if len(cfgs) == 64 else f"batch64[:{len(cfgs)}]", "cases": len(cfgs),
+            "cells_per_step": cells, "grids": sorted({f"{c.nx}x{c.ny}" for c in cfgs}),
+            "global_batch": len(cfgs) * world, "parallelism": f"replicas x{world}",
+            "l2": f"{cells * 16 / 1e6:.0f} MB of FP32 sweep arrays per launch set; no flush"}
+
+
+def run_reference(args, cfg, config):
+    """--impl reference: the oracle on the host cores, same metric; config:
+    the timed arm's `config` object (for the batch, one of its cases is the
+    bounded sample)."""
     rank = env_int("RANK", 0)
     if rank != 0:
         return 0
@@ -317,8 +336,9 @@ def run_reference(args, cfg):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": cfg.name, "nx": cfg.nx, "ny": cfg.ny, "global_batch": 1, "path": "cpu-oracle",
-                   "poisson_sweeps_per_step": statistics.mean(sweeps), "omega_p": w},
+        "config": config,
+        "details": {"path": "cpu-oracle", "sample_workload": cfg.name,
+                    "poisson_sweeps_per_step": statistics.mean(sweeps), "omega_p": w},
         "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": threads, "kind": "oracle",
                          "sample": f"{args.warmup} untimed + {args.steps} timed full steps of {cfg.name} "
                                    f"from the uniform free stream, FP64 oracle, {threads} OpenMP threads in the "
@@ -476,15 +496,13 @@ def run_batch(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 sweeps, f64 residual/update/norms", "data": "synthetic",
-            "config": {"workload": "batch64" if args.cases == 64 else f"batch64[:{args.cases}]",
-                       "cases": args.cases, "cells_per_step": sum(cells),
-                       "grids": sorted({f"{c.nx}x{c.ny}" for c in cfgs}), "global_batch": args.cases * world,
-                       "parallelism": f"replicas x{world}", "path": "mixed, batched, " + ("graph replay" if args.batch_launch == "graphs" else
-                                                                 "direct programmatic dependent launches"),
-                       "warm_start": "previous increment", "sor_us_per_sweep_whole_batch": prof["sor_us_per_sweep"],
-                       "poisson_sweeps_per_step_sum": statistics.mean(sum(x["sweeps_p"] for x in st) for st in stats),
-                       "l2": f"{sum(cells) * 16 / 1e6:.0f} MB of FP32 sweep arrays per launch set; no flush",
-                       "div_max": max(x["div_max"] for st in stats for x in st)},
+            "config": batch_config(cfgs, world),
+            "details": {"path": "mixed, batched, " + ("graph replay" if args.batch_launch == "graphs" else
+                                                      "direct programmatic dependent launches"),
+                        "warm_start": "previous increment", "sor_us_per_sweep_whole_batch": prof["sor_us_per_sweep"],
+                        "poisson_sweeps_per_step_sum": statistics.mean(sum(x["sweeps_p"] for x in st)
+                                                                       for st in stats),
+                        "div_max": max(x["div_max"] for st in stats for x in st)},
             "gpu_launches": prof["launches"],
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -529,11 +547,11 @@ def main():
     from paper_2402_17337_gb300 import workloads as W
     if args.workload == "batch64":
         if args.impl == "reference":
-            return run_reference(args, W.batch64()[0])
+            return run_reference(args, W.batch64()[0], batch_config(W.batch64()[:args.cases], env_int("WORLD_SIZE", 1)))
         return run_batch(args)
     cfg = getattr(W, args.workload)()
     if args.impl == "reference":
-        return run_reference(args, cfg)
+        return run_reference(args, cfg, workload_config(cfg, env_int("WORLD_SIZE", 1)))
 
     import numpy as np
     import torch
@@ -794,15 +812,13 @@ def main():
             "dtype": ("f32 sweeps, f64 residual/update/norms" + (", bf16 U-Net" if learned else ""))
                      if precision >= 1 else "f64",
             "data": "synthetic",
-            "config": {"workload": cfg.name, "nx": cfg.nx, "ny": cfg.ny, "global_batch": world,
-                       "parallelism": f"replicas x{world}", "path": args.precision, "warm_start": ws_desc,
-                       "omega_p": cfg.omega_p, "omega_p_grid_formula": omega_default,
-                       "mixed_plain_warmstart": plain_ws, "plain_fp64": fp64, "multigrid_variant": mg,
-                       "steps_counted": total_ok, "poisson_sweeps_per_step": statistics.mean(sweeps),
-                       "helm_sweeps_per_step": statistics.mean(st["sweeps_u"] + st["sweeps_v"] for st in stats),
-                       "l2": f"state 14 FP64 fields x {cfg.cells * 8 / 1e6:.0f} MB > L2 (129 MB); FP32 sweep "
-                             f"arrays {cfg.cells * 16 / 1e6:.0f} MB; no flush",
-                       "div_max": max(st["div_max"] for st in stats)},
+            "config": workload_config(cfg, world),
+            "details": {"path": args.precision, "warm_start": ws_desc,
+                        "omega_p": cfg.omega_p, "omega_p_grid_formula": omega_default,
+                        "mixed_plain_warmstart": plain_ws, "plain_fp64": fp64, "multigrid_variant": mg,
+                        "steps_counted": total_ok, "poisson_sweeps_per_step": statistics.mean(sweeps),
+                        "helm_sweeps_per_step": statistics.mean(st["sweeps_u"] + st["sweeps_v"] for st in stats),
+                        "div_max": max(st["div_max"] for st in stats)},
             "gpu_launches": launches,
             "roofline": roof,
             "network": netroof,
