@@ -61,6 +61,8 @@ SOR32_TRAFFIC = {
     ("plunge_4096x2048", (80, 16, 16, 8)): 115.323392e6,
     ("plunge_2048x1024", (80, 16, 16, 10)): 25.23136e6,
     ("plunge_4096x2048", (80, 16, 16, 10)): 118.77504e6,
+    ("plunge_2048x1024", (80, 16, 16, 9)): 25.23264e6,
+    ("plunge_4096x2048", (80, 16, 16, 9)): 115.576576e6,
 }
 # warp instructions issued per launch of the FP32 sweep kernel (ncu smsp__inst_executed.sum of one
 # launch, profiles/k_sor32_rb_*.md), by workload and tile shape: the issue roofline of a kernel that is
@@ -72,6 +74,8 @@ SOR32_INST = {
     ("plunge_4096x2048", (80, 16, 16, 8)): 61.66415e6,
     ("plunge_2048x1024", (80, 16, 16, 10)): 13.381214e6,
     ("plunge_4096x2048", (80, 16, 16, 10)): 52.308382e6,
+    ("plunge_2048x1024", (80, 16, 16, 9)): 13.40867e6,
+    ("plunge_4096x2048", (80, 16, 16, 9)): 52.41571e6,
 }
 WORKLOADS = ("plunge_2048x1024", "plunge_4096x2048", "unet_1024x512", "batch64")
 METRIC = "cell-steps/s at div<1e-8: learned warm-start+mixed vs plain FP64, one GB300"

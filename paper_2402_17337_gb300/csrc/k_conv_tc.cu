@@ -512,7 +512,7 @@ unsigned int* error_flag(unsigned int** dev) {
   static std::once_flag once;
   std::call_once(once, [] {
     void* h = nullptr;
-    if (cudaHostAlloc(&h, sizeof(unsigned int), cudaHostAllocMapped) == cudaSuccess) {
+    if (cudaHostAlloc(&h, sizeof(unsigned int), cudaHostAllocMapped | cudaHostAllocPortable) == cudaSuccess) {
       host = static_cast<unsigned int*>(h);
       *host = 0u;
       void* d = nullptr;
@@ -530,6 +530,20 @@ unsigned int* error_flag(unsigned int** dev) {
 int tmem_min_smem(int cols) {
   const int k = 512 / cols;  // CTAs whose columns fit
   return SM_SMEM / (k + 1) - 2048 + 1;
+}
+
+// kernel attributes (shared memory size and carveout) are set once per device
+bool first_use_on_device(int which) {
+  static std::mutex mu;
+  static unsigned long long done[2] = {0ull, 0ull};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return true;
+  std::lock_guard<std::mutex> lock(mu);
+  const unsigned long long bit = 1ull << dev;
+  if (done[which] & bit) return false;
+  done[which] |= bit;
+  return true;
 }
 
 int pow2_at_least(int v) {
@@ -620,12 +634,10 @@ int conv3x3_wgrad(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* G
       return -1;
     }
   }
-  static bool attr = false;
-  if (!attr) {
+  if (first_use_on_device(1)) {
     cudaFuncSetAttribute(k_conv3x3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_MAX);
     cudaFuncSetAttribute(k_conv3x3_wgrad_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
                          (int)cudaSharedmemCarveoutMaxShared);
-    attr = true;
   }
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -714,14 +726,12 @@ int conv3x3(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* X, int 
     set_last_error("cuTensorMapEncodeTiled rejected an activation view");
     return -1;
   }
-  static bool attr = false;
-  if (!attr) {
+  if (first_use_on_device(0)) {
     // the largest shared-memory carveout, so that several CTAs fit on an SM
     for (auto k : {k_conv3x3_tc<true>, k_conv3x3_tc<false>}) {
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_MAX);
       cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     }
-    attr = true;
   }
   // persistent CTAs: as many as fit on the device at once (shared memory,
   // with 1 KB static and 1 KB reserved per CTA; threads; tensor-memory
