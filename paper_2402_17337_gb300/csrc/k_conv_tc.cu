@@ -32,6 +32,10 @@
 // and ReLU, while the next tile accumulates into a second accumulator.
 // Every wait is bounded: a wait that gives up sets a flag in mapped host
 // memory and the CTA skips the rest of its work.
+//
+// The weight gradient (k_conv3x3_wgrad_tc, below) is a GEMM over pixels
+// whose operands come MN-major straight from TMA boxes of the same
+// [pixel][8 channels] form.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
