@@ -1150,7 +1150,7 @@ int step_pre(ibm_ctx* c, ibm_step_stats* st, double* thr) {
   c->prof.launches += 1;
   if (c->has_body) {
     launch_body_source(c->stream, g, c->band, c->fc, c->uh, c->vh, c->b, c->qband, dt, c->rowsum, c->sc);
-    c->prof.launches += 3;
+    c->prof.launches += 3;  // row sums, their total, the mass source
   }
   // a7: warm start.  The solve starts from the previous increment, or from
   // its linear extrapolation in time; the learned form adds the U-Net's

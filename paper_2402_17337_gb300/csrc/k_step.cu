@@ -354,9 +354,48 @@ __device__ __forceinline__ void body_sums_body(Geo g, Band B, const uint8_t* __r
   sc->body_sum[1] = sv;
   sc->cbar = sv > 0.0 ? sdv / sv : 0.0;
 }
-__global__ void k_body_sums(Geo g, Band B, const uint8_t* __restrict__ fc, const double* __restrict__ uh,
-                            const double* __restrict__ vh, double* __restrict__ rowsum, DevScalars* sc) {
-  body_sums_body(g, B, fc, uh, vh, rowsum, sc, blockIdx.x, blockIdx.y);
+
+// The same sums over many SMs: one warp per band row, whose lanes evaluate 32
+// consecutive cells at a time while every lane adds the body cells' values
+// in increasing i (broadcast by shuffles), the order of the sequential loop
+// above, so the row sums are the same bit for bit; k_body_total then adds
+// the rows in order.
+__global__ void k_body_rows(Geo g, Band B, const uint8_t* __restrict__ fc, const double* __restrict__ uh,
+                            const double* __restrict__ vh, double* __restrict__ rowsum) {
+  const int bj = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (bj >= B.h) return;  // the whole warp
+  const int j = B.j0 + bj;
+  double a = 0.0, b = 0.0;
+  for (int c0 = 0; c0 < B.w; c0 += 32) {
+    const int bi = c0 + lane;
+    double dv = 0.0, v = 0.0;
+    const bool on = bi < B.w && fc[bj * B.w + bi];
+    if (on) {
+      const int i = B.i0 + bi;
+      v = g.dx[i] * g.dy[j];
+      dv = cell_div(g, uh, vh, i, j) * v;
+    }
+    for (unsigned m = __ballot_sync(0xffffffffu, on); m; m &= m - 1) {
+      const int src = __ffs(m) - 1;
+      a += __shfl_sync(0xffffffffu, dv, src);
+      b += __shfl_sync(0xffffffffu, v, src);
+    }
+  }
+  if (lane == 0) {
+    rowsum[2 * bj] = a;
+    rowsum[2 * bj + 1] = b;
+  }
+}
+__global__ void k_body_total(Band B, const double* __restrict__ rowsum, DevScalars* sc) {
+  double sdv = 0.0, sv = 0.0;
+#pragma unroll 8
+  for (int bj = 0; bj < B.h; ++bj) {
+    sdv += rowsum[2 * bj];
+    sv += rowsum[2 * bj + 1];
+  }
+  sc->body_sum[0] = sdv;
+  sc->body_sum[1] = sv;
+  sc->cbar = sv > 0.0 ? sdv / sv : 0.0;
 }
 
 // On body cells (centre inside the body) continuity is replaced by div u = q,
@@ -669,7 +708,8 @@ void launch_rhs(cudaStream_t s, const Geo& g, const double* uh, const double* vh
 void launch_body_source(cudaStream_t s, const Geo& g, const Band& band, const uint8_t* fc, const double* uh,
                         const double* vh, double* b, double* qband, double dt, double* rowsum,
                         DevScalars* sc) {
-  k_body_sums<<<1, 1024, 0, s>>>(g, band, fc, uh, vh, rowsum, sc);
+  k_body_rows<<<(band.h + 7) / 8, 256, 0, s>>>(g, band, fc, uh, vh, rowsum);
+  k_body_total<<<1, 1, 0, s>>>(band, rowsum, sc);
   k_body_fix<<<grid2(band.w, band.h), dim3(TBX, TBY), 0, s>>>(g, band, fc, uh, vh, b, qband, 1.0 / dt, sc);
 }
 
