@@ -334,7 +334,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // ------------------------------------------------------- weight gradient
 //
 // dW[co][tap][ci] += sum over pixels p of G[p][co] X[p + shift(tap)][ci], a
-// GEMM per tap with M = 128 output channels (rows beyond Cout zero), N = NT
+// GEMM per tap with M = 128 output channels (a tile of them; rows beyond
+// Cout zero), N = NT
 // input channels, K = pixels.  Both operands come as TMA boxes of [pixel][8
 // channels], i.e. MN-major: a core matrix is 8 pixels (K) x 8 channels (MN),
 // 16 bytes per pixel; K groups of 8 pixels are 128 bytes apart, MN groups of
@@ -346,8 +347,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 struct WgGeom {
   int P;                // pixels per chunk (a multiple of 16, <= 128)
   int NT, ntiles_ci;    // input channels per tile, tiles
-  int cog;              // 8-channel groups of G that hold channels (< Cout)
-  int a_region, b_region, a_bytes, b_bytes, stage_bytes, tx_bytes, stages;
+  int co_tiles;         // tiles of 128 output channels
+  int a_region, b_region, a_bytes, b_bytes, stage_bytes, stages;
   int tmem_cols, chunks_x, nchunks, ksplit;
 };
 
@@ -361,9 +362,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   volatile int* abort = &abort_flag;
   const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // work unit: blockIdx.x = (ksplit part, tap row, channel tile)
-  const int part = blockIdx.x % G.ksplit, rest = blockIdx.x / G.ksplit;
-  const int dy = rest % 3, zt = rest / 3;
+  // work unit: blockIdx.x = (ksplit part, tap row, input-channel tile,
+  // output-channel tile)
+  const int part = blockIdx.x % G.ksplit;
+  int rest = blockIdx.x / G.ksplit;
+  const int dy = rest % 3;
+  rest /= 3;
+  const int zt = rest % G.ntiles_ci, co0 = (rest / G.ntiles_ci) * 128;
+  const int cog = (Cout - co0) / 8 < 16 ? (Cout - co0) / 8 : 16;  // 8-channel groups of G in this tile
+  const int tx_bytes = cog * G.P * 16 + (G.NT / 8) * (G.P + 2) * 16;
   const int c_begin = (int)((long)G.nchunks * part / G.ksplit), c_end = (int)((long)G.nchunks * (part + 1) / G.ksplit);
   const int nq = c_end - c_begin, S = G.stages;
   if (warp == 0) {
@@ -373,10 +380,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   // the MN groups of A beyond Cout are never loaded: zero them in every stage
-  const int zero_bytes = (16 - G.cog) * G.a_region;
+  const int zero_bytes = (16 - cog) * G.a_region;
   for (int s = 0; s < S; ++s) {
     uint4* z = reinterpret_cast<uint4*>(smem_raw + (sbase - smem_u32(smem_raw)) + s * G.stage_bytes +
-                                        G.cog * G.a_region);
+                                        cog * G.a_region);
     for (int k = threadIdx.x; k < zero_bytes / 16; k += blockDim.x) z[k] = make_uint4(0, 0, 0, 0);
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes seen by the tensor cores
@@ -404,8 +411,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (q >= S && !wait_or_abort(smem_u32(&bar_empty[s]), (uint32_t)(q / S - 1) & 1u, abort)) break;
         const int x0 = (c % G.chunks_x) * G.P, y = c / G.chunks_x;
         const uint32_t st = sbase + s * G.stage_bytes, bar = smem_u32(&bar_full[s]);
-        mbar_expect_tx(bar, G.tx_bytes);
-        for (int g = 0; g < G.cog; ++g) tma_load_3d(st + g * G.a_region, &tmG, 8 * g, x0, y, bar);
+        mbar_expect_tx(bar, tx_bytes);
+        for (int g = 0; g < cog; ++g) tma_load_3d(st + g * G.a_region, &tmG, co0 + 8 * g, x0, y, bar);
         for (int g = 0; g < G.NT / 8; ++g)
           tma_load_3d(st + G.a_bytes + g * G.b_region, &tmX, zt * G.NT + 8 * g, x0 - 1, y + dy - 1, bar);
         issued = q + 1;
@@ -445,7 +452,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // epilogue: lane = output channel co, 16 input channels per load
     if (wait_or_abort(smem_u32(&bar_acc), 0u, abort)) {
       tc_fence_after();
-      const int co = warp * 32 + lane;
+      const int co = co0 + warp * 32 + lane;
       for (int t = 0; t < 3; ++t)
         for (int c0 = 0; c0 < G.NT; c0 += 16) {
           float v[16];
@@ -588,7 +595,7 @@ int conv3x3_wgrad(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* G
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   unsigned int* err_dev = nullptr;
   error_flag(&err_dev);
-  if (!enc || !err_dev || Cout > 128 || Cin % 16 || Cout % 16) {
+  if (!enc || !err_dev || Cin % 16 || Cout % 16) {
     set_last_error("weight gradient: unsupported channel counts or no tensor-map encoder");
     return -1;
   }
@@ -596,13 +603,12 @@ int conv3x3_wgrad(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* G
   G.P = W >= 128 ? 128 : (pow2_at_least(W) < 16 ? 16 : pow2_at_least(W));
   G.NT = Cin <= 128 ? Cin : 128;
   G.ntiles_ci = (Cin + G.NT - 1) / G.NT;
-  G.cog = Cout / 8;
+  G.co_tiles = (Cout + 127) / 128;
   G.a_region = G.P * 16;
   G.a_bytes = 16 * G.a_region;
   G.b_region = ((G.P + 2) * 16 + 127) / 128 * 128;
   G.b_bytes = (G.NT / 8) * G.b_region;
   G.stage_bytes = (G.a_bytes + G.b_bytes + 1023) / 1024 * 1024;
-  G.tx_bytes = G.cog * G.P * 16 + (G.NT / 8) * (G.P + 2) * 16;
   G.stages = 3 * G.stage_bytes + 1024 <= TC_SMEM_MAX ? 3 : 2;
   G.tmem_cols = pow2_at_least(3 * G.NT < 32 ? 32 : 3 * G.NT);
   G.chunks_x = (W + G.P - 1) / G.P;
@@ -651,7 +657,7 @@ int conv3x3_wgrad(cudaStream_t s, int H, int W, int Cin, int Cout, const bf16* G
   if (per_sm > 512 / G.tmem_cols) per_sm = 512 / G.tmem_cols;
   if (per_sm < 1) per_sm = 1;
   // split the pixel chunks so that the CTAs fill the device once
-  const int units = 3 * G.ntiles_ci;
+  const int units = 3 * G.ntiles_ci * G.co_tiles;
   G.ksplit = (int)((long)nsm * per_sm / units);
   if (G.ksplit < 1) G.ksplit = 1;
   if (G.ksplit > G.nchunks) G.ksplit = G.nchunks;

@@ -81,7 +81,8 @@ def _gpu_net(w, seed=7):
 
 EXACT_CASES = [((16, 32, 32, 48), 16, 24, 1, 1 / 64),     # tiny, one pixel tile per row
                ((16, 32, 32, 48), 120, 200, 2, 1 / 64),   # ragged pixel tiles (200 = 3 x 64 + 8) at every level
-               ((32, 64, 128, 128), 128, 256, 1, 1 / 16)]  # the learned warm start's widths
+               ((32, 64, 128, 128), 128, 256, 1, 1 / 16),  # the learned warm start's widths
+               ((16, 32, 64, 256), 32, 64, 3, 1 / 16)]     # 256 and 320 channels: several channel tiles
 
 
 def _frac_bits(a):
