@@ -1174,16 +1174,17 @@ int step_pre(ibm_ctx* c, ibm_step_stats* st, double* thr) {
       if (rc) return rc;
       CUDA_TRY(cudaMemcpyAsync(c->phi_old, c->phi, c->nelem * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
       launch_ws_apply(c->stream, g, c->Hc, c->Wc, c->ws_out, c->ws_cT, c->ws_max, c->phi);
+      // both residual norms in one pass and one wait
       CUDA_TRY(cudaMemsetAsync(&c->sc->res_bits, 0, 8, c->stream));
-      launch_poisson_res(c->stream, g, c->phi, c->b, &c->sc->res_bits);
+      CUDA_TRY(cudaMemsetAsync(&c->sc->res2_bits, 0, 8, c->stream));
+      launch_poisson_res2(c->stream, g, c->phi, c->phi_old, c->b, &c->sc->res_bits, &c->sc->res2_bits);
+      CUDA_TRY(cudaMemcpyAsync(&c->sc_host->res2_bits, &c->sc->res2_bits, sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, c->stream));
       double r_learned = 0.0, r_plain = 0.0;
-      rc = read_norm(c, &c->sc->res_bits, &r_learned);
+      rc = read_norm(c, &c->sc->res_bits, &r_learned);  // waits for the stream
       if (rc) return rc;
-      CUDA_TRY(cudaMemsetAsync(&c->sc->res_bits, 0, 8, c->stream));
-      launch_poisson_res(c->stream, g, c->phi_old, c->b, &c->sc->res_bits);
-      rc = read_norm(c, &c->sc->res_bits, &r_plain);
-      if (rc) return rc;
-      c->prof.launches += unet_forward_launches() + 3;
+      r_plain = bits_to_double(c->sc_host->res2_bits);
+      c->prof.launches += unet_forward_launches() + 2;
       c->prof.ws_applied += 1;
       if (r_learned < 0.5 * r_plain)
         c->prof.ws_kept += 1;

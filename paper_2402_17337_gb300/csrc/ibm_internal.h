@@ -78,6 +78,7 @@ struct DevScalars {
   double S_prev[2];              // momentum inside the body at the previous step
   double force[2];               // Fx, Fy of the last step
   double sum_q;
+  unsigned long long res2_bits;  // a second infinity norm accumulator (two residuals in one pass)
 };
 
 constexpr int RED_BLOCKS = 64;   // fixed partial-reduction width (deterministic sums)
@@ -113,6 +114,10 @@ void launch_poisson_half(cudaStream_t s, const Geo& g, double* phi, const double
                          int colour, double omega);
 void launch_poisson_res(cudaStream_t s, const Geo& g, const double* phi, const double* b,
                         unsigned long long* res_bits);
+// ||b - L_p phi_a||_inf and ||b - L_p phi_b||_inf in one pass, each summed as
+// by launch_poisson_res
+void launch_poisson_res2(cudaStream_t s, const Geo& g, const double* phi_a, const double* phi_b, const double* b,
+                         unsigned long long* bits_a, unsigned long long* bits_b);
 void launch_shift(cudaStream_t s, const Geo& g, double* phi, const DevScalars* sc);
 void launch_bmax(cudaStream_t s, const Geo& g, const double* b, unsigned long long* bits);
 void launch_fill_hash(cudaStream_t s, const Geo& g, double* x);
