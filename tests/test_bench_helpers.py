@@ -44,3 +44,19 @@ def test_unet_flops_match_the_convolutions_the_oracle_runs(widths, H, W, monkeyp
     calls[-1] = (px, cin, 1)      # only output channel 0 is the prediction
     flops = sum(2 * 9 * ci * co * n for n, ci, co in calls)
     assert bench.unet_forward_flops(widths, H, W) == flops
+
+
+def test_config_names_only_the_workload():
+    """Both arms print the same `config` object (built from the workload
+    alone); measurement results go to `details`, never into `config`."""
+    from paper_2402_17337_gb300 import workloads as W
+    bench = load_bench()
+    cfg = W.plunge_2048x1024()
+    a = bench.workload_config(cfg, 1)
+    b = bench.workload_config(W.plunge_2048x1024(), 1)
+    assert a == b and a["workload"] == "plunge_2048x1024" and (a["nx"], a["ny"]) == (2048, 1024)
+    assert set(a) == {"workload", "nx", "ny", "global_batch", "parallelism", "l2"}
+    cases = W.batch64()
+    c = bench.batch_config(cases, 2)
+    assert c["workload"] == "batch64" and c["cases"] == 64 and c["global_batch"] == 128
+    assert c["cells_per_step"] == sum(x.cells for x in cases)
