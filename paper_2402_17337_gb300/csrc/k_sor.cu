@@ -351,6 +351,10 @@ __device__ __forceinline__ void helm32_half_body(Geo g, HelmF32 h32, int grid, f
 __global__ void k_helm32_half(Geo g, HelmF32 h32, int grid, float* __restrict__ d, const float* __restrict__ r,
                               const float* __restrict__ invd, Band B, const uint8_t* __restrict__ fl,
                               const double* __restrict__ al, int colour, float omega, float beta) {
+  // launched as a programmatic dependent of the previous half-sweep: nothing
+  // is read before that launch has completed and its writes are visible
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   helm32_half_body(g, h32, grid, d, r, invd, B, fl, al, colour, omega, beta, blockIdx.x, blockIdx.y);
 }
 
@@ -452,8 +456,16 @@ void launch_helm32_half(cudaStream_t s, const Geo& g, const HelmF32& h32, int gr
                         const float* invd, const Band& band, const uint8_t* fl, const double* al, int colour,
                         float omega, float beta) {
   int ni = grid == 0 ? g.nx - 1 : g.nx, nj = grid == 0 ? g.ny : g.ny - 1;
-  k_helm32_half<<<grid2((ni + 1) / 2, nj), dim3(TBX, TBY), 0, s>>>(g, h32, grid, d, r, invd, band, fl, al, colour,
-                                                                   omega, beta);
+  cudaLaunchConfig_t lc{};
+  lc.gridDim = grid2((ni + 1) / 2, nj);
+  lc.blockDim = dim3(TBX, TBY);
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  cudaLaunchKernelEx(&lc, k_helm32_half, g, h32, grid, d, r, invd, band, fl, al, colour, omega, beta);
 }
 
 void launch_helm_add(cudaStream_t s, const Geo& g, int grid, double* x, const float* d) {
